@@ -1,0 +1,193 @@
+/*
+ * slmc.h -- C ABI of libslmc, the GB300 (sm_103a) hot path of symmetry-enforced
+ * self-learning Monte Carlo for the 2D Holstein model (arXiv:1802.06177).
+ *
+ * What the library computes (paper passages in brackets):
+ *   - ln|det(I + B_L ... B_1)|, its sign and the equal-time Green's function
+ *     G = (I + B_L ... B_1)^-1 for phonon fields x[N, L], with
+ *     B_l = diag(exp(-dtau lambda x[:, l])) exp(-dtau K)      [Suppl. Eq. (S2), (S3)];
+ *   - the full log-weight ln w(x) = 2 ln|det| + dtau lambda sum x - dtau S_Bose
+ *                                                              [Sec. "Model", Eq. (S2)];
+ *   - the symmetric effective model E_eff, its features and local Metropolis sweeps
+ *                                                              [Eq. (4) / (S7)];
+ *   - the cumulative update with exact acceptance              [Eq. (6)];
+ *   - the multi-linear regression of E_eff on ln w             [Eq. (5)];
+ *   - the CDW structure factor S(pi, pi) from G                [Sec. "Results"].
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments are DEVICE pointers owned by the caller (for example the
+ *     data pointers of torch tensors); the library never frees or retains them. The
+ *     library owns only the context and the workspace it allocates in slmc_init.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL = legacy default
+ *     stream); no call synchronises the host, so outputs are valid once the stream has
+ *     reached that point. A context may be used by one stream at a time.
+ *   - Site index i = ix + Lx * iy on the periodic Lx x Ly square lattice, N = Lx * Ly.
+ *     Phonon fields are row-major double x[n][N][L] (x[f*N*L + i*L + l]); column l
+ *     (0-based) belongs to slice matrix B_{l+1}. Matrices returned to the caller (G) are
+ *     row-major double [n][N][N].
+ *   - The coupling is the particle-hole symmetric lambda * x_i * (n_i - 1); the paper's
+ *     field X is x shifted by its mirror axis alpha = -g/Omega^2, and a = lambda/omega0^2
+ *     is the distance of the double-well minima from that axis.
+ *   - Effective-model couplings are a device array J[6] = {E0, J_k, J_p, J_p', J_nn,
+ *     J_nn'} with ln w_eff(x) = -dtau (E0 + J_k F_k + J_p F_p + J_p' F_p' + J_nn F_nn
+ *     + J_nn' F_nn').
+ *   - Every call returns a status code. Argument errors are detected on the host before
+ *     anything is enqueued. Errors that only the GPU can see (non-finite input or result,
+ *     a singular matrix) set a sticky flag in the context and make the affected outputs
+ *     NaN (sign 0); slmc_get_error synchronises the stream and reports them.
+ */
+#ifndef SLMC_H
+#define SLMC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SLMC_API __attribute__((visibility("default")))
+#else
+#define SLMC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SLMC_OK 0
+#define SLMC_ERR_ARG 1          /* bad argument (NULL pointer, size out of range) */
+#define SLMC_ERR_NONFINITE 2    /* NaN/Inf in an input field or a result */
+#define SLMC_ERR_CUDA 3         /* a CUDA runtime call failed */
+#define SLMC_ERR_TIMEOUT 4      /* a bounded device-side wait gave up */
+#define SLMC_ERR_UNSUPPORTED 5  /* valid but unsupported shape (odd side for checkerboard, N > 1024) */
+#define SLMC_ERR_NOMEM 6        /* workspace allocation failed in slmc_init */
+#define SLMC_ERR_SINGULAR 7     /* exactly singular matrix met in the final LU */
+
+/* Arithmetic of the slice products B_l ... B_{l+n_s-1} U between two stabilisations.
+ * The pivoted QR, the D scales, the final LU / log-det / G and every Metropolis
+ * log-ratio are FP64 in all modes. */
+#define SLMC_PREC_FP64 0    /* FP64 FMA */
+#define SLMC_PREC_FP32 1    /* FP32 FMA (SIMT) */
+#define SLMC_PREC_TF32X3 2  /* tensor cores, 3 x TF32 split products, FP32 accumulation */
+#define SLMC_PREC_BF16X9 3  /* tensor cores, 9 x BF16 split products, FP32 accumulation */
+
+/* Model, discretisation and algorithm parameters. */
+typedef struct slmc_params {
+    int Lx, Ly;          /* periodic lattice sides, >= 2 each; N = Lx * Ly <= 1024 */
+    int L;               /* imaginary-time slices, >= 1; beta = L * dtau */
+    double dtau;         /* Trotter step (> 0) */
+    double t;            /* nearest-neighbour hopping */
+    double mu;           /* chemical potential (0 = half filling) */
+    double omega0;       /* phonon frequency Omega (M = 1), > 0 */
+    double lambda;       /* electron-phonon coupling g */
+    int n_s;             /* slices multiplied between two QR stabilisations, >= 1 */
+    int precision;       /* SLMC_PREC_* */
+    double sweep_delta;  /* half-width of the uniform local proposal x -> x + U[-d, d] */
+    uint64_t seed;       /* Philox-4x32-10 key for sweeps and acceptance draws */
+} slmc_params;
+
+typedef struct slmc_ctx slmc_ctx;
+
+/* Returns a static, human-readable name for a status code. */
+SLMC_API const char* slmc_status_string(int status);
+
+/* Creates a context on the current CUDA device: validates *p, builds exp(-dtau K) on the
+ * device [Eq. (2), (S2)] and allocates the workspace for up to max_fields fields per
+ * internal batch (calls with more fields are processed in batches of max_fields).
+ * Workspace is about (6 N^2 + 4 N L) * 8 bytes per field. On success *out owns it.
+ * Errors: SLMC_ERR_ARG (p or out NULL, sizes out of range), SLMC_ERR_UNSUPPORTED
+ * (N > 1024), SLMC_ERR_NOMEM, SLMC_ERR_CUDA. */
+SLMC_API int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out);
+
+/* Frees the context and its workspace (synchronises the device first). NULL is a no-op. */
+SLMC_API int slmc_destroy(slmc_ctx* ctx);
+
+/* Synchronises `stream`, returns and clears the sticky device-side error of the context
+ * (SLMC_OK, SLMC_ERR_NONFINITE or SLMC_ERR_SINGULAR), or SLMC_ERR_CUDA if a kernel failed. */
+SLMC_API int slmc_get_error(slmc_ctx* ctx, void* stream);
+
+/* ln|det(I + B_L ... B_1)| and its sign for n fields, one spin species
+ * [Suppl. Eq. (S2)]. The product is stabilised every n_s slices by a pivoted
+ * Householder QR (UDT form); the last group may hold fewer than n_s slices.
+ *   x      [n][N][L] input fields (read only)
+ *   lndet  [n] output, ln|det|
+ *   sign   [n] output, +1 / -1 (0 if the result is not finite)
+ * n = 0 is a no-op. */
+SLMC_API int slmc_logdet(slmc_ctx* ctx, const double* x, int n, double* lndet, int* sign, void* stream);
+
+/* As slmc_logdet, and also the equal-time Green's function G = (I + B_L ... B_1)^-1
+ * (the paper's G(L) of Suppl. Eq. (S3)), written row-major to G[n][N][N]. */
+SLMC_API int slmc_greens(slmc_ctx* ctx, const double* x, int n, double* G, double* lndet, int* sign,
+                void* stream);
+
+/* Full log-weight of n configurations [Sec. "Model", Eq. (S2)]:
+ *   ln w = 2 ln|det| + dtau lambda sum_{i,l} x - dtau sum_{i,l} [omega0^2 x^2 / 2
+ *          + (x_{i,l+1} - x_{i,l})^2 / (2 dtau^2)]   (l periodic).
+ * lnw [n] output; lndet [n] and sign [n] optional outputs (may be NULL). */
+SLMC_API int slmc_log_weight(slmc_ctx* ctx, const double* x, int n, double* lnw, double* lndet, int* sign,
+                    void* stream);
+
+/* The five features of the symmetric effective model [Eq. (4) / (S7)] for n fields:
+ * F[n][5] = {F_k, F_p, F_p', F_nn, F_nn'} with
+ *   F_k = sum (x_{i,l+1} - x_{i,l})^2,  F_p = sum (x^4/4 - a^2 x^2/2),
+ *   F_p' = sum (x^6/6 - a^2 x^4/4),     F_nn = sum over bonds (+x, +y from each site) x_i x_j,
+ *   F_nn' = sum x_{i,l} x_{i,l+1}      (all sums over sites and slices, l periodic). */
+SLMC_API int slmc_eff_features(slmc_ctx* ctx, const double* x, int n, double* F, void* stream);
+
+/* ln w_eff(x) = -dtau (E0 + J . F(x)) for n fields into lnw_eff[n]; J is a device [6]. */
+SLMC_API int slmc_eff_log_weight(slmc_ctx* ctx, const double* x, int n, const double* J, double* lnw_eff,
+                        void* stream);
+
+/* Metropolis sweeps of the effective model on n independent chains, in place
+ * [Sec. "SLMC": local updates are O(1) on the bosonic model]. One sweep visits the
+ * checkerboard colours (ix + iy + l) mod 2 in the order first_colour, 1 - first_colour;
+ * each site proposes x + U[-sweep_delta, sweep_delta] and accepts with probability
+ * min(1, exp(-dtau dE_eff)). Sweep s of this call uses the Philox counter
+ * (i*L + l, sweep0 + s, chain, 0) with key = seed. Requires even Lx, Ly and L
+ * (else SLMC_ERR_UNSUPPORTED).
+ *   x       [n][N][L] in/out
+ *   J       [6] device couplings
+ *   n_acc   [n] int64 in/out: accepted local moves are added (may be NULL) */
+SLMC_API int slmc_eff_sweep(slmc_ctx* ctx, double* x, int n, const double* J, int nsweeps, uint64_t sweep0,
+                   int first_colour, long long* n_acc, void* stream);
+
+/* Prepares chain state for slmc_cumulative_update: lnw[n] = ln w(x) and, if s_cdw is not
+ * NULL, s_cdw[n] = S(pi,pi) of each configuration. */
+SLMC_API int slmc_chain_init(slmc_ctx* ctx, const double* x, int n, double* lnw, double* s_cdw, void* stream);
+
+/* nupdates cumulative updates of n independent chains [Eq. (6)]. Update u (global index
+ * update0 + u) of chain c draws Philox block (update0 + u, 0, c, 1): bit 0 of word 0 is
+ * the first colour, words 2-3 the acceptance uniform. It then runs nsweeps effective-
+ * model sweeps with sweep counters (update0 + u) * nsweeps + s, evaluates the exact
+ * ln w(x') and accepts with min{1, [w(x')/w(x)] [w_eff(x)/w_eff(x')]}; on rejection x is
+ * restored. The random starting colour makes the proposal reversible w.r.t. w_eff.
+ *   x            [n][N][L] in/out chain states
+ *   J            [6] device couplings of E_eff
+ *   lnw          [n] in/out cached exact ln w of the current states
+ *   s_cdw        [n] in/out cached S(pi,pi) of the current states (may be NULL)
+ *   n_acc        [n] int64 in/out, accepted cumulative updates are added (may be NULL)
+ *   n_sweep_acc  [n] int64 in/out, accepted local moves are added (may be NULL)
+ *   obs          [nupdates][n] out, S(pi,pi) of the state after each update (may be NULL;
+ *                requires s_cdw) */
+SLMC_API int slmc_cumulative_update(slmc_ctx* ctx, double* x, int n, const double* J, int nsweeps,
+                           int nupdates, uint64_t update0, double* lnw, double* s_cdw,
+                           long long* n_acc, long long* n_sweep_acc, double* obs, void* stream);
+
+/* Multi-linear regression of the effective model [Eq. (5)]: least squares of
+ * lnw[c] on [1, F(xs[c])] over nconf configurations (Givens-rotation QR in FP64), then
+ * (E0, J) = -coefficients / dtau.
+ *   xs     [nconf][N][L] configurations, lnw [nconf] their exact log-weights
+ *   J_out  [6] device output {E0, J_k, J_p, J_p', J_nn, J_nn'}
+ *   resid  [1] device output, RMS residual of ln w (may be NULL)
+ * nconf must be >= 6. */
+SLMC_API int slmc_fit_eff(slmc_ctx* ctx, const double* xs, const double* lnw, int nconf, double* J_out,
+                 double* resid, void* stream);
+
+/* CDW structure factor per configuration [Sec. "Results"] from G [n][N][N] (row-major):
+ * S = (1/N) sum_ij s_i s_j [4 (1 - G_ii)(1 - G_jj) + 2 (delta_ij - G_ji) G_ij],
+ * s_i = (-1)^(ix+iy). Output S[n]. */
+SLMC_API int slmc_measure_cdw(slmc_ctx* ctx, const double* G, int n, double* S, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLMC_H */

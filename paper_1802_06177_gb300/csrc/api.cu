@@ -1,0 +1,298 @@
+// C ABI of libslmc: argument validation, workspace ownership and the enqueue order of the
+// kernels that make up each entry point. No entry point synchronises the host except
+// slmc_init, slmc_destroy and slmc_get_error.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <new>
+
+#include "slmc_internal.cuh"
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+#define SLMC_CK(expr)                                    \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess) return SLMC_ERR_CUDA;     \
+    } while (0)
+
+#define SLMC_TRY(expr)                 \
+    do {                               \
+        int st_ = (expr);              \
+        if (st_ != SLMC_OK) return st_; \
+    } while (0)
+
+constexpr int kMaxGridY = 65535;
+
+int validate(const slmc_params* p) {
+    if (!p) return SLMC_ERR_ARG;
+    if (p->Lx < 2 || p->Ly < 2 || p->L < 1 || p->n_s < 1) return SLMC_ERR_ARG;
+    if (!(p->dtau > 0.0) || !(p->omega0 > 0.0) || !std::isfinite(p->t) || !std::isfinite(p->mu) ||
+        !std::isfinite(p->lambda) || !std::isfinite(p->dtau) || !std::isfinite(p->omega0) ||
+        !std::isfinite(p->sweep_delta) || p->sweep_delta < 0.0)
+        return SLMC_ERR_ARG;
+    if (p->precision < SLMC_PREC_FP64 || p->precision > SLMC_PREC_BF16X9) return SLMC_ERR_ARG;
+    if ((long long)p->Lx * p->Ly > SLMC_MAX_N) return SLMC_ERR_UNSUPPORTED;
+    if ((long long)p->Lx * p->Ly * p->L >= (1ll << 31)) return SLMC_ERR_UNSUPPORTED;
+    return SLMC_OK;
+}
+
+bool checkerboard_ok(const slmc_ctx* c) { return c->p.Lx % 2 == 0 && c->p.Ly % 2 == 0 && c->L % 2 == 0; }
+
+// Scratch columns of ctx->scal ([8][max_fields]) and ctx->iscal ([4][max_fields]).
+double* scal(slmc_ctx* c, int col) { return c->scal + (size_t)col * c->max_fields; }
+int* iscal(slmc_ctx* c, int col) { return c->iscal + (size_t)col * c->max_fields; }
+
+// Stabilised UDT chain + final LU for fields [0, nf) of one batch (nf <= max_fields).
+int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, double* G, cudaStream_t s) {
+    SLMC_CK(slmc::set_identity(c, nf, s));
+    for (int l0 = 0; l0 < c->L; l0 += c->p.n_s) {
+        const int nsl = std::min(c->p.n_s, c->L - l0);
+        if (c->p.precision == SLMC_PREC_TF32X3 || c->p.precision == SLMC_PREC_BF16X9)
+            SLMC_CK(slmc::tc_slice_group(c, x, nf, l0, nsl, s));
+        else
+            SLMC_CK(slmc::slice_group(c, x, nf, l0, nsl, s));
+        SLMC_CK(slmc::qr_pivoted(c, nf, s));
+        SLMC_CK(slmc::form_q(c, nf, s));
+        SLMC_CK(slmc::t_update(c, nf, s));
+    }
+    SLMC_CK(slmc::final_logdet(c, nf, lndet, sign, s));
+    if (G) SLMC_CK(slmc::final_greens(c, nf, G, s));
+    return SLMC_OK;
+}
+
+template <typename F>
+int for_batches(slmc_ctx* c, int n, F&& fn) {
+    for (int f0 = 0; f0 < n; f0 += c->max_fields) {
+        const int nf = std::min(c->max_fields, n - f0);
+        SLMC_TRY(fn(f0, nf));
+    }
+    return SLMC_OK;
+}
+
+void free_ctx(slmc_ctx* c) {
+    void* bufs[] = {c->E64, c->E32, c->Etf, c->Ebf, c->Y, c->QR, c->U, c->Ta, c->Tb, c->lnD, c->tau,
+                    c->perm, c->piv, c->sgnU, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* slmc_status_string(int status) {
+    switch (status) {
+        case SLMC_OK: return "ok";
+        case SLMC_ERR_ARG: return "invalid argument";
+        case SLMC_ERR_NONFINITE: return "non-finite input or result";
+        case SLMC_ERR_CUDA: return "CUDA runtime error";
+        case SLMC_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SLMC_ERR_UNSUPPORTED: return "unsupported shape or mode";
+        case SLMC_ERR_NOMEM: return "out of device memory";
+        case SLMC_ERR_SINGULAR: return "singular matrix";
+        default: return "unknown status";
+    }
+}
+
+int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
+    if (!out) return SLMC_ERR_ARG;
+    *out = nullptr;
+    SLMC_TRY(validate(p));
+    if (max_fields < 1 || max_fields > kMaxGridY) return SLMC_ERR_ARG;
+    if (p->precision == SLMC_PREC_TF32X3 || p->precision == SLMC_PREC_BF16X9) return SLMC_ERR_UNSUPPORTED;
+    slmc_ctx* c = new (std::nothrow) slmc_ctx();
+    if (!c) return SLMC_ERR_NOMEM;
+    c->p = *p;
+    c->N = p->Lx * p->Ly;
+    c->L = p->L;
+    c->max_fields = max_fields;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return SLMC_ERR_CUDA;
+    }
+    const size_t N = c->N, L = c->L, F = max_fields, NN = N * N;
+    bool ok = true;
+    auto alloc = [&](auto** ptr, size_t bytes) {
+        if (!ok) return;
+        if (cudaMalloc(reinterpret_cast<void**>(ptr), bytes) != cudaSuccess) ok = false;
+    };
+    alloc(&c->E64, NN * sizeof(double));
+    alloc(&c->E32, NN * sizeof(float));
+    if (p->precision == SLMC_PREC_TF32X3) alloc(&c->Etf, 2 * NN * sizeof(uint32_t));
+    if (p->precision == SLMC_PREC_BF16X9) alloc(&c->Ebf, 3 * NN * sizeof(uint16_t));
+    alloc(&c->Y, F * NN * sizeof(double));
+    alloc(&c->QR, F * NN * sizeof(double));
+    alloc(&c->U, F * NN * sizeof(double));
+    alloc(&c->Ta, F * NN * sizeof(double));
+    alloc(&c->Tb, F * NN * sizeof(double));
+    alloc(&c->lnD, F * N * sizeof(double));
+    alloc(&c->tau, F * N * sizeof(double));
+    alloc(&c->perm, F * N * sizeof(int));
+    alloc(&c->piv, F * N * sizeof(int));
+    alloc(&c->sgnU, F * sizeof(int));
+    alloc(&c->x_old, F * N * L * sizeof(double));
+    alloc(&c->scal, 8 * F * sizeof(double));
+    alloc(&c->iscal, 4 * F * sizeof(int));
+    alloc(&c->feat, 8 * F * sizeof(double));
+    alloc(&c->fitR, 64 * sizeof(double));
+    alloc(&c->err, sizeof(unsigned int));
+    if (!ok) {
+        cudaGetLastError();
+        free_ctx(c);
+        return SLMC_ERR_NOMEM;
+    }
+    if (cudaMemset(c->err, 0, sizeof(unsigned int)) != cudaSuccess ||
+        slmc::build_hopping_exp(c, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        free_ctx(c);
+        return SLMC_ERR_CUDA;
+    }
+    *out = c;
+    return SLMC_OK;
+}
+
+int slmc_destroy(slmc_ctx* c) {
+    if (!c) return SLMC_OK;
+    const cudaError_t e = cudaDeviceSynchronize();
+    free_ctx(c);
+    return e == cudaSuccess ? SLMC_OK : SLMC_ERR_CUDA;
+}
+
+int slmc_get_error(slmc_ctx* c, void* stream) {
+    if (!c) return SLMC_ERR_ARG;
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return SLMC_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return SLMC_ERR_CUDA;
+    unsigned int bits = 0;
+    if (cudaMemcpy(&bits, c->err, sizeof(bits), cudaMemcpyDeviceToHost) != cudaSuccess) return SLMC_ERR_CUDA;
+    if (bits && cudaMemset(c->err, 0, sizeof(bits)) != cudaSuccess) return SLMC_ERR_CUDA;
+    if (bits & SLMC_EBIT_SINGULAR) return SLMC_ERR_SINGULAR;
+    if (bits & SLMC_EBIT_NONFINITE) return SLMC_ERR_NONFINITE;
+    return SLMC_OK;
+}
+
+int slmc_logdet(slmc_ctx* c, const double* x, int n, double* lndet, int* sign, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!x || !lndet || !sign))) return SLMC_ERR_ARG;
+    const size_t NL = (size_t)c->N * c->L;
+    return for_batches(c, n, [&](int f0, int nf) {
+        return logdet_batch(c, x + f0 * NL, nf, lndet + f0, sign + f0, nullptr, as_stream(stream));
+    });
+}
+
+int slmc_greens(slmc_ctx* c, const double* x, int n, double* G, double* lndet, int* sign, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!x || !G || !lndet || !sign))) return SLMC_ERR_ARG;
+    const size_t NL = (size_t)c->N * c->L, NN = (size_t)c->N * c->N;
+    return for_batches(c, n, [&](int f0, int nf) {
+        return logdet_batch(c, x + f0 * NL, nf, lndet + f0, sign + f0, G + f0 * NN, as_stream(stream));
+    });
+}
+
+int slmc_log_weight(slmc_ctx* c, const double* x, int n, double* lnw, double* lndet, int* sign, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!x || !lnw))) return SLMC_ERR_ARG;
+    const size_t NL = (size_t)c->N * c->L;
+    cudaStream_t s = as_stream(stream);
+    return for_batches(c, n, [&](int f0, int nf) {
+        double* ld = lndet ? lndet + f0 : scal(c, 0);
+        int* sg = sign ? sign + f0 : iscal(c, 0);
+        SLMC_TRY(logdet_batch(c, x + f0 * NL, nf, ld, sg, nullptr, s));
+        SLMC_CK(slmc::bose_log_weight(c, x + f0 * NL, nf, ld, lnw + f0, s));
+        return SLMC_OK;
+    });
+}
+
+int slmc_eff_features(slmc_ctx* c, const double* x, int n, double* F, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!x || !F))) return SLMC_ERR_ARG;
+    if (n == 0) return SLMC_OK;
+    SLMC_CK(slmc::eff_features(c, x, n, nullptr, F, 5, nullptr, as_stream(stream)));
+    return SLMC_OK;
+}
+
+int slmc_eff_log_weight(slmc_ctx* c, const double* x, int n, const double* J, double* lnw_eff, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!x || !J || !lnw_eff))) return SLMC_ERR_ARG;
+    if (n == 0) return SLMC_OK;
+    SLMC_CK(slmc::eff_features(c, x, n, J, nullptr, 0, lnw_eff, as_stream(stream)));
+    return SLMC_OK;
+}
+
+int slmc_eff_sweep(slmc_ctx* c, double* x, int n, const double* J, int nsweeps, uint64_t sweep0, int first_colour,
+                   long long* n_acc, void* stream) {
+    if (!c || n < 0 || n > kMaxGridY || nsweeps < 0 || (first_colour != 0 && first_colour != 1) ||
+        (n > 0 && (!x || !J)))
+        return SLMC_ERR_ARG;
+    if (!checkerboard_ok(c)) return SLMC_ERR_UNSUPPORTED;
+    cudaStream_t s = as_stream(stream);
+    for (int sw = 0; sw < nsweeps && n > 0; ++sw)
+        for (int h = 0; h < 2; ++h)
+            SLMC_CK(slmc::eff_half_sweep(c, x, n, 0, J, sweep0 + sw, first_colour ^ h, nullptr, 0, n_acc, s));
+    return SLMC_OK;
+}
+
+int slmc_chain_init(slmc_ctx* c, const double* x, int n, double* lnw, double* s_cdw, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!x || !lnw))) return SLMC_ERR_ARG;
+    const size_t NL = (size_t)c->N * c->L;
+    cudaStream_t s = as_stream(stream);
+    return for_batches(c, n, [&](int f0, int nf) {
+        SLMC_TRY(logdet_batch(c, x + f0 * NL, nf, scal(c, 0), iscal(c, 0), s_cdw ? c->QR : nullptr, s));
+        SLMC_CK(slmc::bose_log_weight(c, x + f0 * NL, nf, scal(c, 0), lnw + f0, s));
+        if (s_cdw) SLMC_CK(slmc::cdw_measure(c, c->QR, nf, s_cdw + f0, nullptr, nullptr, s));
+        return SLMC_OK;
+    });
+}
+
+int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int nsweeps, int nupdates,
+                           uint64_t update0, double* lnw, double* s_cdw, long long* n_acc, long long* n_sweep_acc,
+                           double* obs, void* stream) {
+    if (!c || n < 0 || nsweeps < 0 || nupdates < 0 || (n > 0 && (!x || !J || !lnw)) || (obs && !s_cdw))
+        return SLMC_ERR_ARG;
+    if (!checkerboard_ok(c)) return SLMC_ERR_UNSUPPORTED;
+    const size_t NL = (size_t)c->N * c->L;
+    cudaStream_t s = as_stream(stream);
+    return for_batches(c, n, [&](int f0, int nf) {
+        double* xc = x + f0 * NL;
+        for (int u = 0; u < nupdates; ++u) {
+            const uint64_t upd = update0 + (uint64_t)u;
+            SLMC_CK(slmc::update_draws(c, nf, f0, upd, iscal(c, 1), scal(c, 4), s));
+            SLMC_CK(cudaMemcpyAsync(c->x_old, xc, nf * NL * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            SLMC_CK(slmc::eff_features(c, xc, nf, J, nullptr, 0, scal(c, 1), s));
+            for (int sw = 0; sw < nsweeps; ++sw)
+                for (int h = 0; h < 2; ++h)
+                    SLMC_CK(slmc::eff_half_sweep(c, xc, nf, f0, J, upd * (uint64_t)nsweeps + sw, 0, iscal(c, 1), h,
+                                                 n_sweep_acc ? n_sweep_acc + f0 : nullptr, s));
+            SLMC_CK(slmc::eff_features(c, xc, nf, J, nullptr, 0, scal(c, 2), s));
+            SLMC_TRY(logdet_batch(c, xc, nf, scal(c, 0), iscal(c, 0), s_cdw ? c->QR : nullptr, s));
+            SLMC_CK(slmc::bose_log_weight(c, xc, nf, scal(c, 0), scal(c, 3), s));
+            SLMC_CK(slmc::accept_update(c, nf, xc, c->x_old, scal(c, 3), scal(c, 1), scal(c, 2), scal(c, 4), lnw + f0,
+                                        iscal(c, 2), n_acc ? n_acc + f0 : nullptr, s));
+            if (s_cdw)
+                SLMC_CK(slmc::cdw_measure(c, c->QR, nf, s_cdw + f0, iscal(c, 2),
+                                          obs ? obs + (size_t)u * n + f0 : nullptr, s));
+        }
+        return SLMC_OK;
+    });
+}
+
+int slmc_fit_eff(slmc_ctx* c, const double* xs, const double* lnw, int nconf, double* J_out, double* resid,
+                 void* stream) {
+    if (!c || nconf < 6 || !xs || !lnw || !J_out) return SLMC_ERR_ARG;
+    const size_t NL = (size_t)c->N * c->L;
+    cudaStream_t s = as_stream(stream);
+    SLMC_CK(slmc::fit_begin(c, s));
+    SLMC_TRY(for_batches(c, nconf, [&](int f0, int nf) {
+        SLMC_CK(slmc::eff_features(c, xs + f0 * NL, nf, nullptr, c->feat, 8, nullptr, s));
+        SLMC_CK(slmc::fit_accumulate(c, c->feat, lnw + f0, nf, s));
+        return SLMC_OK;
+    }));
+    SLMC_CK(slmc::fit_finish(c, nconf, J_out, resid, s));
+    return SLMC_OK;
+}
+
+int slmc_measure_cdw(slmc_ctx* c, const double* G, int n, double* S, void* stream) {
+    if (!c || n < 0 || (n > 0 && (!G || !S))) return SLMC_ERR_ARG;
+    if (n == 0) return SLMC_OK;
+    SLMC_CK(slmc::cdw_measure(c, G, n, S, nullptr, nullptr, as_stream(stream)));
+    return SLMC_OK;
+}
+
+}  // extern "C"

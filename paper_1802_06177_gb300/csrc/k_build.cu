@@ -1,0 +1,73 @@
+// E = exp(-dtau K) for the periodic square lattice [Eq. (2), Suppl. Eq. (S2)], built on the
+// device from the plane-wave eigenbasis of K:
+//   E_ij = (1/N) sum_k cos(k . (r_i - r_j)) exp(-dtau eps_k),  eps_k = -2t (cos kx + cos ky) - mu,
+// k = 2 pi (nx/Lx, ny/Ly). Phases are formed as exact rationals and evaluated with cospi.
+// Low-precision copies and tensor-core operand splits of E are derived from the FP64 matrix.
+#include <cuda_bf16.h>
+
+#include "slmc_internal.cuh"
+
+namespace {
+
+__global__ void k_hopping_exp(double* __restrict__ E, int Lx, int Ly, double dtau, double t, double mu) {
+    const int N = Lx * Ly;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    const int i = idx / N, j = idx - (idx / N) * N;
+    const int dx = ((i % Lx) - (j % Lx) + Lx) % Lx;
+    const int dy = ((i / Lx) - (j / Lx) + Ly) % Ly;
+    double acc = 0.0;
+    for (int ny = 0; ny < Ly; ++ny) {
+        for (int nx = 0; nx < Lx; ++nx) {
+            const double eps = -2.0 * t * (cospi(2.0 * nx / Lx) + cospi(2.0 * ny / Ly)) - mu;
+            const int px = (nx * dx) % Lx, py = (ny * dy) % Ly;
+            const double phase = (double)px / Lx + (double)py / Ly;  // in [0, 2)
+            acc += cospi(2.0 * phase) * exp(-dtau * eps);
+        }
+    }
+    E[idx] = acc / N;
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+}
+
+__global__ void k_split_E(const double* __restrict__ E, float* __restrict__ E32, uint32_t* __restrict__ Etf,
+                          uint16_t* __restrict__ Ebf, int NN) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= NN) return;
+    const float v = (float)E[idx];
+    E32[idx] = v;
+    if (Etf) {
+        const uint32_t hi = to_tf32(v);
+        const uint32_t lo = to_tf32(v - __uint_as_float(hi));
+        Etf[idx] = hi;
+        Etf[NN + idx] = lo;
+    }
+    if (Ebf) {
+        const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
+        const float r1 = v - __bfloat162float(b0);
+        const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(b1);
+        const __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
+        Ebf[idx] = __bfloat16_as_ushort(b0);
+        Ebf[NN + idx] = __bfloat16_as_ushort(b1);
+        Ebf[2 * NN + idx] = __bfloat16_as_ushort(b2);
+    }
+}
+
+}  // namespace
+
+namespace slmc {
+
+cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s) {
+    const int N = c->N;
+    const int NN = N * N;
+    k_hopping_exp<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->p.Lx, c->p.Ly, c->p.dtau, c->p.t, c->p.mu);
+    k_split_E<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->E32, c->Etf, c->Ebf, NN);
+    return cudaGetLastError();
+}
+
+}  // namespace slmc

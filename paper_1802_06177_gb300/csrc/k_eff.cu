@@ -1,0 +1,334 @@
+// Bosonic parts of the weight, the symmetric effective model and its Markov chain, the
+// cumulative-update acceptance, the CDW structure factor and the E_eff regression.
+//
+//   ln w       = 2 ln|det| + dtau lam sum x - dtau sum [w0^2 x^2/2 + (x_{l+1}-x_l)^2/(2 dtau^2)]
+//                                                             [Sec. "Model", Suppl. Eq. (S2)]
+//   ln w_eff   = -dtau (E0 + J_k F_k + J_p F_p + J_p' F_p' + J_nn F_nn + J_nn' F_nn')
+//                                                             [Eq. (4) / (S7)]
+//   acceptance = min{1, [w(x')/w(x)] [w_eff(x)/w_eff(x')]}   [Eq. (6)]
+//   S(pi,pi)   = (1/N) sum_ij s_i s_j [4 (1-G_ii)(1-G_jj) + 2 (d_ij - G_ji) G_ij]  [Sec. "Results"]
+//   fit        = least squares of ln w on [1, F]               [Eq. (5)]
+//
+// Site i = ix + Lx iy, field element (i, l) at i*L + l. All reductions use a fixed
+// order (per-thread strided partial sums, then a shared-memory tree), so results are
+// reproducible run to run.
+#include <cfloat>
+
+#include "slmc_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red /* [NV][kThreads] */) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[q * kThreads + threadIdx.x] = v[q];
+    __syncthreads();
+    for (int h = kThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) red[q * kThreads + threadIdx.x] += red[q * kThreads + threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = red[q * kThreads];
+}
+
+__global__ void __launch_bounds__(kThreads) k_bose(const double* __restrict__ x, int N, int L, double dtau, double lam,
+                                                   double w02, const double* __restrict__ lndet, double* __restrict__ lnw) {
+    __shared__ double red[kThreads];
+    const int f = blockIdx.x;
+    const double* xf = x + (size_t)f * N * L;
+    const double inv2dt2 = 1.0 / (2.0 * dtau * dtau);
+    double acc[1] = {0.0};
+    for (int idx = threadIdx.x; idx < N * L; idx += kThreads) {
+        const int i = idx / L, l = idx - i * L;
+        const double v = xf[idx];
+        const double vn = xf[(size_t)i * L + (l + 1 == L ? 0 : l + 1)];
+        const double d = vn - v;
+        acc[0] += dtau * lam * v - dtau * (0.5 * w02 * v * v + d * d * inv2dt2);
+    }
+    block_sum<1>(acc, red);
+    if (threadIdx.x == 0) lnw[f] = (lndet ? 2.0 * lndet[f] : 0.0) + acc[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_features(const double* __restrict__ x, int Lx, int Ly, int L, double a2,
+                                                       double dtau, const double* __restrict__ J,
+                                                       double* __restrict__ F, int ldF, double* __restrict__ lnw_eff) {
+    __shared__ double red[5 * kThreads];
+    const int f = blockIdx.x;
+    const int N = Lx * Ly;
+    const double* xf = x + (size_t)f * N * L;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int idx = threadIdx.x; idx < N * L; idx += kThreads) {
+        const int i = idx / L, l = idx - i * L;
+        const int ix = i % Lx, iy = i / Lx;
+        const double v = xf[idx];
+        const double vt = xf[(size_t)i * L + (l + 1 == L ? 0 : l + 1)];
+        const double vx = xf[(size_t)((ix + 1 == Lx ? 0 : ix + 1) + Lx * iy) * L + l];
+        const double vy = xf[(size_t)(ix + Lx * (iy + 1 == Ly ? 0 : iy + 1)) * L + l];
+        const double v2 = v * v;
+        const double d = vt - v;
+        acc[0] += d * d;
+        acc[1] += v2 * v2 * 0.25 - a2 * v2 * 0.5;
+        acc[2] += v2 * v2 * v2 * (1.0 / 6.0) - a2 * v2 * v2 * 0.25;
+        acc[3] += v * (vx + vy);
+        acc[4] += v * vt;
+    }
+    block_sum<5>(acc, red);
+    if (threadIdx.x == 0) {
+        if (F)
+            for (int q = 0; q < 5; ++q) F[(size_t)f * ldF + q] = acc[q];
+        if (lnw_eff) {
+            const double e = J[0] + J[1] * acc[0] + J[2] * acc[1] + J[3] * acc[2] + J[4] * acc[3] + J[5] * acc[4];
+            lnw_eff[f] = -dtau * e;
+        }
+    }
+}
+
+// Terms of E0 + J.F that contain one site value v.
+__device__ __forceinline__ double local_energy(const double* J, double a2, double v, double up, double dn, double nb) {
+    const double v2 = v * v;
+    const double du = up - v, dd = v - dn;
+    return J[1] * (du * du + dd * dd) + J[2] * (v2 * v2 * 0.25 - a2 * v2 * 0.5) +
+           J[3] * (v2 * v2 * v2 * (1.0 / 6.0) - a2 * v2 * v2 * 0.25) + J[4] * v * nb + J[5] * v * (up + dn);
+}
+
+// One checkerboard half-sweep over all chains. Thread s of chain f owns site i = s / (L/2)
+// and the slice l of the requested colour in the pair (2 (s mod L/2), 2 (s mod L/2) + 1).
+__global__ void __launch_bounds__(kThreads) k_half_sweep(double* __restrict__ x, int Lx, int Ly, int L,
+                                                         const double* __restrict__ Jg, double dtau, double a2,
+                                                         double delta, uint32_t key0, uint32_t key1, uint32_t sweep,
+                                                         int colour, const int* __restrict__ colour_pc, int cxor,
+                                                         int chain0, unsigned long long* __restrict__ n_acc) {
+    __shared__ double J[6];
+    __shared__ int s_cnt;
+    if (threadIdx.x < 6) J[threadIdx.x] = Jg[threadIdx.x];
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const int f = blockIdx.y;
+    const int N = Lx * Ly, half = L / 2;
+    const int s = blockIdx.x * kThreads + threadIdx.x;
+    int accepted = 0;
+    if (s < N * half) {
+        const int c = colour_pc ? (colour_pc[f] ^ cxor) : colour;
+        const int i = s / half, lp = s - i * half;
+        const int ix = i % Lx, iy = i / Lx;
+        const int l = 2 * lp + ((ix + iy + c) & 1);
+        double* xf = x + (size_t)f * N * L;
+        const double v = xf[(size_t)i * L + l];
+        const double up = xf[(size_t)i * L + (l + 1 == L ? 0 : l + 1)];
+        const double dn = xf[(size_t)i * L + (l == 0 ? L - 1 : l - 1)];
+        const int xp = (ix + 1 == Lx ? 0 : ix + 1) + Lx * iy, xm = (ix == 0 ? Lx - 1 : ix - 1) + Lx * iy;
+        const int yp = ix + Lx * (iy + 1 == Ly ? 0 : iy + 1), ym = ix + Lx * (iy == 0 ? Ly - 1 : iy - 1);
+        const double nb = xf[(size_t)xp * L + l] + xf[(size_t)xm * L + l] + xf[(size_t)yp * L + l] + xf[(size_t)ym * L + l];
+        const slmc::u32x4 w = slmc::philox4x32_10(slmc::u32x4{(uint32_t)(i * L + l), sweep, (uint32_t)(chain0 + f), 0u}, key0, key1);
+        const double u1 = slmc::uniform53(w.x, w.y), u2 = slmc::uniform53(w.z, w.w);
+        // x' = x + delta (2 u1 - 1), rounded step by step (no contraction) as in the oracle
+        const double xn = __dadd_rn(v, __dmul_rn(delta, __dadd_rn(__dmul_rn(2.0, u1), -1.0)));
+        const double dE = local_energy(J, a2, xn, up, dn, nb) - local_energy(J, a2, v, up, dn, nb);
+        const double dlnw = -dtau * dE;
+        if (dlnw >= 0.0 || u2 < exp(dlnw)) {
+            xf[(size_t)i * L + l] = xn;
+            accepted = 1;
+        }
+    }
+    const unsigned int ballot = __ballot_sync(0xffffffffu, accepted);
+    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(&s_cnt, __popc(ballot));
+    __syncthreads();
+    if (threadIdx.x == 0 && n_acc && s_cnt) atomicAdd(n_acc + f, (unsigned long long)s_cnt);
+}
+
+__global__ void k_update_draws(int nf, int chain0, uint32_t update, uint32_t key0, uint32_t key1,
+                               int* __restrict__ first, double* __restrict__ u) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const slmc::u32x4 w = slmc::philox4x32_10(slmc::u32x4{update, 0u, (uint32_t)(chain0 + f), 1u}, key0, key1);
+    first[f] = (int)(w.x & 1u);
+    u[f] = slmc::uniform53(w.z, w.w);
+}
+
+__global__ void k_accept(int nf, const double* __restrict__ lnw_new, const double* __restrict__ lnweff_old,
+                         const double* __restrict__ lnweff_new, const double* __restrict__ u, double* __restrict__ lnw,
+                         int* __restrict__ accepted, unsigned long long* __restrict__ n_acc) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const double lnA = (lnw_new[f] - lnw[f]) - (lnweff_new[f] - lnweff_old[f]);
+    const bool acc = lnA >= 0.0 || u[f] < exp(lnA);
+    accepted[f] = acc ? 1 : 0;
+    if (acc) {
+        lnw[f] = lnw_new[f];
+        if (n_acc) n_acc[f] += 1ull;
+    }
+}
+
+__global__ void k_restore(double* __restrict__ x, const double* __restrict__ x_old, const int* __restrict__ accepted,
+                          int NL) {
+    const int f = blockIdx.y;
+    if (accepted[f]) return;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NL; idx += gridDim.x * blockDim.x)
+        x[(size_t)f * NL + idx] = x_old[(size_t)f * NL + idx];
+}
+
+__global__ void __launch_bounds__(kThreads) k_cdw(const double* __restrict__ G, int Lx, int Ly, double* __restrict__ S,
+                                                  const int* __restrict__ only_if, double* __restrict__ obs) {
+    __shared__ double red[3 * kThreads];
+    const int f = blockIdx.x;
+    const int N = Lx * Ly;
+    const size_t NN = (size_t)N * N;
+    const bool update = !only_if || only_if[f];
+    if (update) {
+        const double* Gf = G + f * NN;
+        double acc[3] = {0.0, 0.0, 0.0};  // sum s_i (1 - G_ii), sum G_ii, sum s_i s_j G_ij G_ji
+        for (int i = threadIdx.x; i < N; i += kThreads) {
+            const double si = (((i % Lx) + (i / Lx)) & 1) ? -1.0 : 1.0;
+            const double g = Gf[(size_t)i * N + i];
+            acc[0] += si * (1.0 - g);
+            acc[1] += g;
+        }
+        for (size_t idx = threadIdx.x; idx < NN; idx += kThreads) {
+            const int i = (int)(idx / N), j = (int)(idx - (size_t)i * N);
+            const double sij = ((((i % Lx) + (i / Lx)) ^ ((j % Lx) + (j / Lx))) & 1) ? -1.0 : 1.0;
+            acc[2] += sij * Gf[idx] * Gf[(size_t)j * N + i];
+        }
+        block_sum<3>(acc, red);  // block-uniform branch: `update` depends on f only
+        if (threadIdx.x == 0) S[f] = (4.0 * acc[0] * acc[0] + 2.0 * acc[1] - 2.0 * acc[2]) / N;
+    }
+    if (obs && threadIdx.x == 0) obs[f] = S[f];
+}
+
+// ---- regression: Givens-rotation QR of the rows [1, (F - F_ref)/sc, y - y_ref] into a 7x7 R ----
+// fitR layout: R[7][7] row-major (0..48), ref[6] (49..54: F_ref[5], y_ref), flag (55), count (56).
+__global__ void k_fit_begin(double* __restrict__ R) {
+    for (int q = threadIdx.x; q < 64; q += blockDim.x) R[q] = 0.0;
+}
+
+__global__ void k_fit_accumulate(double* __restrict__ R, const double* __restrict__ feat, int ldF,
+                                 const double* __restrict__ lnw, int nconf, double sc) {
+    // one warp: lane m < 7 holds column m of the current row and of R's rows
+    const int lane = threadIdx.x;
+    if (lane == 0 && R[55] == 0.0) {
+        for (int q = 0; q < 5; ++q) R[49 + q] = feat[q];
+        R[54] = lnw[0];
+        R[55] = 1.0;
+    }
+    __syncwarp();
+    double Rrow[7];
+    for (int k = 0; k < 7; ++k) Rrow[k] = (lane < 7) ? R[k * 7 + lane] : 0.0;
+    for (int c = 0; c < nconf; ++c) {
+        double a;
+        if (lane == 0) a = 1.0;
+        else if (lane < 6) a = (feat[(size_t)c * ldF + lane - 1] - R[49 + lane - 1]) / sc;
+        else if (lane == 6) a = lnw[c] - R[54];
+        else a = 0.0;
+        for (int k = 0; k < 7; ++k) {
+            const double ak = __shfl_sync(0xffffffffu, a, k);
+            const double rkk = __shfl_sync(0xffffffffu, Rrow[k], k);
+            if (ak == 0.0) continue;
+            const double r = hypot(rkk, ak);
+            const double cs = rkk / r, sn = ak / r;
+            if (lane == k) {
+                Rrow[k] = r;
+                a = 0.0;
+            } else if (lane > k && lane < 7) {
+                const double rk = Rrow[k];
+                Rrow[k] = cs * rk + sn * a;
+                a = -sn * rk + cs * a;
+            }
+        }
+    }
+    for (int k = 0; k < 7; ++k)
+        if (lane < 7) R[k * 7 + lane] = Rrow[k];
+    if (lane == 0) R[56] += nconf;
+}
+
+__global__ void k_fit_finish(const double* __restrict__ R, double dtau, double sc, double* __restrict__ J,
+                             double* __restrict__ resid, unsigned int* __restrict__ err) {
+    if (threadIdx.x != 0) return;
+    double c[6];
+    bool ok = true;
+    for (int k = 5; k >= 0; --k) {
+        double s = R[k * 7 + 6];
+        for (int m = k + 1; m < 6; ++m) s -= R[k * 7 + m] * c[m];
+        if (R[k * 7 + k] == 0.0) ok = false;
+        c[k] = s / R[k * 7 + k];
+    }
+    double icpt = c[0] + R[54];
+    for (int q = 0; q < 5; ++q) icpt -= c[q + 1] * R[49 + q] / sc;
+    J[0] = -icpt / dtau;
+    for (int q = 0; q < 5; ++q) J[q + 1] = -(c[q + 1] / sc) / dtau;
+    if (resid) resid[0] = fabs(R[6 * 7 + 6]) / sqrt(fmax(R[56], 1.0));
+    if (!ok) atomicOr(err, SLMC_EBIT_SINGULAR);
+}
+
+}  // namespace
+
+namespace slmc {
+
+cudaError_t bose_log_weight(slmc_ctx* c, const double* x, int nf, const double* lndet, double* lnw, cudaStream_t s) {
+    k_bose<<<nf, kThreads, 0, s>>>(x, c->N, c->L, c->p.dtau, c->p.lambda, c->p.omega0 * c->p.omega0, lndet, lnw);
+    return cudaGetLastError();
+}
+
+cudaError_t eff_features(slmc_ctx* c, const double* x, int nf, const double* J, double* F, int ldF, double* lnw_eff,
+                         cudaStream_t s) {
+    const double a = c->p.lambda / (c->p.omega0 * c->p.omega0);
+    k_features<<<nf, kThreads, 0, s>>>(x, c->p.Lx, c->p.Ly, c->L, a * a, c->p.dtau, J, F, ldF, lnw_eff);
+    return cudaGetLastError();
+}
+
+cudaError_t eff_half_sweep(slmc_ctx* c, double* x, int nf, int chain0, const double* J, uint64_t sweep, int colour,
+                           const int* colour_per_chain, int colour_xor, long long* n_acc, cudaStream_t s) {
+    const double a = c->p.lambda / (c->p.omega0 * c->p.omega0);
+    const int sites = c->N * (c->L / 2);
+    dim3 grid((sites + kThreads - 1) / kThreads, nf);
+    k_half_sweep<<<grid, kThreads, 0, s>>>(x, c->p.Lx, c->p.Ly, c->L, J, c->p.dtau, a * a, c->p.sweep_delta,
+                                           (uint32_t)(c->p.seed & 0xffffffffu), (uint32_t)(c->p.seed >> 32),
+                                           (uint32_t)sweep, colour, colour_per_chain, colour_xor, chain0,
+                                           reinterpret_cast<unsigned long long*>(n_acc));
+    return cudaGetLastError();
+}
+
+cudaError_t update_draws(slmc_ctx* c, int nf, int chain0, uint64_t update, int* first_colour, double* u_acc,
+                         cudaStream_t s) {
+    k_update_draws<<<(nf + 127) / 128, 128, 0, s>>>(nf, chain0, (uint32_t)update, (uint32_t)(c->p.seed & 0xffffffffu),
+                                                    (uint32_t)(c->p.seed >> 32), first_colour, u_acc);
+    return cudaGetLastError();
+}
+
+cudaError_t accept_update(slmc_ctx* c, int nf, double* x, const double* x_old, const double* lnw_new,
+                          const double* lnweff_old, const double* lnweff_new, const double* u_acc, double* lnw,
+                          int* accepted, long long* n_acc, cudaStream_t s) {
+    k_accept<<<(nf + 127) / 128, 128, 0, s>>>(nf, lnw_new, lnweff_old, lnweff_new, u_acc, lnw, accepted,
+                                              reinterpret_cast<unsigned long long*>(n_acc));
+    const int NL = c->N * c->L;
+    dim3 grid((NL + 255) / 256 < 64 ? (NL + 255) / 256 : 64, nf);
+    k_restore<<<grid, 256, 0, s>>>(x, x_old, accepted, NL);
+    return cudaGetLastError();
+}
+
+cudaError_t cdw_measure(slmc_ctx* c, const double* G, int nf, double* S, const int* only_if, double* obs,
+                        cudaStream_t s) {
+    k_cdw<<<nf, kThreads, 0, s>>>(G, c->p.Lx, c->p.Ly, S, only_if, obs);
+    return cudaGetLastError();
+}
+
+cudaError_t fit_begin(slmc_ctx* c, cudaStream_t s) {
+    k_fit_begin<<<1, 64, 0, s>>>(c->fitR);
+    return cudaGetLastError();
+}
+
+cudaError_t fit_accumulate(slmc_ctx* c, const double* feat, const double* lnw, int nconf, cudaStream_t s) {
+    k_fit_accumulate<<<1, 32, 0, s>>>(c->fitR, feat, 8, lnw, nconf, (double)c->N * c->L);
+    return cudaGetLastError();
+}
+
+cudaError_t fit_finish(slmc_ctx* c, int nconf, double* J_out, double* resid, cudaStream_t s) {
+    (void)nconf;
+    k_fit_finish<<<1, 32, 0, s>>>(c->fitR, c->p.dtau, (double)c->N * c->L, J_out, resid, c->err);
+    return cudaGetLastError();
+}
+
+}  // namespace slmc

@@ -1,0 +1,255 @@
+// Final step of the stabilised determinant [Suppl. Eq. (S2), (S3)], FP64.
+// With B_L ... B_1 = U D T and D = D_b D_s (D_b = max(D, 1), D_s = min(D, 1)):
+//   I + U D T = U D_b M,   M = D_b^-1 U^T + D_s T,
+//   ln|det(I + B_L ... B_1)| = sum ln D_b + ln|det M|,  sign = det(U) sign(det M),
+//   G = (I + B_L ... B_1)^-1 = M^-1 D_b^-1 U^T.
+// M is factored by a right-looking LU with partial pivoting (one CTA per field); G is
+// solved column by column (one warp per column, no block synchronisation).
+#include <cfloat>
+#include <climits>
+
+#include "slmc_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// M (column-major, written over Y) from U (column-major), T (column-major) and lnD.
+__global__ void __launch_bounds__(kThreads) k_assemble_M(const double* __restrict__ Uall, const double* __restrict__ Tall,
+                                                         const double* __restrict__ lnD_all, double* __restrict__ Mall,
+                                                         int N) {
+    const int f = blockIdx.x;
+    const size_t NN = (size_t)N * N;
+    extern __shared__ double sm[];
+    double* sb = sm;      // D_b^-1
+    double* ss = sm + N;  // D_s
+    for (int i = threadIdx.x; i < N; i += kThreads) {
+        const double l = lnD_all[(size_t)f * N + i];
+        sb[i] = exp(-fmax(l, 0.0));
+        ss[i] = exp(fmin(l, 0.0));
+    }
+    __syncthreads();
+    const double* U = Uall + f * NN;
+    const double* T = Tall + f * NN;
+    double* M = Mall + f * NN;
+    for (size_t idx = threadIdx.x; idx < NN; idx += kThreads) {
+        const int j = (int)(idx / N), i = (int)(idx - (size_t)j * N);
+        M[idx] = fma(sb[i], U[(size_t)i * N + j], ss[i] * T[idx]);
+    }
+}
+
+template <int MAXR>
+__global__ void __launch_bounds__(kThreads) k_lu(double* __restrict__ Mall, int* __restrict__ piv_all,
+                                                 const double* __restrict__ lnD_all, const int* __restrict__ sgnU,
+                                                 double* __restrict__ lndet, int* __restrict__ sign,
+                                                 unsigned int* __restrict__ err, int N) {
+    const int f = blockIdx.x;
+    const size_t NN = (size_t)N * N;
+    double* __restrict__ M = Mall + f * NN;
+    extern __shared__ double s_l[];  // [N] multipliers of the current step
+    __shared__ int s_p;
+    __shared__ double s_logabs;
+    __shared__ int s_neg, s_sing;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_logabs = 0.0;
+        s_neg = 0;
+        s_sing = 0;
+    }
+    __syncthreads();
+    for (int k = 0; k < N; ++k) {
+        const int m = N - k;
+        if (warp == 0) {
+            double col[MAXR];
+            double bv = -1.0;
+            int bi = INT_MAX;
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r) {
+                const int ii = lane + 32 * r;
+                col[r] = (ii < m) ? M[(size_t)k * N + k + ii] : 0.0;
+                const double a = fabs(col[r]);
+                if (ii < m && (a > bv || (a == bv && ii < bi))) {
+                    bv = a;
+                    bi = ii;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (bi == INT_MAX) bi = 0;  // NaN column: no swap
+            // pivot value (row k+bi) and the current diagonal element (row k) it swaps with
+            double pval = 0.0;
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r) {
+                const double vb = __shfl_sync(0xffffffffu, col[r], bi & 31);
+                if (r == bi / 32) pval = vb;
+            }
+            const double top = __shfl_sync(0xffffffffu, col[0], 0);
+            const double rinv = (pval != 0.0) ? 1.0 / pval : 0.0;
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r) {
+                const int ii = lane + 32 * r;
+                if (ii >= m) continue;
+                double v = col[r];
+                if (ii == 0) v = pval;
+                else if (ii == bi) v = top;
+                if (ii == 0) {
+                    M[(size_t)k * N + k] = v;
+                } else {
+                    const double l = v * rinv;
+                    s_l[k + ii] = l;
+                    M[(size_t)k * N + k + ii] = l;
+                }
+            }
+            if (lane == 0) {
+                s_p = k + bi;
+                piv_all[(size_t)f * N + k] = k + bi;
+                if (pval == 0.0) s_sing = 1;
+                s_logabs += log(fabs(pval));
+                s_neg ^= (pval < 0.0) ^ (bi != 0);
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        for (int j = warp; j < N; j += kWarps) {
+            if (j == k) continue;
+            double* Mj = M + (size_t)j * N;
+            if (p != k && lane == 0) {
+                const double a = Mj[k];
+                Mj[k] = Mj[p];
+                Mj[p] = a;
+            }
+            if (j < k) continue;
+            __syncwarp();
+            const double u = Mj[k];
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r) {
+                const int ii = lane + 32 * r;
+                if (ii >= 1 && ii < m) Mj[k + ii] = fma(-s_l[k + ii], u, Mj[k + ii]);
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        double ld = s_logabs;
+        for (int i = 0; i < N; ++i) ld += fmax(lnD_all[(size_t)f * N + i], 0.0);
+        const bool ok = !s_sing && isfinite(ld);
+        lndet[f] = ok ? ld : __longlong_as_double(0x7ff8000000000000ll);
+        sign[f] = ok ? (sgnU[f] * (s_neg ? -1 : 1)) : 0;
+        if (s_sing) atomicOr(err, SLMC_EBIT_SINGULAR);
+        else if (!ok) atomicOr(err, SLMC_EBIT_NONFINITE);
+    }
+}
+
+// G[:, j] = M^-1 (D_b^-1 U^T)[:, j] with the LU factors of M; one warp per column, the
+// right-hand side kept in shared memory. Output row-major G[f][i][j].
+template <int MAXR>
+__global__ void __launch_bounds__(256) k_greens(const double* __restrict__ LUall, const int* __restrict__ piv_all,
+                                                const double* __restrict__ Uall, const double* __restrict__ lnD_all,
+                                                double* __restrict__ Gout, int N) {
+    const int f = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = blockIdx.x * 8 + warp;
+    extern __shared__ double sm[];
+    double* b = sm + (size_t)warp * N;
+    if (j >= N) return;
+    const size_t NN = (size_t)N * N;
+    const double* __restrict__ LU = LUall + f * NN;
+    const double* __restrict__ U = Uall + f * NN;
+    const double* __restrict__ lnD = lnD_all + (size_t)f * N;
+    const int* __restrict__ piv = piv_all + (size_t)f * N;
+    for (int i = lane; i < N; i += 32) b[i] = exp(-fmax(lnD[i], 0.0)) * U[(size_t)i * N + j];
+    __syncwarp();
+    if (lane == 0) {
+        for (int k = 0; k < N; ++k) {
+            const int p = piv[k];
+            if (p != k) {
+                const double a = b[k];
+                b[k] = b[p];
+                b[p] = a;
+            }
+        }
+    }
+    __syncwarp();
+    for (int k = 0; k < N - 1; ++k) {  // unit lower triangle
+        const double yk = b[k];
+        const double* __restrict__ col = LU + (size_t)k * N;
+#pragma unroll
+        for (int r = 0; r < MAXR; ++r) {
+            const int i = lane + 32 * r;
+            if (i > k && i < N) b[i] = fma(-col[i], yk, b[i]);
+        }
+        __syncwarp();
+    }
+    for (int k = N - 1; k >= 0; --k) {  // upper triangle
+        const double* __restrict__ col = LU + (size_t)k * N;
+        const double gk = b[k] / col[k];
+        __syncwarp();
+        if (lane == 0) b[k] = gk;
+#pragma unroll
+        for (int r = 0; r < MAXR; ++r) {
+            const int i = lane + 32 * r;
+            if (i < k) b[i] = fma(-col[i], gk, b[i]);
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < N; i += 32) Gout[f * NN + (size_t)i * N + j] = b[i];
+}
+
+template <int MAXR>
+cudaError_t launch_final(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s) {
+    const int N = c->N;
+    k_assemble_M<<<nf, kThreads, 2 * N * sizeof(double), s>>>(c->U, c->Ta, c->lnD, c->Y, N);
+    k_lu<MAXR><<<nf, kThreads, N * sizeof(double), s>>>(c->Y, c->piv, c->lnD, c->sgnU, lndet, sign, c->err, N);
+    return cudaGetLastError();
+}
+
+template <int MAXR>
+cudaError_t launch_greens(slmc_ctx* c, int nf, double* G, cudaStream_t s) {
+    const int N = c->N;
+    const size_t smem = (size_t)8 * N * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_greens<MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + 7) / 8, nf);
+    k_greens<MAXR><<<grid, 256, smem, s>>>(c->Y, c->piv, c->U, c->lnD, G, N);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace slmc {
+
+cudaError_t final_logdet(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s) {
+    switch (rows_per_lane_class(c->N)) {
+        case 1: return launch_final<1>(c, nf, lndet, sign, s);
+        case 2: return launch_final<2>(c, nf, lndet, sign, s);
+        case 4: return launch_final<4>(c, nf, lndet, sign, s);
+        case 5: return launch_final<5>(c, nf, lndet, sign, s);
+        case 8: return launch_final<8>(c, nf, lndet, sign, s);
+        case 12: return launch_final<12>(c, nf, lndet, sign, s);
+        case 18: return launch_final<18>(c, nf, lndet, sign, s);
+        default: return launch_final<32>(c, nf, lndet, sign, s);
+    }
+}
+
+cudaError_t final_greens(slmc_ctx* c, int nf, double* G, cudaStream_t s) {
+    switch (rows_per_lane_class(c->N)) {
+        case 1: return launch_greens<1>(c, nf, G, s);
+        case 2: return launch_greens<2>(c, nf, G, s);
+        case 4: return launch_greens<4>(c, nf, G, s);
+        case 5: return launch_greens<5>(c, nf, G, s);
+        case 8: return launch_greens<8>(c, nf, G, s);
+        case 12: return launch_greens<12>(c, nf, G, s);
+        case 18: return launch_greens<18>(c, nf, G, s);
+        default: return launch_greens<32>(c, nf, G, s);
+    }
+}
+
+}  // namespace slmc

@@ -1,0 +1,170 @@
+// SIMT panel kernels of the slice-group product and of the T update.
+//
+// Slice group [Suppl. Eq. (S2)]: for one stabilisation group of nsl slices starting at l0,
+//   Y = B_{l0+nsl} ... B_{l0+1} U,   B_l = diag(exp(-dtau lambda x[:, l-1])) E.
+// Left multiplication acts on every column of U independently, so one CTA owns a panel
+// of NB columns of one field, keeps it in shared memory across all nsl slices and streams
+// E (symmetric, L2-resident) once per slice; the diagonal phonon scaling of each slice is
+// applied in the epilogue before the panel is reused. Only U is read from and Y written to
+// global memory, once per group.
+//
+// T update (UDT stabilisation): T_new = Rt P^T T_old with Rt the scaled upper triangle of the
+// pivoted QR (column-major, strictly-lower part holds Householder vectors and is skipped)
+// and (P^T T_old)[k, :] = T_old[perm[k], :]. Same panel kernel with a per-field triangular A.
+//
+// Layout: every N x N matrix is column-major, element (i, j) at j*N + i.
+#include "slmc_internal.cuh"
+
+namespace {
+
+constexpr int kWarps = 8;
+
+template <typename T>
+__device__ __forceinline__ T slice_scale(double xv, double dtlam);
+template <>
+__device__ __forceinline__ double slice_scale<double>(double xv, double dtlam) { return exp(-dtlam * xv); }
+template <>
+__device__ __forceinline__ float slice_scale<float>(double xv, double dtlam) {
+    return expf(-(float)dtlam * (float)xv);
+}
+
+template <typename T, int MAXR, int CPT, bool TRI>
+__global__ void __launch_bounds__(256) k_panel(const T* __restrict__ A, size_t a_stride,
+                                               const double* __restrict__ B, const int* __restrict__ perm,
+                                               double* __restrict__ out, const double* __restrict__ x,
+                                               int N, int L, int l0, int nsl, double dtlam) {
+    constexpr int NB = kWarps * CPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* P0 = reinterpret_cast<T*>(smem_raw);
+    T* P1 = P0 + (size_t)NB * N;
+    T* sc = P1 + (size_t)NB * N;
+    const int f = blockIdx.y, j0 = blockIdx.x * NB;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t NN = (size_t)N * N;
+    const T* Af = A + (size_t)f * a_stride;
+    const double* Bf = B + (size_t)f * NN;
+    const int* pf = perm ? perm + (size_t)f * N : nullptr;
+
+    for (int idx = tid; idx < NB * N; idx += 256) {
+        const int jj = idx / N, k = idx - jj * N, j = j0 + jj;
+        T v = T(0);
+        if (j < N) v = (T)Bf[(size_t)j * N + (pf ? pf[k] : k)];
+        P0[idx] = v;
+    }
+    T* Pin = P0;
+    T* Pout = P1;
+    for (int s = 0; s < nsl; ++s) {
+        if (x) {
+            const double* xf = x + (size_t)f * N * L + l0 + s;
+            for (int i = tid; i < N; i += 256) sc[i] = slice_scale<T>(xf[(size_t)i * L], dtlam);
+        }
+        __syncthreads();
+        T acc[MAXR][CPT];
+#pragma unroll
+        for (int r = 0; r < MAXR; ++r)
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) acc[r][c] = T(0);
+        for (int k = 0; k < N; ++k) {
+            T pv[CPT];
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) pv[c] = Pin[(warp + kWarps * c) * N + k];
+            const T* Ak = Af + (size_t)k * N;
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r) {
+                if (TRI && 32 * r > k) continue;  // rows below the diagonal of Rt
+                const int i = lane + 32 * r;
+                const T a = (i < N && (!TRI || i <= k)) ? __ldg(Ak + i) : T(0);
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) acc[r][c] = fma(a, pv[c], acc[r][c]);
+            }
+        }
+        const bool last = (s == nsl - 1);
+#pragma unroll
+        for (int r = 0; r < MAXR; ++r) {
+            const int i = lane + 32 * r;
+            if (i >= N) continue;
+            const T si = x ? sc[i] : T(1);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int jj = warp + kWarps * c;
+                const T v = acc[r][c] * si;
+                if (last) {
+                    if (j0 + jj < N) out[(size_t)f * NN + (size_t)(j0 + jj) * N + i] = (double)v;
+                } else {
+                    Pout[jj * N + i] = v;
+                }
+            }
+        }
+        T* tmp = Pin;
+        Pin = Pout;
+        Pout = tmp;
+        __syncthreads();
+    }
+}
+
+template <typename T, int MAXR, int CPT, bool TRI>
+cudaError_t launch_panel(const T* A, size_t a_stride, const double* B, const int* perm, double* out,
+                         const double* x, int N, int L, int l0, int nsl, double dtlam, int nf, cudaStream_t s) {
+    constexpr int NB = kWarps * CPT;
+    const size_t smem = (size_t)(2 * NB * N + N) * sizeof(T);
+    auto kern = k_panel<T, MAXR, CPT, TRI>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + NB - 1) / NB, nf);
+    kern<<<grid, 256, smem, s>>>(A, a_stride, B, perm, out, x, N, L, l0, nsl, dtlam);
+    return cudaGetLastError();
+}
+
+template <typename T, bool TRI>
+cudaError_t dispatch_panel(const T* A, size_t a_stride, const double* B, const int* perm, double* out,
+                           const double* x, int N, int L, int l0, int nsl, double dtlam, int nf, cudaStream_t s) {
+    switch (slmc::rows_per_lane_class(N)) {
+        case 1: return launch_panel<T, 1, 4, TRI>(A, a_stride, B, perm, out, x, N, L, l0, nsl, dtlam, nf, s);
+        case 2: return launch_panel<T, 2, 4, TRI>(A, a_stride, B, perm, out, x, N, L, l0, nsl, dtlam, nf, s);
+        case 4: return launch_panel<T, 4, 4, TRI>(A, a_stride, B, perm, out, x, N, L, l0, nsl, dtlam, nf, s);
+        case 5: return launch_panel<T, 5, 4, TRI>(A, a_stride, B, perm, out, x, N, L, l0, nsl, dtlam, nf, s);
+        case 8: return launch_panel<T, 8, 4, TRI>(A, a_stride, B, perm, out, x, N, L, l0, nsl, dtlam, nf, s);
+        case 12: return launch_panel<T, 12, 2, TRI>(A, a_stride, B, perm, out, x, N, L, l0, nsl, dtlam, nf, s);
+        case 18: return launch_panel<T, 18, 1, TRI>(A, a_stride, B, perm, out, x, N, L, l0, nsl, dtlam, nf, s);
+        default: return launch_panel<T, 32, 1, TRI>(A, a_stride, B, perm, out, x, N, L, l0, nsl, dtlam, nf, s);
+    }
+}
+
+__global__ void k_identity(double* __restrict__ U, double* __restrict__ T, double* __restrict__ lnD, int N) {
+    const int f = blockIdx.y;
+    const size_t NN = (size_t)N * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+        const double v = (idx % (N + 1) == 0) ? 1.0 : 0.0;
+        U[(size_t)f * NN + idx] = v;
+        T[(size_t)f * NN + idx] = v;
+        if (idx < (size_t)N) lnD[(size_t)f * N + idx] = 0.0;
+    }
+}
+
+}  // namespace
+
+namespace slmc {
+
+cudaError_t slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s) {
+    const double dtlam = c->p.dtau * c->p.lambda;
+    if (c->p.precision == SLMC_PREC_FP32)
+        return dispatch_panel<float, false>(c->E32, 0, c->U, nullptr, c->Y, x, c->N, c->L, l0, nsl, dtlam, nf, s);
+    return dispatch_panel<double, false>(c->E64, 0, c->U, nullptr, c->Y, x, c->N, c->L, l0, nsl, dtlam, nf, s);
+}
+
+cudaError_t t_update(slmc_ctx* c, int nf, cudaStream_t s) {
+    const size_t NN = (size_t)c->N * c->N;
+    cudaError_t e = dispatch_panel<double, true>(c->QR, NN, c->Ta, c->perm, c->Tb, nullptr, c->N, c->L, 0, 1, 0.0, nf, s);
+    double* t = c->Ta;
+    c->Ta = c->Tb;
+    c->Tb = t;
+    return e;
+}
+
+cudaError_t set_identity(slmc_ctx* c, int nf, cudaStream_t s) {
+    dim3 grid(64, nf);
+    k_identity<<<grid, 256, 0, s>>>(c->U, c->Ta, c->lnD, c->N);
+    return cudaGetLastError();
+}
+
+}  // namespace slmc

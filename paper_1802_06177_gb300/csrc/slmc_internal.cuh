@@ -1,0 +1,117 @@
+// Internal declarations shared by the libslmc translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/slmc.h"
+
+// Device-side sticky error bits (ctx->err).
+#define SLMC_EBIT_NONFINITE 1u
+#define SLMC_EBIT_SINGULAR 2u
+
+#define SLMC_MAX_N 1024
+
+struct slmc_ctx {
+    slmc_params p;
+    int N, L, max_fields, device;
+    // exp(-dtau K), built on the device from the plane-wave eigenbasis of K.
+    double* E64;
+    float* E32;
+    // tensor-core operand splits of E (filled only in the matching precision modes)
+    uint32_t* Etf;   // [2][N][N] TF32 hi / lo bit patterns
+    uint16_t* Ebf;   // [3][N][N] BF16 three-way split
+    // Per-field workspace, [max_fields][N][N] column-major unless stated.
+    double* Y;       // slice-group product; reused for M in the final step
+    double* QR;      // packed pivoted-QR output; reused for G in the cumulative update
+    double* U;       // orthogonal factor
+    double* Ta;      // T factor (ping)
+    double* Tb;      // T factor (pong)
+    double* lnD;     // [max_fields][N] ln of the D scales
+    double* tau;     // [max_fields][N] Householder coefficients
+    int* perm;       // [max_fields][N] column permutation of the last QR
+    int* piv;        // [max_fields][N] LU row pivots
+    int* sgnU;       // [max_fields] det(U) = +-1
+    // Chain workspace.
+    double* x_old;   // [max_fields][N][L]
+    double* scal;    // [max_fields][8] scratch scalars per chain
+    int* iscal;      // [max_fields][4] scratch ints per chain
+    // Regression workspace.
+    double* feat;    // [max_fields][8]
+    double* fitR;    // [64] Givens-QR state of the regression
+    unsigned int* err;
+};
+
+namespace slmc {
+
+// ---- launch helpers ---------------------------------------------------------------
+inline int rows_per_lane_class(int N) {
+    const int r = (N + 31) / 32;
+    if (r <= 1) return 1;
+    if (r <= 2) return 2;
+    if (r <= 4) return 4;
+    if (r <= 5) return 5;
+    if (r <= 8) return 8;
+    if (r <= 12) return 12;
+    if (r <= 18) return 18;
+    return 32;
+}
+
+// ---- Philox-4x32-10 (Salmon et al., SC'11), written from the published definition ----
+struct u32x4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = u32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    }
+    return c;
+}
+
+// 53-bit uniform double in [0, 1) from two words (top 27 bits of hi, top 26 of lo).
+__device__ __forceinline__ double uniform53(uint32_t hi, uint32_t lo) {
+    return ((double)(hi >> 5) * 67108864.0 + (double)(lo >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+// ---- warp reductions ----------------------------------------------------------------
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace slmc
+
+// ---- kernel launchers (defined in the .cu files) ---------------------------------------
+namespace slmc {
+cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s);
+cudaError_t slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s);
+cudaError_t tc_slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s);
+cudaError_t t_update(slmc_ctx* c, int nf, cudaStream_t s);
+cudaError_t qr_pivoted(slmc_ctx* c, int nf, cudaStream_t s);
+cudaError_t form_q(slmc_ctx* c, int nf, cudaStream_t s);
+cudaError_t set_identity(slmc_ctx* c, int nf, cudaStream_t s);
+cudaError_t final_logdet(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s);
+cudaError_t final_greens(slmc_ctx* c, int nf, double* G, cudaStream_t s);
+cudaError_t bose_log_weight(slmc_ctx* c, const double* x, int nf, const double* lndet, double* lnw,
+                            cudaStream_t s);
+cudaError_t eff_features(slmc_ctx* c, const double* x, int nf, const double* J, double* F, int ldF,
+                         double* lnw_eff, cudaStream_t s);
+cudaError_t eff_half_sweep(slmc_ctx* c, double* x, int nf, int chain0, const double* J, uint64_t sweep,
+                           int colour, const int* colour_per_chain, int colour_xor, long long* n_acc,
+                           cudaStream_t s);
+cudaError_t update_draws(slmc_ctx* c, int nf, int chain0, uint64_t update, int* first_colour, double* u_acc,
+                         cudaStream_t s);
+cudaError_t accept_update(slmc_ctx* c, int nf, double* x, const double* x_old, const double* lnw_new,
+                          const double* lnweff_old, const double* lnweff_new, const double* u_acc,
+                          double* lnw, int* accepted, long long* n_acc, cudaStream_t s);
+cudaError_t cdw_measure(slmc_ctx* c, const double* G, int nf, double* S, const int* only_if,
+                        double* obs, cudaStream_t s);
+cudaError_t fit_begin(slmc_ctx* c, cudaStream_t s);
+cudaError_t fit_accumulate(slmc_ctx* c, const double* feat, const double* lnw, int nconf,
+                           cudaStream_t s);
+cudaError_t fit_finish(slmc_ctx* c, int nconf, double* J_out, double* resid, cudaStream_t s);
+}  // namespace slmc

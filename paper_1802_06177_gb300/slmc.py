@@ -1,0 +1,220 @@
+"""Thin ctypes binding of libslmc (include/slmc.h). Argument marshalling only: every step
+of the computation runs in the library's CUDA kernels. Arrays are torch CUDA tensors;
+torch provides device memory and the current stream. There is no CPU fallback: if the
+library is missing or fails to load, every call raises."""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libslmc.so")
+
+PRECISION = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x9": 3}
+STATUS = {0: "ok", 1: "invalid argument", 2: "non-finite input or result", 3: "CUDA runtime error",
+          4: "bounded device wait timed out", 5: "unsupported shape or mode", 6: "out of device memory",
+          7: "singular matrix"}
+
+
+class SlmcError(RuntimeError):
+    def __init__(self, fn, status):
+        super().__init__("%s failed: %s (status %d)" % (fn, STATUS.get(status, "unknown"), status))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("L", ctypes.c_int), ("dtau", ctypes.c_double),
+                ("t", ctypes.c_double), ("mu", ctypes.c_double), ("omega0", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("n_s", ctypes.c_int), ("precision", ctypes.c_int),
+                ("sweep_delta", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", "slmc_logdet", "slmc_greens",
+           "slmc_log_weight", "slmc_eff_features", "slmc_eff_log_weight", "slmc_eff_sweep", "slmc_chain_init",
+           "slmc_cumulative_update", "slmc_fit_eff", "slmc_measure_cdw")
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Loads libslmc.so and declares the argument types of every entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libslmc.so not found at %s: build it with `python -c \"import __graft_entry__ as g; "
+                           "g.build()\"` (there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    P, I, D, U64, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p
+    sig = {
+        "slmc_status_string": ([I], ctypes.c_char_p),
+        "slmc_init": ([ctypes.POINTER(Params), I, ctypes.POINTER(P)], I),
+        "slmc_destroy": ([P], I),
+        "slmc_get_error": ([P, V], I),
+        "slmc_logdet": ([P, P, I, P, P, V], I),
+        "slmc_greens": ([P, P, I, P, P, P, V], I),
+        "slmc_log_weight": ([P, P, I, P, P, P, V], I),
+        "slmc_eff_features": ([P, P, I, P, V], I),
+        "slmc_eff_log_weight": ([P, P, I, P, P, V], I),
+        "slmc_eff_sweep": ([P, P, I, P, I, U64, I, P, V], I),
+        "slmc_chain_init": ([P, P, I, P, P, V], I),
+        "slmc_cumulative_update": ([P, P, I, P, I, I, U64, P, P, P, P, P, V], I),
+        "slmc_fit_eff": ([P, P, P, I, P, P, V], I),
+        "slmc_measure_cdw": ([P, P, I, P, V], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t, dtype, name, shape=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    return t.data_ptr()
+
+
+def _stream(device):
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class Context:
+    """One libslmc context (model parameters, exp(-dtau K), workspace) on one CUDA device."""
+
+    def __init__(self, Lx, Ly, L, dtau=0.1, t=1.0, mu=0.0, omega0=1.0, lam=1.0, n_s=10, precision="fp64",
+                 sweep_delta=0.5, seed=0, max_fields=64, device=None):
+        self.lib = load_library()
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.device = torch.device("cuda", torch.cuda.current_device() if dev.index is None else dev.index)
+        self.Lx, self.Ly, self.L = Lx, Ly, L
+        self.N = Lx * Ly
+        self.dtau, self.lam, self.omega0, self.n_s = dtau, lam, omega0, n_s
+        self.precision = precision
+        self.params = Params(Lx, Ly, L, dtau, t, mu, omega0, lam, n_s, PRECISION[precision], sweep_delta,
+                             seed & ((1 << 64) - 1))
+        self._ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self._check("slmc_init", self.lib.slmc_init(ctypes.byref(self.params), max_fields,
+                                                        ctypes.byref(self._ctx)))
+
+    # -- helpers -----------------------------------------------------------------------
+    def _check(self, fn, status):
+        if status != 0:
+            raise SlmcError(fn, status)
+
+    def _fields(self, x, name="x"):
+        if x.dim() != 3 or x.shape[1] != self.N or x.shape[2] != self.L:
+            raise ValueError("%s must have shape [n, %d, %d]" % (name, self.N, self.L))
+        return _ptr(x, torch.float64, name), x.shape[0]
+
+    def _empty(self, shape, dtype=torch.float64):
+        return torch.empty(shape, dtype=dtype, device=self.device)
+
+    def close(self):
+        if self._ctx:
+            self.lib.slmc_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_error(self):
+        """Synchronises the current stream and raises if a kernel flagged an error."""
+        self._check("slmc_get_error", self.lib.slmc_get_error(self._ctx, _stream(self.device)))
+
+    # -- entry points ------------------------------------------------------------------
+    def logdet(self, x, lndet=None, sign=None):
+        px, n = self._fields(x)
+        lndet = self._empty(n) if lndet is None else lndet
+        sign = self._empty(n, torch.int32) if sign is None else sign
+        self._check("slmc_logdet", self.lib.slmc_logdet(self._ctx, px, n, _ptr(lndet, torch.float64, "lndet", (n,)),
+                                                        _ptr(sign, torch.int32, "sign", (n,)), _stream(self.device)))
+        return lndet, sign
+
+    def greens(self, x, G=None, lndet=None, sign=None):
+        px, n = self._fields(x)
+        G = self._empty((n, self.N, self.N)) if G is None else G
+        lndet = self._empty(n) if lndet is None else lndet
+        sign = self._empty(n, torch.int32) if sign is None else sign
+        self._check("slmc_greens", self.lib.slmc_greens(
+            self._ctx, px, n, _ptr(G, torch.float64, "G", (n, self.N, self.N)),
+            _ptr(lndet, torch.float64, "lndet", (n,)), _ptr(sign, torch.int32, "sign", (n,)), _stream(self.device)))
+        return G, lndet, sign
+
+    def log_weight(self, x):
+        px, n = self._fields(x)
+        lnw, lndet, sign = self._empty(n), self._empty(n), self._empty(n, torch.int32)
+        self._check("slmc_log_weight", self.lib.slmc_log_weight(self._ctx, px, n, _ptr(lnw, torch.float64, "lnw"),
+                                                                _ptr(lndet, torch.float64, "lndet"),
+                                                                _ptr(sign, torch.int32, "sign"), _stream(self.device)))
+        return lnw, lndet, sign
+
+    def eff_features(self, x):
+        px, n = self._fields(x)
+        F = self._empty((n, 5))
+        self._check("slmc_eff_features", self.lib.slmc_eff_features(self._ctx, px, n, _ptr(F, torch.float64, "F"),
+                                                                    _stream(self.device)))
+        return F
+
+    def eff_log_weight(self, x, J):
+        px, n = self._fields(x)
+        out = self._empty(n)
+        self._check("slmc_eff_log_weight", self.lib.slmc_eff_log_weight(
+            self._ctx, px, n, _ptr(J, torch.float64, "J", (6,)), _ptr(out, torch.float64, "out"), _stream(self.device)))
+        return out
+
+    def eff_sweep(self, x, J, nsweeps, sweep0=0, first_colour=0, n_acc=None):
+        px, n = self._fields(x)
+        self._check("slmc_eff_sweep", self.lib.slmc_eff_sweep(
+            self._ctx, px, n, _ptr(J, torch.float64, "J", (6,)), nsweeps, sweep0, first_colour,
+            _ptr(n_acc, torch.int64, "n_acc", (n,)), _stream(self.device)))
+        return x
+
+    def chain_init(self, x, want_cdw=True):
+        px, n = self._fields(x)
+        lnw = self._empty(n)
+        s = self._empty(n) if want_cdw else None
+        self._check("slmc_chain_init", self.lib.slmc_chain_init(self._ctx, px, n, _ptr(lnw, torch.float64, "lnw"),
+                                                                _ptr(s, torch.float64, "s_cdw"), _stream(self.device)))
+        return lnw, s
+
+    def cumulative_update(self, x, J, nsweeps, nupdates, update0, lnw, s_cdw=None, n_acc=None, n_sweep_acc=None,
+                          want_obs=False):
+        px, n = self._fields(x)
+        obs = self._empty((nupdates, n)) if want_obs else None
+        self._check("slmc_cumulative_update", self.lib.slmc_cumulative_update(
+            self._ctx, px, n, _ptr(J, torch.float64, "J", (6,)), nsweeps, nupdates, update0,
+            _ptr(lnw, torch.float64, "lnw", (n,)), _ptr(s_cdw, torch.float64, "s_cdw", (n,)),
+            _ptr(n_acc, torch.int64, "n_acc", (n,)), _ptr(n_sweep_acc, torch.int64, "n_sweep_acc", (n,)),
+            _ptr(obs, torch.float64, "obs"), _stream(self.device)))
+        return obs
+
+    def fit_eff(self, xs, lnw):
+        px, n = self._fields(xs, "xs")
+        J = self._empty(6)
+        resid = self._empty(1)
+        self._check("slmc_fit_eff", self.lib.slmc_fit_eff(self._ctx, px, _ptr(lnw, torch.float64, "lnw", (n,)), n,
+                                                          _ptr(J, torch.float64, "J"), _ptr(resid, torch.float64, "r"),
+                                                          _stream(self.device)))
+        return J, resid
+
+    def measure_cdw(self, G):
+        n = G.shape[0]
+        S = self._empty(n)
+        self._check("slmc_measure_cdw", self.lib.slmc_measure_cdw(
+            self._ctx, _ptr(G, torch.float64, "G", (n, self.N, self.N)), n, _ptr(S, torch.float64, "S"),
+            _stream(self.device)))
+        return S

@@ -1,0 +1,165 @@
+"""Parity of the CUDA determinant path (slmc_logdet / slmc_greens / slmc_log_weight,
+called through the C ABI) with the FP64 oracle, element by element on the same seeded
+fields. Bar: |d ln det| <= 1e-8 and |d G| <= 1e-9 in FP64 mode."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import HolsteinParams
+from oracle.fermion import fermion_logdet
+from oracle.lattice import dispersion, exp_hopping, staggered_sign
+from oracle.weight import log_weight
+from paper_1802_06177_gb300 import inputs
+from tests.gpu_util import cuda, make_ctx
+
+pytestmark = pytest.mark.gpu
+
+TOL_LNDET_FP64 = 1e-8
+TOL_G_FP64 = 1e-9
+
+
+def oracle_many(p, x, want_G=True):
+    E = exp_hopping(p.Lx, p.Ly, p.t, p.mu, p.dtau)
+    out = [fermion_logdet(p, xf, E=E, want_G=want_G) for xf in x]
+    return (np.array([o[0] for o in out]), np.array([o[1] for o in out]),
+            np.array([o[2] for o in out]) if want_G else None)
+
+
+@pytest.mark.parametrize("Lx,Ly,L,n_s,nf,kind", [
+    (4, 4, 40, 10, 64, "gaussian"),       # small workload, all 64 fields
+    (6, 4, 37, 8, 12, "gaussian"),        # Lx != Ly, ragged last group
+    (10, 10, 30, 7, 6, "mixed"),          # N = 100: ragged rows per lane
+    (12, 12, 120, 10, 6, "mixed"),        # 12x12 workload shape, sampled fields
+    (2, 2, 5, 10, 3, "gaussian"),         # L < n_s: one short group
+    (4, 4, 16, 1, 4, "gaussian"),         # QR after every slice
+])
+def test_logdet_and_greens_fp64(Lx, Ly, L, n_s, nf, kind):
+    seed = 1000 + Lx * 100 + L
+    x = (inputs.gaussian_fields(nf, Lx, Ly, L, seed=seed) if kind == "gaussian"
+         else inputs.mixed_fields(nf, Lx, Ly, L, seed=seed))
+    ctx = make_ctx(Lx, L, n_s, Ly=Ly, max_fields=64)
+    G, lndet, sign = ctx.greens(cuda(x))
+    lndet2, sign2 = ctx.logdet(cuda(x))
+    torch.cuda.synchronize()
+    ctx.get_error()
+    p = HolsteinParams(Lx, Ly, L, n_s=n_s)
+    l_ref, s_ref, G_ref = oracle_many(p, x)
+    assert np.abs(lndet.cpu().numpy() - l_ref).max() <= TOL_LNDET_FP64
+    assert np.array_equal(sign.cpu().numpy(), s_ref)
+    assert np.abs(G.cpu().numpy() - G_ref).max() <= TOL_G_FP64
+    assert np.array_equal(lndet.cpu().numpy(), lndet2.cpu().numpy())
+    assert np.array_equal(sign2.cpu().numpy(), s_ref)
+
+
+def test_batches_larger_than_workspace():
+    x = inputs.gaussian_fields(11, 4, 4, 20, seed=5)
+    ctx = make_ctx(4, 20, 5, max_fields=4)  # 3 internal batches, last one ragged
+    lndet, sign = ctx.logdet(cuda(x))
+    l_ref, s_ref, _ = oracle_many(HolsteinParams(4, 4, 20, n_s=5), x, want_G=False)
+    assert np.abs(lndet.cpu().numpy() - l_ref).max() <= TOL_LNDET_FP64
+    assert np.array_equal(sign.cpu().numpy(), s_ref)
+
+
+def test_empty_batch_is_noop():
+    ctx = make_ctx(4, 10, 5)
+    lndet, sign = ctx.logdet(torch.empty((0, 16, 10), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    assert lndet.numel() == 0
+
+
+def test_negative_determinants_match_sign():
+    # large dtau and strong fields give negative single-species determinants
+    from oracle.fermion import block_matrix
+    rng = np.random.default_rng(11)
+    x = 3.0 * rng.standard_normal((64, 4, 6))
+    ctx = make_ctx(2, 6, 1, dtau=1.0)
+    lndet, sign = ctx.logdet(cuda(x))
+    p = HolsteinParams(2, 2, 6, dtau=1.0, n_s=1)
+    E = exp_hopping(2, 2, 1.0, 0.0, 1.0)
+    ref = [np.linalg.slogdet(block_matrix(E, xf, 1.0, 1.0)) for xf in x]
+    s_ref = np.array([int(r[0]) for r in ref])
+    assert (s_ref < 0).any()
+    assert np.array_equal(sign.cpu().numpy(), s_ref)
+    assert np.abs(lndet.cpu().numpy() - np.array([r[1] for r in ref])).max() < 1e-7
+
+
+def test_closed_forms_on_gpu():
+    # lambda = 0 and the static staggered field at the 16x16, L=160 shape
+    Lx, L = 16, 160
+    eps, _, _ = dispersion(Lx, Lx, 1.0, 0.0)
+    ctx0 = make_ctx(Lx, L, 8, lam=0.0, max_fields=2)
+    l0, s0 = ctx0.logdet(torch.zeros((1, Lx * Lx, L), dtype=torch.float64, device="cuda"))
+    ref0 = np.sum(np.log1p(np.exp(-16.0 * eps)))
+    assert abs(l0.item() - ref0) <= TOL_LNDET_FP64 and s0.item() == 1
+    m = 0.8
+    xs = np.repeat((m * staggered_sign(Lx, Lx))[:, None], L, axis=1)[None]
+    ctx = make_ctx(Lx, L, 8, max_fields=2)
+    ls, ss = ctx.logdet(cuda(xs))
+    theta = np.arccosh(np.cosh(0.1 * m) * np.cosh(0.1 * eps))
+    refs = np.sum(np.log(2 * np.cosh(L * theta / 2)))
+    assert abs(ls.item() - refs) <= TOL_LNDET_FP64 and ss.item() == 1
+
+
+def test_atomic_limit_on_gpu():
+    x = inputs.gaussian_fields(3, 4, 4, 30, seed=3)
+    ctx = make_ctx(4, 30, 7, t=0.0)
+    G, lndet, _ = ctx.greens(cuda(x))
+    ref = np.sum(np.log1p(np.exp(-0.1 * x.sum(axis=2))), axis=1)
+    assert np.abs(lndet.cpu().numpy() - ref).max() <= TOL_LNDET_FP64
+    Gd = 1.0 / (1.0 + np.exp(-0.1 * x.sum(axis=2)))
+    assert np.abs(G.cpu().numpy() - np.stack([np.diag(g) for g in Gd])).max() <= TOL_G_FP64
+
+
+def test_log_weight_fp64():
+    x = inputs.mixed_fields(6, 6, 6, 24, seed=9)
+    ctx = make_ctx(6, 24, 6, lam=1.0, omega0=1.0)
+    lnw, lndet, sign = ctx.log_weight(cuda(x))
+    p = HolsteinParams(6, 6, 24, n_s=6)
+    ref = np.array([log_weight(p, xf)[0] for xf in x])
+    assert np.abs(lnw.cpu().numpy() - ref).max() <= 2 * TOL_LNDET_FP64 + 1e-10 * np.abs(ref).max()
+    # even in x (particle-hole symmetry of the full weight)
+    lnw_m, _, _ = ctx.log_weight(cuda(-x))
+    assert np.abs(lnw.cpu().numpy() - lnw_m.cpu().numpy()).max() < 1e-8
+
+
+def test_full_size_16x16_L160_sampled():
+    # The 16x16, beta=16 workload in the launch configuration the benchmark uses (many
+    # fields per batch); the oracle checks a sample of them one by one.
+    nf = 64
+    x = inputs.mixed_fields(nf, 16, 16, 160, seed=0x1802061772)
+    ctx = make_ctx(16, 160, 8, max_fields=nf)
+    lndet, sign = ctx.logdet(cuda(x))
+    torch.cuda.synchronize()
+    ctx.get_error()
+    p = HolsteinParams(16, 16, 160, n_s=8)
+    E = exp_hopping(16, 16, 1.0, 0.0, 0.1)
+    for f in (0, 17, nf // 2, nf - 1):
+        l_ref, s_ref, _ = fermion_logdet(p, x[f], E=E, want_G=False)
+        assert abs(lndet[f].item() - l_ref) <= TOL_LNDET_FP64
+        assert sign[f].item() == s_ref
+
+
+def test_fp32_slices_error_budget():
+    # FP32 slice products (FP64 QR / LU): error reported against the FP64 oracle; the
+    # bound here is only a sanity envelope, the measured error is recorded by the bench.
+    x = inputs.mixed_fields(8, 12, 12, 120, seed=21)
+    ctx = make_ctx(12, 120, 10, precision="fp32", max_fields=8)
+    lndet, sign = ctx.logdet(cuda(x))
+    l_ref, s_ref, _ = oracle_many(HolsteinParams(12, 12, 120, n_s=10), x, want_G=False)
+    err = np.abs(lndet.cpu().numpy() - l_ref).max()
+    assert err < 1e-2, err
+    assert np.array_equal(sign.cpu().numpy(), s_ref)
+
+
+def test_nonfinite_field_is_reported():
+    from paper_1802_06177_gb300.slmc import SlmcError
+    x = inputs.gaussian_fields(2, 4, 4, 10, seed=1)
+    x[1, 3, 4] = np.nan
+    ctx = make_ctx(4, 10, 5)
+    lndet, sign = ctx.logdet(cuda(x))
+    with pytest.raises(SlmcError) as e:
+        ctx.get_error()
+    assert e.value.status == 2
+    assert np.isnan(lndet[1].item()) and sign[1].item() == 0
+    assert np.isfinite(lndet[0].item()) and sign[0].item() == 1
+    ctx.get_error()  # cleared
