@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark of the stabilised fermion log-weight ln det(I + B_L ... B_1) on one or more
+GB300 GPUs (one process per GPU; chains are independent, so N GPUs run N independent
+batches: weak scaling, no collective on the data path).
+
+Workload (default): 16x16 periodic lattice (N = 256), beta = 16 (L = 160 slices,
+dtau = 0.1), stabilisation every n_s = 8 slices, t = 1, mu = 0, omega0 = 1, lambda = 1;
+512 seeded synthetic fields per GPU, half iid N(0, 1) and half the CDW pattern
+0.8 (-1)^(ix+iy) + N(0, 0.3^2). The fields (168 MB) and the workspace (1.5 GB) are larger
+than L2, so no explicit flush is needed between steps.
+
+One step = one pass of the whole hot path over the batch: a cumulative update of every
+chain (effective-model checkerboard sweeps, E_eff, exact ln w with the stabilised
+determinant and G, the Eq. (6) acceptance, S(pi,pi)) followed by the regression of E_eff
+on the batch. value = ln det evaluations per second = chains / step time, in the mixed
+precision mode (slice products in --precision, FP64 QR / D scales / LU / log-ratio).
+
+--impl reference times the CPU oracle (plain FP64 numpy) on the host cores instead.
+"""
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "stabilised ln det(I+B_L...B_1) evals/s, mixed vs FP64 on one GB300, % of peak"
+UNIT = "evals/s"
+
+# Roofline denominators. HBM and BF16 come from MEASURED_PEAKS.json when present. The FP64,
+# FP32 and TF32 pipes are not in that file: "alu" peaks are the nominal figures (FP64
+# 1.25 TFLOP/s), with the throughput probe of profiles/hw_probe_gb300.md reported beside
+# them (FP64 DFMA 1.01, FP32 FFMA 73.3, cuBLAS TF32 1062 TFLOP/s).
+NOMINAL = {"fp64_tflops": 1.25, "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "hbm_gbs": 6800.0}
+PROBED = {"fp64_tflops": 1.01, "fp32_tflops": 73.3, "tf32_tflops": 1062.0}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = {"hbm_gbs": 6800.0, "source": "fallback"}
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained"):
+                if k in d:
+                    peaks[k] = float(d[k])
+            peaks["source"] = "measured"
+        except Exception:
+            pass
+    return peaks
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle timing (spawned workers, one BLAS thread each)
+# ---------------------------------------------------------------------------------------
+def _oracle_logdet_worker(args):
+    wl_name, nf, fid = args
+    from oracle import HolsteinParams
+    from oracle.fermion import fermion_logdet
+    from paper_1802_06177_gb300 import inputs
+    from paper_1802_06177_gb300.workloads import WORKLOADS
+    wl = WORKLOADS[wl_name]
+    p = HolsteinParams(wl.Lx, wl.Lx, wl.L, n_s=wl.n_s)
+    gen = inputs.mixed_fields if wl.fields == "mixed" else inputs.gaussian_fields
+    x = gen(nf, wl.Lx, wl.Lx, wl.L, seed=wl.seed)[fid]
+    lndet, sign, _ = fermion_logdet(p, x, want_G=False)
+    return fid, lndet, sign
+
+
+def oracle_pool(nproc):
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("MKL_NUM_THREADS", "1")
+    return mp.get_context("spawn").Pool(nproc)
+
+
+def oracle_logdets(pool, wl_name, nf, field_ids):
+    """Oracle ln|det| of fields of the benchmark batch (seeded exactly as on rank 0)."""
+    return {f: (l, sg) for f, l, sg in pool.map(_oracle_logdet_worker, [(wl_name, nf, f) for f in field_ids])}
+
+
+# ---------------------------------------------------------------------------------------
+# GPU clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        reasons = sorted({n for r in rows for n, v in zip(self.NAMES, r[5:9]) if "Active" in v and "Not" not in v})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------
+# algorithmic work per launch call of each kernel class (flops or bytes), per field
+# ---------------------------------------------------------------------------------------
+def class_work(cls, wl, nsl_mean):
+    N, L = wl.N, wl.L
+    if cls == "slice":
+        return 2.0 * N ** 3 * nsl_mean, "flop"
+    if cls == "qr":
+        return 4.0 / 3.0 * N ** 3, "flop"
+    if cls == "formq":
+        return 4.0 / 3.0 * N ** 3, "flop"
+    if cls == "tupdate":
+        return 1.0 * N ** 3, "flop"
+    if cls == "greens":
+        return 2.0 * N ** 3, "flop"
+    if cls == "sweep":
+        return 8.0 * N * L * 1.5, "byte"  # read the field once, write the updated half
+    return None, None
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, local, world
+
+
+def max_over_ranks(value, world, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1802_06177_gb300.workloads import WORKLOADS
+    wl = WORKLOADS[args.workload]
+    nproc = min(16, os.cpu_count() or 1)
+    pool = oracle_pool(nproc)
+    times = []
+    for s in range(args.warmup + args.steps):
+        done, _, wall = time_oracle_step(pool, nproc, wl.name, args.nsweeps)
+        if s >= args.warmup:
+            times.append((done, wall))
+    pool.close()
+    done = sum(d for d, _ in times)
+    wall = sum(w for _, w in times)
+    value = done / wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, args, "f64 oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle",
+                             "sample": "per step: %d chains (one per core), one oracle cumulative update each "
+                                       "(%d E_eff sweeps, exact ln w with UDT log-det and G, Eq. 6 accept) on %s"
+                                       % (nproc, args.nsweeps, wl.name)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _oracle_step_worker(args):
+    wl_name, chain, nsweeps = args
+    import numpy as np
+
+    from oracle import HolsteinParams
+    from oracle.chain import cumulative_update
+    from oracle.lattice import exp_hopping
+    from oracle.weight import log_weight
+    from paper_1802_06177_gb300 import inputs
+    from paper_1802_06177_gb300.workloads import WORKLOADS
+    wl = WORKLOADS[wl_name]
+    p = HolsteinParams(wl.Lx, wl.Lx, wl.L, n_s=wl.n_s)
+    E = exp_hopping(wl.Lx, wl.Lx, 1.0, 0.0, 0.1)
+    x = inputs.gaussian_fields(1, wl.Lx, wl.Lx, wl.L, seed=wl.seed + 7 * chain)[0]
+    J = np.array([50.25, 0.05, 0.0, 0.0, 0.5])
+    lw = log_weight(p, x, E)[0]
+    t0 = time.perf_counter()
+    cumulative_update(p, x, lw, 0.0, J, nsweeps, 0, chain, wl.seed, 0.3, E=E)
+    return time.perf_counter() - t0
+
+
+def time_oracle_step(pool, nproc, wl_name, nsweeps):
+    t0 = time.perf_counter()
+    per = pool.map(_oracle_step_worker, [(wl_name, c, nsweeps) for c in range(nproc)])
+    return nproc, max(per), time.perf_counter() - t0
+
+
+def config_of(wl, args, precision):
+    return {"workload": wl.name, "model": "holstein_2d", "N": wl.N, "Lx": wl.Lx, "L": wl.L, "beta": wl.beta,
+            "n_s": wl.n_s, "chains_per_gpu": args.fields or wl.nfields, "nsweeps": args.nsweeps,
+            "precision": precision, "global_batch": (args.fields or wl.nfields) * args.gpus,
+            "parallelism": "replicas x%d" % args.gpus,
+            "l2": "inputs larger than L2 (fields %.0f MB + workspace), no flush" % (
+                (args.fields or wl.nfields) * wl.N * wl.L * 8 / 1e6)}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1802_06177_gb300 import inputs
+    from paper_1802_06177_gb300.slmc import Context
+    from paper_1802_06177_gb300.workloads import WORKLOADS
+
+    rank, local, world = dist_setup(args)
+    wl = WORKLOADS[args.workload]
+    nf = args.fields or wl.nfields
+    pool = None
+    nproc = min(16, os.cpu_count() or 1)
+    if rank == 0 and not args.no_cpu_baseline:
+        pool = oracle_pool(nproc)  # spawn before the first GPU call
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed = wl.seed + 1000003 * rank
+    xh = inputs.mixed_fields(nf, wl.Lx, wl.Lx, wl.L, seed=seed) if wl.fields == "mixed" else \
+        inputs.gaussian_fields(nf, wl.Lx, wl.Lx, wl.L, seed=seed)
+    x0 = torch.from_numpy(xh).to(dev)
+
+    def make(prec):
+        return Context(wl.Lx, wl.Lx, wl.L, n_s=wl.n_s, precision=prec, max_fields=nf, seed=seed, sweep_delta=0.3,
+                       device=dev)
+
+    def setup(ctx):
+        x = x0.clone()
+        lnw0, _, _ = ctx.log_weight(x)
+        J, _ = ctx.fit_eff(x, lnw0)  # self-learned couplings of the initial batch
+        lnw, s = ctx.chain_init(x)
+        n_acc = torch.zeros(nf, dtype=torch.int64, device=dev)
+        n_sw = torch.zeros(nf, dtype=torch.int64, device=dev)
+        return {"x": x, "J": J, "lnw": lnw, "s": s, "n_acc": n_acc, "n_sw": n_sw}
+
+    def step(ctx, st, k):
+        if args.mode == "logdet":
+            ctx.logdet(st["x"])
+            return
+        ctx.cumulative_update(st["x"], st["J"], args.nsweeps, 1, k, st["lnw"], st["s"], st["n_acc"], st["n_sw"])
+        st["J_fit"], _ = ctx.fit_eff(st["x"], st["lnw"])
+
+    def timed(ctx, st, steps, warmup, k0, profile=False, clocks=False):
+        for k in range(warmup):
+            step(ctx, st, k0 + k)
+        torch.cuda.synchronize()
+        barrier(world)
+        sampler = ClockSampler(local) if clocks else None
+        if profile:
+            ctx.profile(True)
+        n0 = ctx.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for k in range(steps):
+            step(ctx, st, k0 + warmup + k)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = ctx.launch_count() - n0
+        prof = ctx.profile_read() if profile else None
+        if profile:
+            ctx.profile(False)
+        clk = sampler.stop() if sampler else None
+        ctx.get_error()
+        barrier(world)
+        return max_over_ranks(ms, world, dev), launches, prof, clk
+
+    # ---- headline: mixed precision --------------------------------------------------
+    ctx = make(args.precision)
+    st = setup(ctx)
+    ms, launches, prof, clk = timed(ctx, st, args.steps, args.warmup, 0, profile=True, clocks=True)
+    ms_step = ms / args.steps
+    value = nf * world / (ms_step / 1e3)
+
+    # ---- e2e through host buffers -----------------------------------------------------
+    xh_pin = torch.from_numpy(st["x"].cpu().numpy()).pin_memory()
+    lnw_h = torch.empty(nf, dtype=torch.float64).pin_memory()
+    s_h = torch.empty(nf, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    e0.record()
+    for k in range(e2e_steps):
+        st["x"].copy_(xh_pin, non_blocking=True)
+        step(ctx, st, 10 ** 6 + k)
+        xh_pin.copy_(st["x"], non_blocking=True)
+        lnw_h.copy_(st["lnw"], non_blocking=True)
+        s_h.copy_(st["s"], non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
+    h2d = nf * wl.N * wl.L * 8
+    d2h = h2d + 2 * nf * 8
+
+    # ---- logdet-only rates and accuracy of each mode ------------------------------------
+    h = args.acc_fields // 2
+    acc_ids = sorted(set(list(range(min(h, nf))) + list(range(nf // 2, min(nf, nf // 2 + args.acc_fields - h)))))
+    xs = x0[acc_ids].contiguous()
+    rates, lndets = {}, {}
+    old_mode = args.mode
+    args.mode = "logdet"
+    ms_ld, _, _, _ = timed(ctx, {"x": x0.clone()}, 1, 1, 0)
+    rates[args.precision] = nf * world / (ms_ld / 1e3)
+    lndets[args.precision] = ctx.logdet(xs)[0].cpu().numpy()
+    ctx.close()
+    fp64_value = None
+    if not args.no_fp64 and args.precision != "fp64":
+        c64 = make("fp64")
+        ms64, _, _, _ = timed(c64, {"x": x0.clone()}, 1, 1, 0)
+        rates["fp64"] = nf * world / (ms64 / 1e3)
+        lndets["fp64"] = c64.logdet(xs)[0].cpu().numpy()
+        args.mode = old_mode
+        if old_mode == "step":
+            st64 = setup(c64)
+            ms64s, _, _, _ = timed(c64, st64, 1, 1, 0)
+            fp64_value = nf * world / (ms64s / 1e3)
+        c64.close()
+    args.mode = old_mode
+
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the dominant kernel class -------------------------------------------
+    peaks = load_peaks()
+    ngroups = math.ceil(wl.L / wl.n_s)
+    nsl_mean = wl.L / ngroups
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_calls = prof[dom]
+    work, kind = class_work(dom, wl, nsl_mean)
+    roof = None
+    if work:
+        per_call = work * nf
+        avg_s = dom_ms / dom_calls / 1e3
+        fp64_cls = dom in ("qr", "formq", "tupdate", "greens") or (dom == "slice" and args.precision == "fp64")
+        if kind == "flop":
+            achieved = per_call / avg_s / 1e12
+            if fp64_cls:
+                peak, pk = NOMINAL["fp64_tflops"], PROBED["fp64_tflops"]
+            else:
+                peak, pk = NOMINAL["fp32_tflops"], PROBED["fp32_tflops"]
+            roof = {"bound": "alu", "pipe": "fp64" if fp64_cls else "fp32", "kernel_class": dom,
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_probed": pk, "frac_of_probed": achieved / pk, "traffic": None,
+                    "algorithmic_per_launch": per_call, "launches_timed": dom_calls, "avg_launch_ms": avg_s * 1e3,
+                    "peak_source": "nominal FP64 1.25 TFLOP/s (alu); probed DFMA rate beside it"}
+        else:
+            achieved = per_call / avg_s / 1e9
+            roof = {"bound": "hbm", "kernel_class": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "algorithmic_per_launch": per_call, "launches_timed": dom_calls, "avg_launch_ms": avg_s * 1e3,
+                    "peak_source": peaks["source"]}
+    total_prof = sum(v[0] for v in prof.values())
+    shares = {k: round(v[0] / total_prof, 4) for k, v in prof.items() if v[0] > 0}
+
+    # ---- accuracy against the FP64 oracle and CPU baseline ----------------------------
+    acc = None
+    cpu = None
+    if pool is not None:
+        ref = oracle_logdets(pool, wl.name, nf, acc_ids)
+        acc = {m: float(np.max(np.abs(v - np.array([ref[i][0] for i in acc_ids])))) for m, v in lndets.items()}
+        acc["sample_fields"] = acc_ids
+        done, busy, wall = time_oracle_step(pool, nproc, wl.name, args.nsweeps)
+        done2, busy2, wall2 = time_oracle_step(pool, nproc, wl.name, args.nsweeps)
+        cpu = {"value": (done + done2) / (wall + wall2), "unit": UNIT, "cores": nproc, "kind": "oracle",
+               "sample": "%d chains x 2 rounds (one per core, 1 BLAS thread each): one oracle cumulative update "
+                         "per chain (%d E_eff sweeps, exact ln w with UDT log-det and G, Eq. 6 accept) on %s"
+                         % (nproc, args.nsweeps, wl.name)}
+        pool.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 slices + f64 stabilisation" if args.precision != "fp64" else "f64",
+            "data": "synthetic", "config": config_of(wl, args, args.precision),
+            "e2e": {"value": nf * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "fp64_value": fp64_value, "logdet_only_evals_per_s": rates, "accuracy_max_abs_dlndet": acc,
+            "time_shares": shares, "mode": args.mode}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="slmc", choices=["slmc", "reference"])
+    ap.add_argument("--workload", default="holstein_16x16_L160")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32x3", "bf16x9"])
+    ap.add_argument("--nsweeps", type=int, default=20)
+    ap.add_argument("--fields", type=int, default=0, help="override chains per GPU (small profiling cases)")
+    ap.add_argument("--mode", default="step", choices=["step", "logdet"])
+    ap.add_argument("--acc-fields", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "slmc":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

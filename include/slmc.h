@@ -186,6 +186,35 @@ SLMC_API int slmc_fit_eff(slmc_ctx* ctx, const double* xs, const double* lnw, in
  * s_i = (-1)^(ix+iy). Output S[n]. */
 SLMC_API int slmc_measure_cdw(slmc_ctx* ctx, const double* G, int n, double* S, void* stream);
 
+/* Kernel classes reported by slmc_profile_read (index into its arrays). */
+#define SLMC_PROF_SLICE 0     /* slice-group products B ... B U */
+#define SLMC_PROF_QR 1        /* pivoted Householder QR */
+#define SLMC_PROF_FORMQ 2     /* formation of Q */
+#define SLMC_PROF_TUPDATE 3   /* T <- Rt P^T T */
+#define SLMC_PROF_FINAL 4     /* identity init, M assembly, LU and log-det */
+#define SLMC_PROF_GREENS 5    /* G solve */
+#define SLMC_PROF_SWEEP 6     /* effective-model half-sweeps */
+#define SLMC_PROF_EFF 7       /* effective-model features / ln w_eff */
+#define SLMC_PROF_BOSE 8      /* bosonic part of ln w */
+#define SLMC_PROF_ACCEPT 9    /* acceptance draws, accept/restore */
+#define SLMC_PROF_FIT 10      /* regression */
+#define SLMC_PROF_CDW 11      /* S(pi,pi) */
+#define SLMC_PROF_NCLASS 12
+
+/* Total number of CUDA kernels this context has enqueued since slmc_init (host counter,
+ * no synchronisation). */
+SLMC_API long long slmc_launch_count(slmc_ctx* ctx);
+
+/* on != 0: from now on every kernel enqueued by the context is bracketed by a pair of
+ * CUDA events on its stream (a few microseconds per launch); on = 0 stops recording.
+ * Enabling clears the accumulated totals. */
+SLMC_API int slmc_profile_enable(slmc_ctx* ctx, int on);
+
+/* Synchronises `stream`, then writes per kernel class the summed device time in ms[c]
+ * and the number of timed launch calls in calls[c] (arrays of SLMC_PROF_NCLASS entries;
+ * calls may be NULL). A call covers the kernels of one class enqueued together. */
+SLMC_API int slmc_profile_read(slmc_ctx* ctx, double* ms, long long* calls, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

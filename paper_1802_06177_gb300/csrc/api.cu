@@ -39,6 +39,57 @@ int validate(const slmc_params* p) {
     return SLMC_OK;
 }
 
+
+// ---- launch accounting and optional event timing ------------------------------------
+cudaEvent_t take_event(slmc_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+}
+
+int flush_profile(slmc_ctx* c) {
+    for (size_t q = 0; q < c->ev_cls.size(); ++q) {
+        cudaEvent_t b = c->ev_rec[2 * q], e = c->ev_rec[2 * q + 1];
+        float ms = 0.f;
+        if (cudaEventSynchronize(e) != cudaSuccess || cudaEventElapsedTime(&ms, b, e) != cudaSuccess)
+            return SLMC_ERR_CUDA;
+        c->prof_ms[c->ev_cls[q]] += ms;
+        c->prof_calls[c->ev_cls[q]] += 1;
+        c->ev_pool.push_back(b);
+        c->ev_pool.push_back(e);
+    }
+    c->ev_cls.clear();
+    c->ev_rec.clear();
+    return SLMC_OK;
+}
+
+// Enqueues fn() (which launches nkernels kernels of class cls on s) with accounting.
+template <typename Fn>
+int launch(slmc_ctx* c, int cls, int nkernels, cudaStream_t s, Fn&& fn) {
+    cudaEvent_t b = nullptr;
+    if (c->prof_on) {
+        b = take_event(c);
+        if (!b || cudaEventRecord(b, s) != cudaSuccess) return SLMC_ERR_CUDA;
+    }
+    if (fn() != cudaSuccess) return SLMC_ERR_CUDA;
+    c->launches += nkernels;
+    if (c->prof_on) {
+        cudaEvent_t e = take_event(c);
+        if (!e || cudaEventRecord(e, s) != cudaSuccess) return SLMC_ERR_CUDA;
+        c->ev_rec.push_back(b);
+        c->ev_rec.push_back(e);
+        c->ev_cls.push_back(cls);
+        if (c->ev_cls.size() >= 4096) return flush_profile(c);  // bounded pool: drains recorded pairs
+    }
+    return SLMC_OK;
+}
+
+#define SLMC_LAUNCH(cls, nk, s, expr) SLMC_TRY(launch(c, (cls), (nk), (s), [&]() { return (expr); }))
+
 bool checkerboard_ok(const slmc_ctx* c) { return c->p.Lx % 2 == 0 && c->p.Ly % 2 == 0 && c->L % 2 == 0; }
 
 // Scratch columns of ctx->scal ([8][max_fields]) and ctx->iscal ([4][max_fields]).
@@ -47,19 +98,19 @@ int* iscal(slmc_ctx* c, int col) { return c->iscal + (size_t)col * c->max_fields
 
 // Stabilised UDT chain + final LU for fields [0, nf) of one batch (nf <= max_fields).
 int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, double* G, cudaStream_t s) {
-    SLMC_CK(slmc::set_identity(c, nf, s));
+    SLMC_LAUNCH(SLMC_PROF_FINAL, 1, s, slmc::set_identity(c, nf, s));
     for (int l0 = 0; l0 < c->L; l0 += c->p.n_s) {
         const int nsl = std::min(c->p.n_s, c->L - l0);
         if (c->p.precision == SLMC_PREC_TF32X3 || c->p.precision == SLMC_PREC_BF16X9)
-            SLMC_CK(slmc::tc_slice_group(c, x, nf, l0, nsl, s));
+            SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::tc_slice_group(c, x, nf, l0, nsl, s));
         else
-            SLMC_CK(slmc::slice_group(c, x, nf, l0, nsl, s));
-        SLMC_CK(slmc::qr_pivoted(c, nf, s));
-        SLMC_CK(slmc::form_q(c, nf, s));
-        SLMC_CK(slmc::t_update(c, nf, s));
+            SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_group(c, x, nf, l0, nsl, s));
+        SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_pivoted(c, nf, s));
+        SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q(c, nf, s));
+        SLMC_LAUNCH(SLMC_PROF_TUPDATE, 1, s, slmc::t_update(c, nf, s));
     }
-    SLMC_CK(slmc::final_logdet(c, nf, lndet, sign, s));
-    if (G) SLMC_CK(slmc::final_greens(c, nf, G, s));
+    SLMC_LAUNCH(SLMC_PROF_FINAL, 2, s, slmc::final_logdet(c, nf, lndet, sign, s));
+    if (G) SLMC_LAUNCH(SLMC_PROF_GREENS, 1, s, slmc::final_greens(c, nf, G, s));
     return SLMC_OK;
 }
 
@@ -73,7 +124,9 @@ int for_batches(slmc_ctx* c, int n, F&& fn) {
 }
 
 void free_ctx(slmc_ctx* c) {
-    void* bufs[] = {c->E64, c->E32, c->Etf, c->Ebf, c->Y, c->QR, c->U, c->Ta, c->Tb, c->lnD, c->tau,
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
+    void* bufs[] = {c->E64, c->F32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->Ta, c->Tb, c->lnD, c->tau,
                     c->perm, c->piv, c->sgnU, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -121,9 +174,9 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
         if (cudaMalloc(reinterpret_cast<void**>(ptr), bytes) != cudaSuccess) ok = false;
     };
     alloc(&c->E64, NN * sizeof(double));
-    alloc(&c->E32, NN * sizeof(float));
-    if (p->precision == SLMC_PREC_TF32X3) alloc(&c->Etf, 2 * NN * sizeof(uint32_t));
-    if (p->precision == SLMC_PREC_BF16X9) alloc(&c->Ebf, 3 * NN * sizeof(uint16_t));
+    alloc(&c->F32, NN * sizeof(float));
+    if (p->precision == SLMC_PREC_TF32X3) alloc(&c->Ftf, 2 * NN * sizeof(uint32_t));
+    if (p->precision == SLMC_PREC_BF16X9) alloc(&c->Fbf, 3 * NN * sizeof(uint16_t));
     alloc(&c->Y, F * NN * sizeof(double));
     alloc(&c->QR, F * NN * sizeof(double));
     alloc(&c->U, F * NN * sizeof(double));
@@ -197,7 +250,7 @@ int slmc_log_weight(slmc_ctx* c, const double* x, int n, double* lnw, double* ln
         double* ld = lndet ? lndet + f0 : scal(c, 0);
         int* sg = sign ? sign + f0 : iscal(c, 0);
         SLMC_TRY(logdet_batch(c, x + f0 * NL, nf, ld, sg, nullptr, s));
-        SLMC_CK(slmc::bose_log_weight(c, x + f0 * NL, nf, ld, lnw + f0, s));
+        SLMC_LAUNCH(SLMC_PROF_BOSE, 1, s, slmc::bose_log_weight(c, x + f0 * NL, nf, ld, lnw + f0, s));
         return SLMC_OK;
     });
 }
@@ -205,14 +258,16 @@ int slmc_log_weight(slmc_ctx* c, const double* x, int n, double* lnw, double* ln
 int slmc_eff_features(slmc_ctx* c, const double* x, int n, double* F, void* stream) {
     if (!c || n < 0 || (n > 0 && (!x || !F))) return SLMC_ERR_ARG;
     if (n == 0) return SLMC_OK;
-    SLMC_CK(slmc::eff_features(c, x, n, nullptr, F, 5, nullptr, as_stream(stream)));
+    cudaStream_t s = as_stream(stream);
+    SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, x, n, nullptr, F, 5, nullptr, s));
     return SLMC_OK;
 }
 
 int slmc_eff_log_weight(slmc_ctx* c, const double* x, int n, const double* J, double* lnw_eff, void* stream) {
     if (!c || n < 0 || (n > 0 && (!x || !J || !lnw_eff))) return SLMC_ERR_ARG;
     if (n == 0) return SLMC_OK;
-    SLMC_CK(slmc::eff_features(c, x, n, J, nullptr, 0, lnw_eff, as_stream(stream)));
+    cudaStream_t s = as_stream(stream);
+    SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, x, n, J, nullptr, 0, lnw_eff, s));
     return SLMC_OK;
 }
 
@@ -225,7 +280,8 @@ int slmc_eff_sweep(slmc_ctx* c, double* x, int n, const double* J, int nsweeps, 
     cudaStream_t s = as_stream(stream);
     for (int sw = 0; sw < nsweeps && n > 0; ++sw)
         for (int h = 0; h < 2; ++h)
-            SLMC_CK(slmc::eff_half_sweep(c, x, n, 0, J, sweep0 + sw, first_colour ^ h, nullptr, 0, n_acc, s));
+            SLMC_LAUNCH(SLMC_PROF_SWEEP, 1, s,
+                        slmc::eff_half_sweep(c, x, n, 0, J, sweep0 + sw, first_colour ^ h, nullptr, 0, n_acc, s));
     return SLMC_OK;
 }
 
@@ -235,8 +291,8 @@ int slmc_chain_init(slmc_ctx* c, const double* x, int n, double* lnw, double* s_
     cudaStream_t s = as_stream(stream);
     return for_batches(c, n, [&](int f0, int nf) {
         SLMC_TRY(logdet_batch(c, x + f0 * NL, nf, scal(c, 0), iscal(c, 0), s_cdw ? c->QR : nullptr, s));
-        SLMC_CK(slmc::bose_log_weight(c, x + f0 * NL, nf, scal(c, 0), lnw + f0, s));
-        if (s_cdw) SLMC_CK(slmc::cdw_measure(c, c->QR, nf, s_cdw + f0, nullptr, nullptr, s));
+        SLMC_LAUNCH(SLMC_PROF_BOSE, 1, s, slmc::bose_log_weight(c, x + f0 * NL, nf, scal(c, 0), lnw + f0, s));
+        if (s_cdw) SLMC_LAUNCH(SLMC_PROF_CDW, 1, s, slmc::cdw_measure(c, c->QR, nf, s_cdw + f0, nullptr, nullptr, s));
         return SLMC_OK;
     });
 }
@@ -253,21 +309,24 @@ int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int n
         double* xc = x + f0 * NL;
         for (int u = 0; u < nupdates; ++u) {
             const uint64_t upd = update0 + (uint64_t)u;
-            SLMC_CK(slmc::update_draws(c, nf, f0, upd, iscal(c, 1), scal(c, 4), s));
+            SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::update_draws(c, nf, f0, upd, iscal(c, 1), scal(c, 4), s));
             SLMC_CK(cudaMemcpyAsync(c->x_old, xc, nf * NL * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            SLMC_CK(slmc::eff_features(c, xc, nf, J, nullptr, 0, scal(c, 1), s));
+            SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, xc, nf, J, nullptr, 0, scal(c, 1), s));
             for (int sw = 0; sw < nsweeps; ++sw)
                 for (int h = 0; h < 2; ++h)
-                    SLMC_CK(slmc::eff_half_sweep(c, xc, nf, f0, J, upd * (uint64_t)nsweeps + sw, 0, iscal(c, 1), h,
-                                                 n_sweep_acc ? n_sweep_acc + f0 : nullptr, s));
-            SLMC_CK(slmc::eff_features(c, xc, nf, J, nullptr, 0, scal(c, 2), s));
+                    SLMC_LAUNCH(SLMC_PROF_SWEEP, 1, s,
+                                slmc::eff_half_sweep(c, xc, nf, f0, J, upd * (uint64_t)nsweeps + sw, 0, iscal(c, 1), h,
+                                                     n_sweep_acc ? n_sweep_acc + f0 : nullptr, s));
+            SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, xc, nf, J, nullptr, 0, scal(c, 2), s));
             SLMC_TRY(logdet_batch(c, xc, nf, scal(c, 0), iscal(c, 0), s_cdw ? c->QR : nullptr, s));
-            SLMC_CK(slmc::bose_log_weight(c, xc, nf, scal(c, 0), scal(c, 3), s));
-            SLMC_CK(slmc::accept_update(c, nf, xc, c->x_old, scal(c, 3), scal(c, 1), scal(c, 2), scal(c, 4), lnw + f0,
-                                        iscal(c, 2), n_acc ? n_acc + f0 : nullptr, s));
+            SLMC_LAUNCH(SLMC_PROF_BOSE, 1, s, slmc::bose_log_weight(c, xc, nf, scal(c, 0), scal(c, 3), s));
+            SLMC_LAUNCH(SLMC_PROF_ACCEPT, 2, s,
+                        slmc::accept_update(c, nf, xc, c->x_old, scal(c, 3), scal(c, 1), scal(c, 2), scal(c, 4),
+                                            lnw + f0, iscal(c, 2), n_acc ? n_acc + f0 : nullptr, s));
             if (s_cdw)
-                SLMC_CK(slmc::cdw_measure(c, c->QR, nf, s_cdw + f0, iscal(c, 2),
-                                          obs ? obs + (size_t)u * n + f0 : nullptr, s));
+                SLMC_LAUNCH(SLMC_PROF_CDW, 1, s,
+                            slmc::cdw_measure(c, c->QR, nf, s_cdw + f0, iscal(c, 2),
+                                              obs ? obs + (size_t)u * n + f0 : nullptr, s));
         }
         return SLMC_OK;
     });
@@ -278,20 +337,47 @@ int slmc_fit_eff(slmc_ctx* c, const double* xs, const double* lnw, int nconf, do
     if (!c || nconf < 6 || !xs || !lnw || !J_out) return SLMC_ERR_ARG;
     const size_t NL = (size_t)c->N * c->L;
     cudaStream_t s = as_stream(stream);
-    SLMC_CK(slmc::fit_begin(c, s));
+    SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_begin(c, s));
     SLMC_TRY(for_batches(c, nconf, [&](int f0, int nf) {
-        SLMC_CK(slmc::eff_features(c, xs + f0 * NL, nf, nullptr, c->feat, 8, nullptr, s));
-        SLMC_CK(slmc::fit_accumulate(c, c->feat, lnw + f0, nf, s));
+        SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, xs + f0 * NL, nf, nullptr, c->feat, 8, nullptr, s));
+        SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_accumulate(c, c->feat, lnw + f0, nf, s));
         return SLMC_OK;
     }));
-    SLMC_CK(slmc::fit_finish(c, nconf, J_out, resid, s));
+    SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_finish(c, nconf, J_out, resid, s));
     return SLMC_OK;
 }
 
 int slmc_measure_cdw(slmc_ctx* c, const double* G, int n, double* S, void* stream) {
     if (!c || n < 0 || (n > 0 && (!G || !S))) return SLMC_ERR_ARG;
     if (n == 0) return SLMC_OK;
-    SLMC_CK(slmc::cdw_measure(c, G, n, S, nullptr, nullptr, as_stream(stream)));
+    cudaStream_t s = as_stream(stream);
+    SLMC_LAUNCH(SLMC_PROF_CDW, 1, s, slmc::cdw_measure(c, G, n, S, nullptr, nullptr, s));
+    return SLMC_OK;
+}
+
+long long slmc_launch_count(slmc_ctx* c) { return c ? c->launches : 0; }
+
+int slmc_profile_enable(slmc_ctx* c, int on) {
+    if (!c) return SLMC_ERR_ARG;
+    if (on) {
+        SLMC_TRY(flush_profile(c));
+        for (int q = 0; q < SLMC_PROF_NCLASS; ++q) {
+            c->prof_ms[q] = 0.0;
+            c->prof_calls[q] = 0;
+        }
+    }
+    c->prof_on = on != 0;
+    return SLMC_OK;
+}
+
+int slmc_profile_read(slmc_ctx* c, double* ms, long long* calls, void* stream) {
+    if (!c || !ms) return SLMC_ERR_ARG;
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return SLMC_ERR_CUDA;
+    SLMC_TRY(flush_profile(c));
+    for (int q = 0; q < SLMC_PROF_NCLASS; ++q) {
+        ms[q] = c->prof_ms[q];
+        if (calls) calls[q] = c->prof_calls[q];
+    }
     return SLMC_OK;
 }
 

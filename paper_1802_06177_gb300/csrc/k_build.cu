@@ -2,7 +2,8 @@
 // device from the plane-wave eigenbasis of K:
 //   E_ij = (1/N) sum_k cos(k . (r_i - r_j)) exp(-dtau eps_k),  eps_k = -2t (cos kx + cos ky) - mu,
 // k = 2 pi (nx/Lx, ny/Ly). Phases are formed as exact rationals and evaluated with cospi.
-// Low-precision copies and tensor-core operand splits of E are derived from the FP64 matrix.
+// Reduced-precision modes multiply by F = E - I (identity added exactly afterwards); its
+// FP32 copy and tensor-core operand splits are derived from the FP64 matrix.
 #include <cuda_bf16.h>
 
 #include "slmc_internal.cuh"
@@ -34,27 +35,29 @@ __device__ __forceinline__ uint32_t to_tf32(float v) {
     return r;
 }
 
-__global__ void k_split_E(const double* __restrict__ E, float* __restrict__ E32, uint32_t* __restrict__ Etf,
-                          uint16_t* __restrict__ Ebf, int NN) {
+__global__ void k_split_F(const double* __restrict__ E, float* __restrict__ F32, uint32_t* __restrict__ Ftf,
+                          uint16_t* __restrict__ Fbf, int N) {
+    const int NN = N * N;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= NN) return;
-    const float v = (float)E[idx];
-    E32[idx] = v;
-    if (Etf) {
+    const double fd = E[idx] - ((idx % (N + 1) == 0) ? 1.0 : 0.0);
+    const float v = (float)fd;
+    F32[idx] = v;
+    if (Ftf) {
         const uint32_t hi = to_tf32(v);
         const uint32_t lo = to_tf32(v - __uint_as_float(hi));
-        Etf[idx] = hi;
-        Etf[NN + idx] = lo;
+        Ftf[idx] = hi;
+        Ftf[NN + idx] = lo;
     }
-    if (Ebf) {
+    if (Fbf) {
         const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
         const float r1 = v - __bfloat162float(b0);
         const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
         const float r2 = r1 - __bfloat162float(b1);
         const __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
-        Ebf[idx] = __bfloat16_as_ushort(b0);
-        Ebf[NN + idx] = __bfloat16_as_ushort(b1);
-        Ebf[2 * NN + idx] = __bfloat16_as_ushort(b2);
+        Fbf[idx] = __bfloat16_as_ushort(b0);
+        Fbf[NN + idx] = __bfloat16_as_ushort(b1);
+        Fbf[2 * NN + idx] = __bfloat16_as_ushort(b2);
     }
 }
 
@@ -66,7 +69,7 @@ cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s) {
     const int N = c->N;
     const int NN = N * N;
     k_hopping_exp<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->p.Lx, c->p.Ly, c->p.dtau, c->p.t, c->p.mu);
-    k_split_E<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->E32, c->Etf, c->Ebf, NN);
+    k_split_F<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->F32, c->Ftf, c->Fbf, N);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/slmc.h"
 
 // Device-side sticky error bits (ctx->err).
@@ -17,10 +19,10 @@ struct slmc_ctx {
     int N, L, max_fields, device;
     // exp(-dtau K), built on the device from the plane-wave eigenbasis of K.
     double* E64;
-    float* E32;
-    // tensor-core operand splits of E (filled only in the matching precision modes)
-    uint32_t* Etf;   // [2][N][N] TF32 hi / lo bit patterns
-    uint16_t* Ebf;   // [3][N][N] BF16 three-way split
+    float* F32;      // F = E - I rounded to FP32 (reduced-precision slices use Y + F Y)
+    // tensor-core operand splits of F (filled only in the matching precision modes)
+    uint32_t* Ftf;   // [2][N][N] TF32 hi / lo bit patterns
+    uint16_t* Fbf;   // [3][N][N] BF16 three-way split
     // Per-field workspace, [max_fields][N][N] column-major unless stated.
     double* Y;       // slice-group product; reused for M in the final step
     double* QR;      // packed pivoted-QR output; reused for G in the cumulative update
@@ -40,6 +42,14 @@ struct slmc_ctx {
     double* feat;    // [max_fields][8]
     double* fitR;    // [64] Givens-QR state of the regression
     unsigned int* err;
+    // Launch accounting and optional per-class event timing (host side).
+    long long launches;
+    bool prof_on;
+    std::vector<cudaEvent_t> ev_pool;            // free events
+    std::vector<int> ev_cls;                      // class of each recorded pair
+    std::vector<cudaEvent_t> ev_rec;             // recorded begin/end pairs
+    double prof_ms[SLMC_PROF_NCLASS];
+    long long prof_calls[SLMC_PROF_NCLASS];
 };
 
 namespace slmc {

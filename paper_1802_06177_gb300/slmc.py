@@ -31,7 +31,10 @@ class Params(ctypes.Structure):
 
 EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", "slmc_logdet", "slmc_greens",
            "slmc_log_weight", "slmc_eff_features", "slmc_eff_log_weight", "slmc_eff_sweep", "slmc_chain_init",
-           "slmc_cumulative_update", "slmc_fit_eff", "slmc_measure_cdw")
+           "slmc_cumulative_update", "slmc_fit_eff", "slmc_measure_cdw", "slmc_launch_count", "slmc_profile_enable",
+           "slmc_profile_read")
+
+PROF_CLASSES = ("slice", "qr", "formq", "tupdate", "final", "greens", "sweep", "eff", "bose", "accept", "fit", "cdw")
 
 _lib = None
 
@@ -61,6 +64,9 @@ def load_library(path=LIB_PATH):
         "slmc_cumulative_update": ([P, P, I, P, I, I, U64, P, P, P, P, P, V], I),
         "slmc_fit_eff": ([P, P, P, I, P, P, V], I),
         "slmc_measure_cdw": ([P, P, I, P, V], I),
+        "slmc_launch_count": ([P], ctypes.c_longlong),
+        "slmc_profile_enable": ([P, I], I),
+        "slmc_profile_read": ([P, P, P, V], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -211,6 +217,21 @@ class Context:
                                                           _stream(self.device)))
         return J, resid
 
+    def launch_count(self):
+        """Kernels enqueued by this context so far."""
+        return int(self.lib.slmc_launch_count(self._ctx))
+
+    def profile(self, on=True):
+        self._check("slmc_profile_enable", self.lib.slmc_profile_enable(self._ctx, 1 if on else 0))
+
+    def profile_read(self):
+        """{class: (total ms, timed calls)} of the event-timed launches since profile(True)."""
+        n = len(PROF_CLASSES)
+        ms = (ctypes.c_double * n)()
+        calls = (ctypes.c_longlong * n)()
+        self._check("slmc_profile_read", self.lib.slmc_profile_read(self._ctx, ms, calls, _stream(self.device)))
+        return {k: (ms[q], calls[q]) for q, k in enumerate(PROF_CLASSES)}
+
     def measure_cdw(self, G):
         n = G.shape[0]
         S = self._empty(n)
@@ -218,3 +239,4 @@ class Context:
             self._ctx, _ptr(G, torch.float64, "G", (n, self.N, self.N)), n, _ptr(S, torch.float64, "S"),
             _stream(self.device)))
         return S
+
