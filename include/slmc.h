@@ -39,6 +39,7 @@
 #ifndef SLMC_H
 #define SLMC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -214,6 +215,31 @@ SLMC_API int slmc_profile_enable(slmc_ctx* ctx, int on);
  * and the number of timed launch calls in calls[c] (arrays of SLMC_PROF_NCLASS entries;
  * calls may be NULL). A call covers the kernels of one class enqueued together. */
 SLMC_API int slmc_profile_read(slmc_ctx* ctx, double* ms, long long* calls, void* stream);
+
+/* Allocation-free ln|det(I + B_L ... B_1)| (the paper has no counterpart; this is a library
+ * service). For callers that cannot allocate device memory where they need the result:
+ * code running during CUDA-graph stream capture, latency-critical loops that must avoid
+ * the allocator and the device synchronisation cudaMalloc may imply, and hosts whose own
+ * allocator owns the device memory budget. No context is needed and nothing is allocated
+ * (no cudaMalloc/cudaFree, no allocating library call): E and the whole UDT workspace live
+ * in one file-scope device array of slmc_logdet_noalloc_scratch_bytes() = 16 MiB that every
+ * GPU loading the library holds until process exit.
+ *   p       model parameters as for slmc_init; precision SLMC_PREC_FP64 or SLMC_PREC_FP32
+ *   x, n, lndet, sign  as for slmc_logdet (device pointers, results on `stream`)
+ * Size limit: the 16 MiB must hold E, F and at least one field's workspace, about
+ * 52 N^2 + 40 N bytes, so N <= 560 (a 16x16 or 20x20 lattice, not 24x24); larger N returns
+ * SLMC_ERR_UNSUPPORTED before anything is enqueued. Fields beyond the array's capacity are
+ * processed in consecutive batches.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture. All calls share the array
+ * and it keeps the last call's contents; each call clears the error word it uses on the
+ * stream. Calls that overlap on the GPU race on the array: serialise them. Device-side
+ * failures are reported only through the outputs (lndet NaN, sign 0). */
+SLMC_API int slmc_logdet_noalloc(const slmc_params* p, const double* x, int n, double* lndet, int* sign,
+                                 void* stream);
+
+/* Size in bytes of the device array used by slmc_logdet_noalloc. */
+SLMC_API size_t slmc_logdet_noalloc_scratch_bytes(void);
 
 #ifdef __cplusplus
 }

@@ -135,6 +135,15 @@ void free_ctx(slmc_ctx* c) {
 
 }  // namespace
 
+namespace slmc {
+// Shared with the allocation-free entry point (k_noalloc.cu): parameter validation and the
+// stabilised UDT chain + LU of slmc_logdet for one batch of fields.
+int validate_params(const slmc_params* p) { return validate(p); }
+int logdet_fields(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, cudaStream_t s) {
+    return logdet_batch(c, x, nf, lndet, sign, nullptr, s);
+}
+}  // namespace slmc
+
 extern "C" {
 
 const char* slmc_status_string(int status) {

@@ -124,4 +124,6 @@ cudaError_t fit_begin(slmc_ctx* c, cudaStream_t s);
 cudaError_t fit_accumulate(slmc_ctx* c, const double* feat, const double* lnw, int nconf,
                            cudaStream_t s);
 cudaError_t fit_finish(slmc_ctx* c, int nconf, double* J_out, double* resid, cudaStream_t s);
+int validate_params(const slmc_params* p);
+int logdet_fields(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, cudaStream_t s);
 }  // namespace slmc

@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
 EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", "slmc_logdet", "slmc_greens",
            "slmc_log_weight", "slmc_eff_features", "slmc_eff_log_weight", "slmc_eff_sweep", "slmc_chain_init",
            "slmc_cumulative_update", "slmc_fit_eff", "slmc_measure_cdw", "slmc_launch_count", "slmc_profile_enable",
-           "slmc_profile_read")
+           "slmc_profile_read", "slmc_logdet_noalloc", "slmc_logdet_noalloc_scratch_bytes")
 
 PROF_CLASSES = ("slice", "qr", "formq", "tupdate", "final", "greens", "sweep", "eff", "bose", "accept", "fit", "cdw")
 
@@ -67,6 +67,8 @@ def load_library(path=LIB_PATH):
         "slmc_launch_count": ([P], ctypes.c_longlong),
         "slmc_profile_enable": ([P, I], I),
         "slmc_profile_read": ([P, P, P, V], I),
+        "slmc_logdet_noalloc": ([ctypes.POINTER(Params), P, I, P, P, V], I),
+        "slmc_logdet_noalloc_scratch_bytes": ([], ctypes.c_size_t),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -240,3 +242,20 @@ class Context:
             _stream(self.device)))
         return S
 
+
+def logdet_noalloc(x, Lx, Ly, L, dtau=0.1, t=1.0, mu=0.0, omega0=1.0, lam=1.0, n_s=10, precision="fp64",
+                   lndet=None, sign=None):
+    """slmc_logdet_noalloc: ln|det| and sign of fields x[n, N, L] without a context and
+    without any device allocation inside the library (its workspace is a fixed 16 MiB
+    device array). Outputs may be passed in preallocated; errors show as NaN / sign 0."""
+    lib = load_library()
+    p = Params(Lx, Ly, L, dtau, t, mu, omega0, lam, n_s, PRECISION[precision], 0.0, 0)
+    n = x.shape[0]
+    lndet = torch.empty(n, dtype=torch.float64, device=x.device) if lndet is None else lndet
+    sign = torch.empty(n, dtype=torch.int32, device=x.device) if sign is None else sign
+    st = lib.slmc_logdet_noalloc(ctypes.byref(p), _ptr(x, torch.float64, "x"), n,
+                                 _ptr(lndet, torch.float64, "lndet", (n,)), _ptr(sign, torch.int32, "sign", (n,)),
+                                 _stream(x.device))
+    if st != 0:
+        raise SlmcError("slmc_logdet_noalloc", st)
+    return lndet, sign
