@@ -83,7 +83,12 @@ typedef struct slmc_params {
     int precision;       /* SLMC_PREC_* */
     double sweep_delta;  /* half-width of the uniform local proposal x -> x + U[-d, d] */
     uint64_t seed;       /* Philox-4x32-10 key for sweeps and acceptance draws */
+    int qr_mode;         /* SLMC_QR_* column ordering of the stabilising QR */
 } slmc_params;
+
+/* Column ordering of the stabilising QR (both FP64, both order columns by ||y_j|| D_j). */
+#define SLMC_QR_PREPIVOT 0  /* sort once per QR, then blocked Householder with WY updates (default) */
+#define SLMC_QR_PIVOTED 1   /* re-pivot on downdated norms at every column (column-by-column) */
 
 typedef struct slmc_ctx slmc_ctx;
 
@@ -227,7 +232,7 @@ SLMC_API int slmc_profile_read(slmc_ctx* ctx, double* ms, long long* calls, void
  *   p       model parameters as for slmc_init; precision SLMC_PREC_FP64 or SLMC_PREC_FP32
  *   x, n, lndet, sign  as for slmc_logdet (device pointers, results on `stream`)
  * Size limit: the 16 MiB must hold E, F and at least one field's workspace, about
- * 52 N^2 + 40 N bytes, so N <= 560 (a 16x16 or 20x20 lattice, not 24x24); larger N returns
+ * 52 N^2 + 300 N bytes, so N <= 560 (a 16x16 or 20x20 lattice, not 24x24); larger N returns
  * SLMC_ERR_UNSUPPORTED before anything is enqueued. Fields beyond the array's capacity are
  * processed in consecutive batches.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress)

@@ -34,6 +34,7 @@ int validate(const slmc_params* p) {
         !std::isfinite(p->sweep_delta) || p->sweep_delta < 0.0)
         return SLMC_ERR_ARG;
     if (p->precision < SLMC_PREC_FP64 || p->precision > SLMC_PREC_BF16X9) return SLMC_ERR_ARG;
+    if (p->qr_mode != SLMC_QR_PREPIVOT && p->qr_mode != SLMC_QR_PIVOTED) return SLMC_ERR_ARG;
     if ((long long)p->Lx * p->Ly > SLMC_MAX_N) return SLMC_ERR_UNSUPPORTED;
     if ((long long)p->Lx * p->Ly * p->L >= (1ll << 31)) return SLMC_ERR_UNSUPPORTED;
     return SLMC_OK;
@@ -105,9 +106,14 @@ int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign,
             SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::tc_slice_group(c, x, nf, l0, nsl, s));
         else
             SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_group(c, x, nf, l0, nsl, s));
-        SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_pivoted(c, nf, s));
-        SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q(c, nf, s));
-        SLMC_LAUNCH(SLMC_PROF_TUPDATE, 1, s, slmc::t_update(c, nf, s));
+        if (c->p.qr_mode == SLMC_QR_PIVOTED) {
+            SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_pivoted(c, nf, s));
+            SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q(c, nf, s));
+        } else {
+            SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_blocked(c, nf, s));
+            SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q_blocked(c, nf, s));
+        }
+        SLMC_LAUNCH(SLMC_PROF_TUPDATE, 1, s, slmc::t_update_tiled(c, nf, s));
     }
     SLMC_LAUNCH(SLMC_PROF_FINAL, 2, s, slmc::final_logdet(c, nf, lndet, sign, s));
     if (G) SLMC_LAUNCH(SLMC_PROF_GREENS, 1, s, slmc::final_greens(c, nf, G, s));
@@ -127,7 +133,7 @@ void free_ctx(slmc_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
     void* bufs[] = {c->E64, c->F32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->Ta, c->Tb, c->lnD, c->tau,
-                    c->perm, c->piv, c->sgnU, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err};
+                    c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -196,6 +202,7 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     alloc(&c->perm, F * N * sizeof(int));
     alloc(&c->piv, F * N * sizeof(int));
     alloc(&c->sgnU, F * sizeof(int));
+    alloc(&c->Sws, F * N * 32 * sizeof(double));
     alloc(&c->x_old, F * N * L * sizeof(double));
     alloc(&c->scal, 8 * F * sizeof(double));
     alloc(&c->iscal, 4 * F * sizeof(int));

@@ -15,7 +15,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-// M (column-major, written over Y) from U (column-major), T (column-major) and lnD.
+// M (column-major, written over Y) from U (column-major), T (row-major) and lnD.
 __global__ void __launch_bounds__(kThreads) k_assemble_M(const double* __restrict__ Uall, const double* __restrict__ Tall,
                                                          const double* __restrict__ lnD_all, double* __restrict__ Mall,
                                                          int N) {
@@ -33,9 +33,9 @@ __global__ void __launch_bounds__(kThreads) k_assemble_M(const double* __restric
     const double* U = Uall + f * NN;
     const double* T = Tall + f * NN;
     double* M = Mall + f * NN;
-    for (size_t idx = threadIdx.x; idx < NN; idx += kThreads) {
+    for (size_t idx = threadIdx.x; idx < NN; idx += kThreads) {  // M column-major, T row-major
         const int j = (int)(idx / N), i = (int)(idx - (size_t)j * N);
-        M[idx] = fma(sb[i], U[(size_t)i * N + j], ss[i] * T[idx]);
+        M[idx] = fma(sb[i], U[(size_t)i * N + j], ss[i] * T[(size_t)i * N + j]);
     }
 }
 

@@ -1,4 +1,4 @@
-// SIMT panel kernels of the slice-group product and of the T update.
+// SIMT panel kernel of the slice-group product.
 //
 // Slice group [Suppl. Eq. (S2)]: for one stabilisation group of nsl slices starting at l0,
 //   Y = B_{l0+nsl} ... B_{l0+1} U,   B_l = diag(exp(-dtau lambda x[:, l-1])) E.
@@ -11,10 +11,6 @@
 // E (symmetric, L2-resident) once per slice; the diagonal phonon scaling of each slice is
 // applied in the epilogue before the panel is reused. Only U is read from and Y written to
 // global memory, once per group.
-//
-// T update (UDT stabilisation): T_new = Rt P^T T_old with Rt the scaled upper triangle of the
-// pivoted QR (column-major, strictly-lower part holds Householder vectors and is skipped)
-// and (P^T T_old)[k, :] = T_old[perm[k], :]. Same panel kernel with a per-field triangular A.
 //
 // Layout: every N x N matrix is column-major, element (i, j) at j*N + i.
 #include "slmc_internal.cuh"
@@ -156,16 +152,6 @@ cudaError_t slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, c
     if (c->p.precision == SLMC_PREC_FP32)  // F = E - I in FP32, identity added in the epilogue
         return dispatch_panel<float, false>(c->F32, 0, c->U, nullptr, c->Y, x, c->N, c->L, l0, nsl, dtlam, 1, nf, s);
     return dispatch_panel<double, false>(c->E64, 0, c->U, nullptr, c->Y, x, c->N, c->L, l0, nsl, dtlam, 0, nf, s);
-}
-
-cudaError_t t_update(slmc_ctx* c, int nf, cudaStream_t s) {
-    const size_t NN = (size_t)c->N * c->N;
-    cudaError_t e =
-        dispatch_panel<double, true>(c->QR, NN, c->Ta, c->perm, c->Tb, nullptr, c->N, c->L, 0, 1, 0.0, 0, nf, s);
-    double* t = c->Ta;
-    c->Ta = c->Tb;
-    c->Tb = t;
-    return e;
 }
 
 cudaError_t set_identity(slmc_ctx* c, int nf, cudaStream_t s) {

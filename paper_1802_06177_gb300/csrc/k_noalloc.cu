@@ -34,7 +34,8 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Bytes of the per-context part (E, F, error word) and of one field's workspace.
 size_t fixed_bytes(size_t N) { return align256(N * N * sizeof(double)) + align256(N * N * sizeof(float)) + 256; }
 size_t field_bytes(size_t N) {
-    return 5 * N * N * sizeof(double) + 2 * N * sizeof(double) + 2 * N * sizeof(int) + sizeof(int);
+    return 5 * N * N * sizeof(double) + 32 * N * sizeof(double) + 2 * N * sizeof(double) + 2 * N * sizeof(int) +
+           sizeof(int);
 }
 
 int scratch_address(int device, unsigned char** out) {
@@ -90,7 +91,8 @@ int slmc_logdet_noalloc(const slmc_params* p, const double* x, int n, double* ln
     c.U = c.QR + F * NN;
     c.Ta = c.U + F * NN;
     c.Tb = c.Ta + F * NN;
-    c.lnD = c.Tb + F * NN;
+    c.Sws = c.Tb + F * NN;
+    c.lnD = c.Sws + F * N * 32;
     c.tau = c.lnD + F * N;
     c.perm = reinterpret_cast<int*>(c.tau + F * N);
     c.piv = c.perm + F * N;

@@ -1,0 +1,455 @@
+// Blocked UDT stabilisation in FP64: pre-pivoted blocked Householder QR, blocked formation
+// of Q, and the T update as a tiled triangular GEMM.
+//
+// On this part the FP64 pipe is the scarce unit, so every FP64 issue slot should be an FMA
+// of the factorisation itself. A column-by-column (BLAS-2) QR spends most slots on
+// reduction trees and norm downdates; here the columns are ordered once by their scaled
+// norms ||y_j|| D_j (pre-pivoting, the ordering full column pivoting starts from), and the
+// unpivoted QR is blocked: a panel of BP columns is factored in shared memory, then the
+// trailing columns receive the panel's reflectors at once through the compact WY form
+// Q_p = I - V S V^T as three small GEMMs (W = V^T C, W' = S^T W, C -= V W') whose inner loops
+// are plain FMAs. Each warp updates its own groups of 8 trailing columns with no block
+// synchronisation. The graded structure that makes this as accurate as per-step pivoting for
+// products of this kind is the column scaling by D, which the pre-sort already captures.
+//
+// As in the unblocked kernel, the QR factors Y itself and carries D as logarithms
+// (pivot keys ||y_j||^2 exp(2 (lnD_j - max lnD)), new scales ln D'_k = ln|R_kk| + lnD_{p_k}).
+// Outputs match the unblocked kernel (logical column order): QR = Rt on/above the diagonal and
+// v_k below it, tau, perm, lnD', sgnU, plus the panels' WY triangles S for the formation of Q.
+#include <cfloat>
+
+#include "slmc_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = 8;
+constexpr int kCT = 8;   // trailing columns per warp group
+constexpr int kRC = 2;   // row chunks (of 32 rows) per lane in the rank-BP update
+
+template <int BP>
+struct QrSmem {
+    static size_t bytes(int N) {
+        return sizeof(double) * ((size_t)N * (BP + 1) + BP * BP + kWarps * BP * kCT + 4 * (size_t)N + 2 * BP) +
+               sizeof(int) * (size_t)N;
+    }
+};
+
+// Rank-BP update of columns [j_begin, N) rows [p, N) of the column-major matrix A (column j
+// stored at col(j)): A <- (I - V op(S) V^T) A, op(S) = S^T for the QR trailing update
+// (Q_p^T A) and S for the backward formation of Q (Q_p A). V is the clean panel in shared
+// memory (rows p..N-1, unit diagonal, zeros above), row stride BP+1.
+template <int BP, bool TRANS, typename ColFn>
+__device__ __forceinline__ void wy_update(const double* __restrict__ Vp, const double* __restrict__ Ssm,
+                                          double* __restrict__ Wsm, int N, int p, int nb, int j_begin, ColFn col) {
+    constexpr int BPS = BP + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* W = Wsm + warp * BP * kCT;
+    const int ncols = N - j_begin;
+    for (int g = warp * kCT; g < ncols; g += kWarps * kCT) {
+        double* cptr[kCT];
+#pragma unroll
+        for (int c = 0; c < kCT; ++c) cptr[c] = (j_begin + g + c < N) ? col(j_begin + g + c) : nullptr;
+        // W[m][c] = sum_r V[r][m] A[r][c]: lane (m, h) owns reflector m = lane % BP and the
+        // CPL columns of half h = lane / BP (A rows are broadcast to the warp)
+        constexpr int CPL = kCT * BP / 32;
+        const int m = lane % BP, h = lane / BP;
+        double* mine[CPL];
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) mine[cc] = (h == 0) ? cptr[cc] : cptr[(CPL < kCT ? CPL : 0) + cc];
+        double acc[CPL];
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) acc[cc] = 0.0;
+        for (int r = p; r < N; ++r) {
+            const double v = Vp[r * BPS + m];
+#pragma unroll
+            for (int cc = 0; cc < CPL; ++cc)
+                if (mine[cc]) acc[cc] = fma(v, mine[cc][r], acc[cc]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) W[m * kCT + h * CPL + cc] = (m < nb) ? acc[cc] : 0.0;
+        __syncwarp();
+        // W' = op(S) W   (same lane ownership)
+        double w2[CPL];
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) w2[cc] = 0.0;
+        if (m < nb) {
+            if (TRANS) {
+                for (int q = 0; q <= m; ++q) {
+                    const double sv = Ssm[q * BP + m];
+#pragma unroll
+                    for (int cc = 0; cc < CPL; ++cc) w2[cc] = fma(sv, W[q * kCT + h * CPL + cc], w2[cc]);
+                }
+            } else {
+                for (int q = m; q < nb; ++q) {
+                    const double sv = Ssm[m * BP + q];
+#pragma unroll
+                    for (int cc = 0; cc < CPL; ++cc) w2[cc] = fma(sv, W[q * kCT + h * CPL + cc], w2[cc]);
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) W[m * kCT + h * CPL + cc] = w2[cc];
+        __syncwarp();
+        // A[r][c] -= sum_m V[r][m] W'[m][c]   (lanes over rows)
+        for (int r0 = p; r0 < N; r0 += 32 * kRC) {
+            double y[kRC][kCT];
+#pragma unroll
+            for (int q = 0; q < kRC; ++q) {
+                const int r = r0 + lane + 32 * q;
+#pragma unroll
+                for (int c = 0; c < kCT; ++c) y[q][c] = (r < N && cptr[c]) ? cptr[c][r] : 0.0;
+            }
+            for (int mm = 0; mm < nb; ++mm) {
+                double wv[kCT];
+#pragma unroll
+                for (int c = 0; c < kCT; ++c) wv[c] = W[mm * kCT + c];
+#pragma unroll
+                for (int q = 0; q < kRC; ++q) {
+                    const int r = r0 + lane + 32 * q;
+                    const double v = (r < N) ? Vp[r * BPS + mm] : 0.0;
+#pragma unroll
+                    for (int c = 0; c < kCT; ++c) y[q][c] = fma(-v, wv[c], y[q][c]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kRC; ++q) {
+                const int r = r0 + lane + 32 * q;
+                if (r < N) {
+#pragma unroll
+                    for (int c = 0; c < kCT; ++c)
+                        if (cptr[c]) cptr[c][r] = y[q][c];
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int BP>
+__global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, double* __restrict__ lnD_all,
+                                                  double* __restrict__ QRall, double* __restrict__ tau_all,
+                                                  int* __restrict__ perm_all, int* __restrict__ sgnU,
+                                                  double* __restrict__ Sall, unsigned int* __restrict__ err, int N) {
+    constexpr int BPS = BP + 1;
+    const int f = blockIdx.x;
+    const size_t NN = (size_t)N * N;
+    double* __restrict__ Y = Yall + f * NN;
+    double* __restrict__ QR = QRall + f * NN;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* Vp = reinterpret_cast<double*>(smraw);
+    double* Ssm = Vp + (size_t)N * BPS;
+    double* Wsm = Ssm + BP * BP;
+    double* s_key = Wsm + kWarps * BP * kCT;
+    double* s_lnd = s_key + N;
+    double* s_lnDn = s_lnd + N;
+    double* s_g = s_lnDn + N;
+    double* s_tau = s_g + N;
+    double* s_beta = s_tau + BP;
+    int* s_perm = reinterpret_cast<int*>(s_beta + BP);
+    __shared__ double s_mx;
+    __shared__ int s_ntriv, s_wide;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // ---- scaled column norms and the pre-pivoting order ----
+    for (int j = tid; j < N; j += kThreads) s_lnd[j] = lnD_all[(size_t)f * N + j];
+    if (tid == 0) {
+        s_ntriv = 0;
+        s_wide = 0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double mx = -DBL_MAX;
+        for (int j = lane; j < N; j += 32) mx = fmax(mx, s_lnd[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_mx = mx;
+    }
+    __syncthreads();
+    for (int j = warp; j < N; j += kWarps) {
+        double a = 0.0;
+        for (int i = lane; i < N; i += 32) {
+            const double y = Y[(size_t)j * N + i];
+            a = fma(y, y, a);
+        }
+        a = slmc::warp_allsum(a);
+        if (lane == 0) {
+            const double key = a * exp(2.0 * (s_lnd[j] - s_mx));
+            s_key[j] = (key >= 0.0) ? key : -1.0;  // NaN sorts last and keeps ranks unique
+        }
+    }
+    __syncthreads();
+    for (int j = tid; j < N; j += kThreads) {
+        const double kj = s_key[j];
+        int r = 0;
+        for (int i = 0; i < N; ++i) {
+            const double ki = s_key[i];
+            r += (ki > kj) || (ki == kj && i < j);
+        }
+        s_perm[r] = j;
+    }
+    __syncthreads();
+    for (int k = tid; k < N; k += kThreads)
+        if (fabs(s_lnd[k]) > 600.0) s_wide = 1;
+
+    // ---- panels ----
+    for (int p = 0; p < N; p += BP) {
+        const int nb = min(BP, N - p);
+        __syncthreads();
+        for (int idx = tid; idx < nb * (N - p); idx += kThreads) {
+            const int c = idx / (N - p), rr = idx - c * (N - p);
+            Vp[(p + rr) * BPS + c] = Y[(size_t)s_perm[p + c] * N + p + rr];
+        }
+        __syncthreads();
+        // unblocked Householder on the panel (shared memory)
+        for (int c = 0; c < nb; ++c) {
+            const int k = p + c;
+            if (warp == 0) {
+                const double alpha = Vp[k * BPS + c];
+                double sig = 0.0;
+                for (int r = k + 1 + lane; r < N; r += 32) {
+                    const double v = Vp[r * BPS + c];
+                    sig = fma(v, v, sig);
+                }
+                sig = slmc::warp_allsum(sig);
+                double tau = 0.0, beta = alpha, scal = 0.0;
+                if (sig != 0.0) {
+                    const double nrm = sqrt(fma(alpha, alpha, sig));
+                    beta = (alpha >= 0.0) ? -nrm : nrm;
+                    tau = (beta - alpha) / beta;
+                    scal = 1.0 / (alpha - beta);
+                }
+                for (int r = k + 1 + lane; r < N; r += 32) Vp[r * BPS + c] *= scal;
+                if (lane == 0) {
+                    s_tau[c] = tau;
+                    s_beta[c] = beta;
+                    tau_all[(size_t)f * N + k] = tau;
+                    if (tau != 0.0) s_ntriv += 1;
+                }
+            }
+            __syncthreads();
+            const double tau = s_tau[c];
+            if (tau != 0.0) {
+                for (int c2 = c + 1 + warp; c2 < nb; c2 += kWarps) {
+                    double d = (lane == 0) ? Vp[k * BPS + c2] : 0.0;  // v_k[k] = 1
+                    for (int r = k + 1 + lane; r < N; r += 32) d = fma(Vp[r * BPS + c], Vp[r * BPS + c2], d);
+                    d = slmc::warp_allsum(d) * tau;
+                    if (lane == 0) Vp[k * BPS + c2] -= d;
+                    for (int r = k + 1 + lane; r < N; r += 32) Vp[r * BPS + c2] = fma(-d, Vp[r * BPS + c], Vp[r * BPS + c2]);
+                }
+            }
+            __syncthreads();
+        }
+        // new scales of this panel's rows
+        if (tid < nb) {
+            const int k = p + tid;
+            const double l = log(fabs(s_beta[tid])) + s_lnd[s_perm[k]];
+            s_lnDn[k] = l;
+            s_g[k] = exp(-l);
+            if (fabs(l) > 600.0) s_wide = 1;
+        }
+        __syncthreads();
+        // write logical columns p..p+nb-1 of the packed output (Rt above, v below)
+        const bool wide = s_wide != 0;
+        for (int c = warp; c < nb; c += kWarps) {
+            const int k = p + c;
+            const int pc = s_perm[k];
+            const double lk = s_lnd[pc];
+            const double ek = wide ? 0.0 : exp(lk);
+            for (int i = lane; i < N; i += 32) {
+                double o;
+                if (i < k) {
+                    const double rv = (i < p) ? Y[(size_t)pc * N + i] : Vp[i * BPS + c];
+                    o = wide ? rv * exp(lk - s_lnDn[i]) : rv * ek * s_g[i];
+                } else if (i == k) {
+                    o = (s_beta[c] >= 0.0) ? 1.0 : -1.0;
+                } else {
+                    o = Vp[i * BPS + c];
+                }
+                QR[(size_t)k * N + i] = o;
+            }
+        }
+        __syncthreads();
+        // clean V (unit diagonal, zeros above) and the Gram matrix G = V^T V in Wsm
+        for (int idx = tid; idx < nb * nb; idx += kThreads) {
+            const int a = idx / nb, c = idx - a * nb;  // Vp row p+a, column c
+            if (a < c) Vp[(p + a) * BPS + c] = 0.0;
+            else if (a == c) Vp[(p + a) * BPS + c] = 1.0;
+        }
+        __syncthreads();
+        double* G = Wsm;  // [BP][BP]
+        for (int pr = warp; pr < nb * nb; pr += kWarps) {
+            const int a = pr / nb, c = pr - a * nb;
+            if (a >= c) continue;
+            double d = 0.0;
+            for (int r = p + c + lane; r < N; r += 32) d = fma(Vp[r * BPS + a], Vp[r * BPS + c], d);
+            d = slmc::warp_allsum(d);
+            if (lane == 0) G[a * BP + c] = d;
+        }
+        __syncthreads();
+        // S: S_cc = tau_c, S[0:c, c] = -tau_c S[0:c, 0:c] G[0:c, c]  (one warp, lane = row)
+        if (warp == 0) {
+            for (int c = 0; c < nb; ++c) {
+                const double tc = s_tau[c];
+                double v = 0.0;
+                if (lane < c) {
+                    for (int q = lane; q < c; ++q) v = fma(Ssm[lane * BP + q], G[q * BP + c], v);
+                    v = -tc * v;
+                } else if (lane == c) {
+                    v = tc;
+                }
+                if (lane < BP) Ssm[lane * BP + c] = (lane <= c) ? v : 0.0;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < nb * BP; idx += kThreads) {
+            const int a = idx / BP, b = idx - a * BP;
+            Sall[(size_t)f * N * BP + (size_t)(p + a) * BP + b] = (b < nb) ? Ssm[a * BP + b] : 0.0;
+        }
+        // trailing update C <- Q_p^T C on logical columns p+nb..N-1
+        wy_update<BP, true>(Vp, Ssm, Wsm, N, p, nb, p + nb, [&](int j) { return Y + (size_t)s_perm[j] * N; });
+    }
+    __syncthreads();
+    bool bad = false;
+    for (int k = tid; k < N; k += kThreads) {
+        lnD_all[(size_t)f * N + k] = s_lnDn[k];
+        perm_all[(size_t)f * N + k] = s_perm[k];
+        bad |= !isfinite(s_lnDn[k]);
+    }
+    if (tid == 0) sgnU[f] = (s_ntriv & 1) ? -1 : 1;
+    if (bad) atomicOr(err, SLMC_EBIT_NONFINITE);
+}
+
+// Q = Q_0 Q_1 ... (Q_p = I - V_p S_p V_p^T), accumulated backwards into U (column-major).
+template <int BP>
+__global__ void __launch_bounds__(kThreads, 2) k_formq_b(const double* __restrict__ QRall, const double* __restrict__ Sall,
+                                                      double* __restrict__ Uall, int N) {
+    constexpr int BPS = BP + 1;
+    const int f = blockIdx.x;
+    const size_t NN = (size_t)N * N;
+    const double* __restrict__ QR = QRall + f * NN;
+    double* __restrict__ U = Uall + f * NN;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* Vp = reinterpret_cast<double*>(smraw);
+    double* Ssm = Vp + (size_t)N * BPS;
+    double* Wsm = Ssm + BP * BP;
+    const int tid = threadIdx.x;
+    for (size_t idx = tid; idx < NN; idx += kThreads) U[idx] = (idx % (N + 1) == 0) ? 1.0 : 0.0;
+    for (int p = ((N - 1) / BP) * BP; p >= 0; p -= BP) {
+        const int nb = min(BP, N - p);
+        __syncthreads();
+        for (int idx = tid; idx < nb * (N - p); idx += kThreads) {
+            const int c = idx / (N - p), r = p + idx - c * (N - p);
+            const int k = p + c;
+            Vp[r * BPS + c] = (r > k) ? QR[(size_t)k * N + r] : (r == k ? 1.0 : 0.0);
+        }
+        for (int idx = tid; idx < nb * BP; idx += kThreads) {
+            const int a = idx / BP, b = idx - a * BP;
+            Ssm[a * BP + b] = Sall[(size_t)f * N * BP + (size_t)(p + a) * BP + b];
+        }
+        __syncthreads();
+        wy_update<BP, false>(Vp, Ssm, Wsm, N, p, nb, p, [&](int j) { return U + (size_t)j * N; });
+    }
+}
+
+// T_new = Rt P^T T_old, T row-major: T_new[i][j] = sum_{k >= i} Rt[i][k] T_old[perm[k]][j].
+// 64x64 output tile per CTA, 4x4 per thread, K chunks of 16 staged in shared memory; chunks
+// entirely below the diagonal of Rt are skipped.
+__global__ void __launch_bounds__(256) k_tupd(const double* __restrict__ QRall, const double* __restrict__ Told,
+                                              const int* __restrict__ perm_all, double* __restrict__ Tnew, int N) {
+    constexpr int TM = 64, TK = 16;
+    __shared__ double As[TK][TM + 4];
+    __shared__ double Bs[TK][TM + 4];
+    const int f = blockIdx.z;
+    const size_t NN = (size_t)N * N;
+    const double* __restrict__ A = QRall + f * NN;
+    const double* __restrict__ B = Told + f * NN;
+    const int* __restrict__ perm = perm_all + (size_t)f * N;
+    const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TM;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int k0 = (i0 / TK) * TK; k0 < N; k0 += TK) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < TK * TM; idx += 256) {
+            const int kk = idx / TM, ii = idx - kk * TM;
+            const int k = k0 + kk, i = i0 + ii, j = j0 + ii;
+            As[kk][ii] = (k < N && i < N && k >= i) ? A[(size_t)k * N + i] : 0.0;
+            Bs[kk][ii] = (k < N && j < N) ? B[(size_t)perm[k] * N + j] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = As[kk][ty * 4 + q];
+                b[q] = Bs[kk][tx * 4 + q];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const int i = i0 + ty * 4 + x;
+        if (i >= N) continue;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int j = j0 + tx * 4 + y;
+            if (j < N) Tnew[f * NN + (size_t)i * N + j] = acc[x][y];
+        }
+    }
+}
+
+template <int BP>
+cudaError_t launch_qrb(slmc_ctx* c, int nf, cudaStream_t s) {
+    const size_t smem = QrSmem<BP>::bytes(c->N);
+    cudaError_t e = cudaFuncSetAttribute(k_qrb<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_qrb<BP><<<nf, kThreads, smem, s>>>(c->Y, c->lnD, c->QR, c->tau, c->perm, c->sgnU, c->Sws, c->err, c->N);
+    return cudaGetLastError();
+}
+
+template <int BP>
+cudaError_t launch_formq_b(slmc_ctx* c, int nf, cudaStream_t s) {
+    const size_t smem = sizeof(double) * ((size_t)c->N * (BP + 1) + BP * BP + kWarps * BP * kCT);
+    cudaError_t e = cudaFuncSetAttribute(k_formq_b<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_formq_b<BP><<<nf, kThreads, smem, s>>>(c->QR, c->Sws, c->U, c->N);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace slmc {
+
+int qr_panel_width(int N) { return N <= 256 ? 32 : 16; }
+
+cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s) {
+    return qr_panel_width(c->N) == 32 ? launch_qrb<32>(c, nf, s) : launch_qrb<16>(c, nf, s);
+}
+
+cudaError_t form_q_blocked(slmc_ctx* c, int nf, cudaStream_t s) {
+    return qr_panel_width(c->N) == 32 ? launch_formq_b<32>(c, nf, s) : launch_formq_b<16>(c, nf, s);
+}
+
+cudaError_t t_update_tiled(slmc_ctx* c, int nf, cudaStream_t s) {
+    const int nt = (c->N + 63) / 64;
+    dim3 grid(nt, nt, nf);
+    k_tupd<<<grid, 256, 0, s>>>(c->QR, c->Ta, c->perm, c->Tb, c->N);
+    double* t = c->Ta;
+    c->Ta = c->Tb;
+    c->Tb = t;
+    return cudaGetLastError();
+}
+
+}  // namespace slmc

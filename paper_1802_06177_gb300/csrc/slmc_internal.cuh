@@ -27,13 +27,14 @@ struct slmc_ctx {
     double* Y;       // slice-group product; reused for M in the final step
     double* QR;      // packed pivoted-QR output; reused for G in the cumulative update
     double* U;       // orthogonal factor
-    double* Ta;      // T factor (ping)
-    double* Tb;      // T factor (pong)
+    double* Ta;      // T factor (ping), row-major
+    double* Tb;      // T factor (pong), row-major
     double* lnD;     // [max_fields][N] ln of the D scales
     double* tau;     // [max_fields][N] Householder coefficients
     int* perm;       // [max_fields][N] column permutation of the last QR
     int* piv;        // [max_fields][N] LU row pivots
     int* sgnU;       // [max_fields] det(U) = +-1
+    double* Sws;     // [max_fields][N][32] WY triangles of the blocked QR panels
     // Chain workspace.
     double* x_old;   // [max_fields][N][L]
     double* scal;    // [max_fields][8] scratch scalars per chain
@@ -100,7 +101,10 @@ namespace slmc {
 cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s);
 cudaError_t slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s);
 cudaError_t tc_slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s);
-cudaError_t t_update(slmc_ctx* c, int nf, cudaStream_t s);
+cudaError_t t_update_tiled(slmc_ctx* c, int nf, cudaStream_t s);
+cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s);
+cudaError_t form_q_blocked(slmc_ctx* c, int nf, cudaStream_t s);
+int qr_panel_width(int N);
 cudaError_t qr_pivoted(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t form_q(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t set_identity(slmc_ctx* c, int nf, cudaStream_t s);

@@ -26,7 +26,9 @@ class Params(ctypes.Structure):
     _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("L", ctypes.c_int), ("dtau", ctypes.c_double),
                 ("t", ctypes.c_double), ("mu", ctypes.c_double), ("omega0", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("n_s", ctypes.c_int), ("precision", ctypes.c_int),
-                ("sweep_delta", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("sweep_delta", ctypes.c_double), ("seed", ctypes.c_uint64), ("qr_mode", ctypes.c_int)]
+
+QR_MODE = {"prepivot": 0, "pivoted": 1}
 
 
 EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", "slmc_logdet", "slmc_greens",
@@ -100,7 +102,7 @@ class Context:
     """One libslmc context (model parameters, exp(-dtau K), workspace) on one CUDA device."""
 
     def __init__(self, Lx, Ly, L, dtau=0.1, t=1.0, mu=0.0, omega0=1.0, lam=1.0, n_s=10, precision="fp64",
-                 sweep_delta=0.5, seed=0, max_fields=64, device=None):
+                 sweep_delta=0.5, seed=0, max_fields=64, device=None, qr_mode="prepivot"):
         self.lib = load_library()
         dev = torch.device("cuda") if device is None else torch.device(device)
         self.device = torch.device("cuda", torch.cuda.current_device() if dev.index is None else dev.index)
@@ -109,7 +111,7 @@ class Context:
         self.dtau, self.lam, self.omega0, self.n_s = dtau, lam, omega0, n_s
         self.precision = precision
         self.params = Params(Lx, Ly, L, dtau, t, mu, omega0, lam, n_s, PRECISION[precision], sweep_delta,
-                             seed & ((1 << 64) - 1))
+                             seed & ((1 << 64) - 1), QR_MODE[qr_mode])
         self._ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             self._check("slmc_init", self.lib.slmc_init(ctypes.byref(self.params), max_fields,
@@ -244,12 +246,12 @@ class Context:
 
 
 def logdet_noalloc(x, Lx, Ly, L, dtau=0.1, t=1.0, mu=0.0, omega0=1.0, lam=1.0, n_s=10, precision="fp64",
-                   lndet=None, sign=None):
+                   lndet=None, sign=None, qr_mode="prepivot"):
     """slmc_logdet_noalloc: ln|det| and sign of fields x[n, N, L] without a context and
     without any device allocation inside the library (its workspace is a fixed 16 MiB
     device array). Outputs may be passed in preallocated; errors show as NaN / sign 0."""
     lib = load_library()
-    p = Params(Lx, Ly, L, dtau, t, mu, omega0, lam, n_s, PRECISION[precision], 0.0, 0)
+    p = Params(Lx, Ly, L, dtau, t, mu, omega0, lam, n_s, PRECISION[precision], 0.0, 0, QR_MODE[qr_mode])
     n = x.shape[0]
     lndet = torch.empty(n, dtype=torch.float64, device=x.device) if lndet is None else lndet
     sign = torch.empty(n, dtype=torch.int32, device=x.device) if sign is None else sign

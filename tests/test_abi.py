@@ -65,6 +65,7 @@ def test_init_rejects_bad_params_on_host(lib_path):
 
 def test_params_struct_layout_matches_header():
     from paper_1802_06177_gb300.slmc import Params
-    # int Lx, Ly, L; pad; 5 doubles; int n_s, precision; double sweep_delta; uint64 seed
-    assert ctypes.sizeof(Params) == 12 + 4 + 5 * 8 + 8 + 8 + 8
+    # int Lx, Ly, L; pad; 5 doubles; int n_s, precision; double sweep_delta; uint64 seed; int qr_mode; pad
+    assert ctypes.sizeof(Params) == 12 + 4 + 5 * 8 + 8 + 8 + 8 + 8
     assert Params.dtau.offset == 16 and Params.n_s.offset == 56 and Params.seed.offset == 72
+    assert Params.qr_mode.offset == 80

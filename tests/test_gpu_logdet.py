@@ -165,3 +165,19 @@ def test_nonfinite_field_is_reported():
     assert np.isnan(lndet[1].item()) and sign[1].item() == 0
     assert np.isfinite(lndet[0].item()) and sign[0].item() == 1
     ctx.get_error()  # cleared
+
+
+@pytest.mark.parametrize("qr_mode", ["prepivot", "pivoted"])
+@pytest.mark.parametrize("Lx,Ly,L,n_s,nf", [(4, 4, 40, 10, 8), (6, 4, 37, 8, 4), (10, 10, 30, 7, 3),
+                                            (18, 18, 36, 9, 2), (24, 24, 48, 8, 1)])
+def test_both_qr_modes(qr_mode, Lx, Ly, L, n_s, nf):
+    # N = 324 and 576 use 16-column panels in the blocked QR; N <= 256 uses 32
+    x = inputs.mixed_fields(nf, Lx, Ly, L, seed=77 + L)
+    ctx = make_ctx(Lx, L, n_s, Ly=Ly, max_fields=nf, qr_mode=qr_mode)
+    G, lndet, sign = ctx.greens(cuda(x))
+    torch.cuda.synchronize()
+    ctx.get_error()
+    l_ref, s_ref, G_ref = oracle_many(HolsteinParams(Lx, Ly, L, n_s=n_s), x)
+    assert np.abs(lndet.cpu().numpy() - l_ref).max() <= TOL_LNDET_FP64
+    assert np.array_equal(sign.cpu().numpy(), s_ref)
+    assert np.abs(G.cpu().numpy() - G_ref).max() <= TOL_G_FP64
