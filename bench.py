@@ -347,6 +347,14 @@ def run_gpu(args):
     lndets[args.precision] = ctx.logdet(xs)[0].cpu().numpy()
     ctx.close()
     fp64_value = None
+    for extra in ([] if args.no_fp64 else ["tf32x3", "bf16x9"]):
+        if extra == args.precision:
+            continue
+        ce = make(extra)
+        ms_e, _, _, _ = timed(ce, {"x": x0.clone()}, 1, 1, 0)
+        rates[extra] = nf * world / (ms_e / 1e3)
+        lndets[extra] = ce.logdet(xs)[0].cpu().numpy()
+        ce.close()
     if not args.no_fp64 and args.precision != "fp64":
         c64 = make("fp64")
         ms64, _, _, _ = timed(c64, {"x": x0.clone()}, 1, 1, 0)

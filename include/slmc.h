@@ -107,7 +107,8 @@ SLMC_API int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out);
 SLMC_API int slmc_destroy(slmc_ctx* ctx);
 
 /* Synchronises `stream`, returns and clears the sticky device-side error of the context
- * (SLMC_OK, SLMC_ERR_NONFINITE or SLMC_ERR_SINGULAR), or SLMC_ERR_CUDA if a kernel failed. */
+ * (SLMC_OK, SLMC_ERR_NONFINITE, SLMC_ERR_SINGULAR, or SLMC_ERR_TIMEOUT if a bounded wait of the
+ * tensor-core pipeline gave up), or SLMC_ERR_CUDA if a kernel failed. */
 SLMC_API int slmc_get_error(slmc_ctx* ctx, void* stream);
 
 /* ln|det(I + B_L ... B_1)| and its sign for n fields, one spin species

@@ -100,10 +100,11 @@ int* iscal(slmc_ctx* c, int col) { return c->iscal + (size_t)col * c->max_fields
 // Stabilised UDT chain + final LU for fields [0, nf) of one batch (nf <= max_fields).
 int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, double* G, cudaStream_t s) {
     SLMC_LAUNCH(SLMC_PROF_FINAL, 1, s, slmc::set_identity(c, nf, s));
+    if (c->p.precision != SLMC_PREC_FP64) SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_scales(c, x, nf, s));
     for (int l0 = 0; l0 < c->L; l0 += c->p.n_s) {
         const int nsl = std::min(c->p.n_s, c->L - l0);
         if (c->p.precision == SLMC_PREC_TF32X3 || c->p.precision == SLMC_PREC_BF16X9)
-            SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::tc_slice_group(c, x, nf, l0, nsl, s));
+            SLMC_LAUNCH(SLMC_PROF_SLICE, slmc::tc_launches(nsl), s, slmc::tc_slice_group(c, x, nf, l0, nsl, s));
         else
             SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_group(c, x, nf, l0, nsl, s));
         if (c->p.qr_mode == SLMC_QR_PIVOTED) {
@@ -132,8 +133,9 @@ int for_batches(slmc_ctx* c, int n, F&& fn) {
 void free_ctx(slmc_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
-    void* bufs[] = {c->E64, c->F32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->Ta, c->Tb, c->lnD, c->tau,
-                    c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err};
+    void* bufs[] = {c->E64, c->F32, c->F32lo, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->Ta, c->Tb, c->lnD, c->tau,
+                    c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err,
+                    c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -171,7 +173,6 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     *out = nullptr;
     SLMC_TRY(validate(p));
     if (max_fields < 1 || max_fields > kMaxGridY) return SLMC_ERR_ARG;
-    if (p->precision == SLMC_PREC_TF32X3 || p->precision == SLMC_PREC_BF16X9) return SLMC_ERR_UNSUPPORTED;
     slmc_ctx* c = new (std::nothrow) slmc_ctx();
     if (!c) return SLMC_ERR_NOMEM;
     c->p = *p;
@@ -190,6 +191,8 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     };
     alloc(&c->E64, NN * sizeof(double));
     alloc(&c->F32, NN * sizeof(float));
+    alloc(&c->F32lo, NN * sizeof(float));
+    if (p->precision != SLMC_PREC_FP64) alloc(&c->sc32, F * L * N * sizeof(float));
     if (p->precision == SLMC_PREC_TF32X3) alloc(&c->Ftf, 2 * NN * sizeof(uint32_t));
     if (p->precision == SLMC_PREC_BF16X9) alloc(&c->Fbf, 3 * NN * sizeof(uint16_t));
     alloc(&c->Y, F * NN * sizeof(double));
@@ -209,13 +212,27 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     alloc(&c->feat, 8 * F * sizeof(double));
     alloc(&c->fitR, 64 * sizeof(double));
     alloc(&c->err, sizeof(unsigned int));
+    const bool tc = p->precision == SLMC_PREC_TF32X3 || p->precision == SLMC_PREC_BF16X9;
+    if (tc) {
+        size_t es = 0;
+        int np = 0;
+        slmc::tc_geometry(c->N, p->precision, &c->tc_npad, &c->tc_nt, &es, &np);
+        const size_t Np = c->tc_npad;
+        alloc(&c->tc_F, np * Np * Np * es);
+        for (int b = 0; b < 2; ++b) {
+            alloc(&c->tc_p[b], np * F * N * Np * es);
+            alloc(&c->tc_y32[b], F * NN * sizeof(float));
+            if (ok && cudaMemset(c->tc_p[b], 0, np * F * N * Np * es) != cudaSuccess) ok = false;
+        }
+    }
     if (!ok) {
         cudaGetLastError();
         free_ctx(c);
         return SLMC_ERR_NOMEM;
     }
     if (cudaMemset(c->err, 0, sizeof(unsigned int)) != cudaSuccess ||
-        slmc::build_hopping_exp(c, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        slmc::build_hopping_exp(c, nullptr) != cudaSuccess || (tc && slmc::tc_init(c, nullptr) != cudaSuccess) ||
+        cudaDeviceSynchronize() != cudaSuccess) {
         free_ctx(c);
         return SLMC_ERR_CUDA;
     }
@@ -237,6 +254,7 @@ int slmc_get_error(slmc_ctx* c, void* stream) {
     unsigned int bits = 0;
     if (cudaMemcpy(&bits, c->err, sizeof(bits), cudaMemcpyDeviceToHost) != cudaSuccess) return SLMC_ERR_CUDA;
     if (bits && cudaMemset(c->err, 0, sizeof(bits)) != cudaSuccess) return SLMC_ERR_CUDA;
+    if (bits & SLMC_EBIT_TIMEOUT) return SLMC_ERR_TIMEOUT;
     if (bits & SLMC_EBIT_SINGULAR) return SLMC_ERR_SINGULAR;
     if (bits & SLMC_EBIT_NONFINITE) return SLMC_ERR_NONFINITE;
     return SLMC_OK;

@@ -35,14 +35,15 @@ __device__ __forceinline__ uint32_t to_tf32(float v) {
     return r;
 }
 
-__global__ void k_split_F(const double* __restrict__ E, float* __restrict__ F32, uint32_t* __restrict__ Ftf,
-                          uint16_t* __restrict__ Fbf, int N) {
+__global__ void k_split_F(const double* __restrict__ E, float* __restrict__ F32, float* __restrict__ F32lo,
+                          uint32_t* __restrict__ Ftf, uint16_t* __restrict__ Fbf, int N) {
     const int NN = N * N;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= NN) return;
     const double fd = E[idx] - ((idx % (N + 1) == 0) ? 1.0 : 0.0);
     const float v = (float)fd;
     F32[idx] = v;
+    if (F32lo) F32lo[idx] = (float)(fd - (double)v);
     if (Ftf) {
         const uint32_t hi = to_tf32(v);
         const uint32_t lo = to_tf32(v - __uint_as_float(hi));
@@ -69,7 +70,7 @@ cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s) {
     const int N = c->N;
     const int NN = N * N;
     k_hopping_exp<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->p.Lx, c->p.Ly, c->p.dtau, c->p.t, c->p.mu);
-    k_split_F<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->F32, c->Ftf, c->Fbf, N);
+    k_split_F<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->F32, c->F32lo, c->Ftf, c->Fbf, N);
     return cudaGetLastError();
 }
 

@@ -132,6 +132,121 @@ cudaError_t dispatch_panel(const T* A, size_t a_stride, const double* B, const i
     }
 }
 
+
+// Reduced-precision (FP32 SIMT) slice group, accuracy-preserving form. Each slice computes
+//   Y' = D_l (Y + F Y),  F = F_hi + F_lo (two FP32 terms of E - I),
+// with the products of one block of 32 k accumulated in FP32 and the block sums combined by
+// TwoSum (Knuth) into a compensated pair, so small far-field contributions are not rounded
+// away against the large running sum; the F_lo term is accumulated separately. Thread t owns
+// output rows t, t+256, ... and all NB columns of the CTA's panel (F is read once per CTA and
+// slice); the panel sits in shared memory k-major, so four columns arrive per 128-bit load.
+template <int RPT, int NB>
+__global__ void __launch_bounds__(256) k_slice_f32(const float* __restrict__ Fhi, const float* __restrict__ Flo,
+                                                   const double* __restrict__ U, double* __restrict__ out,
+                                                   const float* __restrict__ sc32, int N, int L, int l0, int nsl) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* P0 = reinterpret_cast<float*>(smem_raw);  // [N][NB]
+    float* P1 = P0 + (size_t)N * NB;
+    const int f = blockIdx.y, j0 = blockIdx.x * NB, tid = threadIdx.x;
+    const size_t NN = (size_t)N * N;
+    for (int idx = tid; idx < NB * N; idx += 256) {
+        const int jj = idx / N, k = idx - jj * N, j = j0 + jj;
+        P0[k * NB + jj] = (j < N) ? (float)U[(size_t)f * NN + (size_t)j * N + k] : 0.f;
+    }
+    float* Pin = P0;
+    float* Pout = P1;
+    for (int s = 0; s < nsl; ++s) {
+        __syncthreads();
+        float hi[RPT][NB], cp[RPT][NB], blk[RPT][NB], lo[RPT][NB];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int c = 0; c < NB; ++c) hi[r][c] = cp[r][c] = blk[r][c] = lo[r][c] = 0.f;
+        for (int k0 = 0; k0 < N; k0 += 32) {
+            const int k1 = min(N, k0 + 32);
+            for (int k = k0; k < k1; ++k) {
+                float pv[NB];
+#pragma unroll
+                for (int c = 0; c < NB; c += 4) {
+                    const float4 q = *reinterpret_cast<const float4*>(Pin + k * NB + c);
+                    pv[c] = q.x;
+                    pv[c + 1] = q.y;
+                    pv[c + 2] = q.z;
+                    pv[c + 3] = q.w;
+                }
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int i = tid + 256 * r;
+                    const float ah = (i < N) ? __ldg(Fhi + (size_t)k * N + i) : 0.f;
+                    const float al = (i < N) ? __ldg(Flo + (size_t)k * N + i) : 0.f;
+#pragma unroll
+                    for (int c = 0; c < NB; ++c) {
+                        blk[r][c] = fmaf(ah, pv[c], blk[r][c]);
+                        lo[r][c] = fmaf(al, pv[c], lo[r][c]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {  // TwoSum(hi, blk) -> hi + error into cp
+                    const float t = __fadd_rn(hi[r][c], blk[r][c]);
+                    const float bp = __fsub_rn(t, hi[r][c]);
+                    const float e = __fadd_rn(__fsub_rn(hi[r][c], __fsub_rn(t, bp)), __fsub_rn(blk[r][c], bp));
+                    cp[r][c] = __fadd_rn(cp[r][c], e);
+                    hi[r][c] = t;
+                    blk[r][c] = 0.f;
+                }
+        }
+        const bool last = (s == nsl - 1);
+        const float* scl = sc32 + ((size_t)f * L + l0 + s) * N;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int i = tid + 256 * r;
+            if (i >= N) continue;
+            const float sc = scl[i];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) {
+                const float fy = __fadd_rn(hi[r][c], __fadd_rn(cp[r][c], lo[r][c]));
+                const float v = __fmul_rn(__fadd_rn(Pin[i * NB + c], fy), sc);
+                if (last) {
+                    if (j0 + c < N) out[(size_t)f * NN + (size_t)(j0 + c) * N + i] = (double)v;
+                } else {
+                    Pout[i * NB + c] = v;
+                }
+            }
+        }
+        float* t = Pin;
+        Pin = Pout;
+        Pout = t;
+    }
+}
+
+template <int RPT, int NB>
+cudaError_t launch_slice_f32(const slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s) {
+    const int N = c->N;
+    const size_t smem = (size_t)2 * N * NB * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_slice_f32<RPT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + NB - 1) / NB, nf);
+    (void)x;
+    k_slice_f32<RPT, NB><<<grid, 256, smem, s>>>(c->F32, c->F32lo, c->U, c->Y, c->sc32, N, c->L, l0, nsl);
+    return cudaGetLastError();
+}
+
+// exp(-dtau lambda x[f][i][l]) in FP64, rounded once to FP32, stored [f][l][i]: the slice
+// scales of the reduced-precision modes (an FP32 exp of an FP32 argument carries a small
+// systematic bias that every slice would repeat).
+__global__ void k_scales(const double* __restrict__ x, float* __restrict__ sc, int N, int L, double dtlam,
+                         size_t total) {
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t f = idx / ((size_t)N * L);
+        const size_t rem = idx - f * N * L;
+        const int i = (int)(rem / L), l = (int)(rem - (size_t)i * L);
+        sc[(f * L + l) * N + i] = (float)exp(-dtlam * x[idx]);
+    }
+}
+
 __global__ void k_identity(double* __restrict__ U, double* __restrict__ T, double* __restrict__ lnD, int N) {
     const int f = blockIdx.y;
     const size_t NN = (size_t)N * N;
@@ -149,9 +264,21 @@ namespace slmc {
 
 cudaError_t slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s) {
     const double dtlam = c->p.dtau * c->p.lambda;
-    if (c->p.precision == SLMC_PREC_FP32)  // F = E - I in FP32, identity added in the epilogue
-        return dispatch_panel<float, false>(c->F32, 0, c->U, nullptr, c->Y, x, c->N, c->L, l0, nsl, dtlam, 1, nf, s);
+    if (c->p.precision == SLMC_PREC_FP32) {  // F = E - I as two FP32 terms, identity added in the epilogue
+        const int rpt = (c->N + 255) / 256;
+        if (rpt == 1) return launch_slice_f32<1, 16>(c, x, nf, l0, nsl, s);
+        if (rpt == 2) return launch_slice_f32<2, 8>(c, x, nf, l0, nsl, s);
+        if (rpt == 3) return launch_slice_f32<3, 8>(c, x, nf, l0, nsl, s);
+        return launch_slice_f32<4, 4>(c, x, nf, l0, nsl, s);
+    }
     return dispatch_panel<double, false>(c->E64, 0, c->U, nullptr, c->Y, x, c->N, c->L, l0, nsl, dtlam, 0, nf, s);
+}
+
+cudaError_t slice_scales(slmc_ctx* c, const double* x, int nf, cudaStream_t s) {
+    const size_t total = (size_t)nf * c->N * c->L;
+    k_scales<<<(unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096), 256, 0, s>>>(
+        x, c->sc32, c->N, c->L, c->p.dtau * c->p.lambda, total);
+    return cudaGetLastError();
 }
 
 cudaError_t set_identity(slmc_ctx* c, int nf, cudaStream_t s) {

@@ -32,10 +32,12 @@ std::mutex g_scratch_mutex;
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Bytes of the per-context part (E, F, error word) and of one field's workspace.
-size_t fixed_bytes(size_t N) { return align256(N * N * sizeof(double)) + align256(N * N * sizeof(float)) + 256; }
-size_t field_bytes(size_t N) {
+size_t fixed_bytes(size_t N) {
+    return align256(N * N * sizeof(double)) + 2 * align256(N * N * sizeof(float)) + 256;
+}
+size_t field_bytes(size_t N, size_t L) {
     return 5 * N * N * sizeof(double) + 32 * N * sizeof(double) + 2 * N * sizeof(double) + 2 * N * sizeof(int) +
-           sizeof(int);
+           sizeof(int) + L * N * sizeof(float);
 }
 
 int scratch_address(int device, unsigned char** out) {
@@ -62,9 +64,10 @@ int slmc_logdet_noalloc(const slmc_params* p, const double* x, int n, double* ln
     if (n < 0 || (n > 0 && (!x || !lndet || !sign))) return SLMC_ERR_ARG;
     if (p->precision != SLMC_PREC_FP64 && p->precision != SLMC_PREC_FP32) return SLMC_ERR_UNSUPPORTED;
     const size_t N = (size_t)p->Lx * p->Ly;
-    if (fixed_bytes(N) + field_bytes(N) > kScratchBytes) return SLMC_ERR_UNSUPPORTED;  // one field must fit
+    const size_t Lz = p->precision == SLMC_PREC_FP32 ? (size_t)p->L : 0;  // slice scales (FP32 mode only)
+    if (fixed_bytes(N) + field_bytes(N, Lz) > kScratchBytes) return SLMC_ERR_UNSUPPORTED;  // one field must fit
     if (n == 0) return SLMC_OK;
-    const int capacity = (int)((kScratchBytes - fixed_bytes(N)) / field_bytes(N));
+    const int capacity = (int)((kScratchBytes - fixed_bytes(N)) / field_bytes(N, Lz));
 
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return SLMC_ERR_CUDA;
@@ -85,6 +88,7 @@ int slmc_logdet_noalloc(const slmc_params* p, const double* x, int n, double* ln
     auto take = [&](size_t bytes) { unsigned char* r = q; q += align256(bytes); return r; };
     c.E64 = reinterpret_cast<double*>(take(NN * sizeof(double)));
     c.F32 = reinterpret_cast<float*>(take(NN * sizeof(float)));
+    c.F32lo = reinterpret_cast<float*>(take(NN * sizeof(float)));
     c.err = reinterpret_cast<unsigned int*>(take(sizeof(unsigned int)));
     c.Y = reinterpret_cast<double*>(q);
     c.QR = c.Y + F * NN;
@@ -97,6 +101,7 @@ int slmc_logdet_noalloc(const slmc_params* p, const double* x, int n, double* ln
     c.perm = reinterpret_cast<int*>(c.tau + F * N);
     c.piv = c.perm + F * N;
     c.sgnU = c.piv + F * N;
+    c.sc32 = Lz ? reinterpret_cast<float*>(c.sgnU + F) : nullptr;
 
     if (cudaMemsetAsync(c.err, 0, sizeof(unsigned int), s) != cudaSuccess) return SLMC_ERR_CUDA;
     if (slmc::build_hopping_exp(&c, s) != cudaSuccess) return SLMC_ERR_CUDA;

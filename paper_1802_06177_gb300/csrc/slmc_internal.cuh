@@ -1,6 +1,7 @@
 // Internal declarations shared by the libslmc translation units (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -11,6 +12,7 @@
 // Device-side sticky error bits (ctx->err).
 #define SLMC_EBIT_NONFINITE 1u
 #define SLMC_EBIT_SINGULAR 2u
+#define SLMC_EBIT_TIMEOUT 4u
 
 #define SLMC_MAX_N 1024
 
@@ -20,6 +22,8 @@ struct slmc_ctx {
     // exp(-dtau K), built on the device from the plane-wave eigenbasis of K.
     double* E64;
     float* F32;      // F = E - I rounded to FP32 (reduced-precision slices use Y + F Y)
+    float* F32lo;    // FP32 rounding residual of F (F ~ F32 + F32lo)
+    float* sc32;     // [max_fields][L][N] slice scales exp(-dtau lambda x), FP64-computed, rounded to FP32
     // tensor-core operand splits of F (filled only in the matching precision modes)
     uint32_t* Ftf;   // [2][N][N] TF32 hi / lo bit patterns
     uint16_t* Fbf;   // [3][N][N] BF16 three-way split
@@ -43,6 +47,14 @@ struct slmc_ctx {
     double* feat;    // [max_fields][8]
     double* fitR;    // [64] Givens-QR state of the regression
     unsigned int* err;
+    // Tensor-core slice path (SLMC_PREC_TF32X3 / BF16X9): operand pieces of F and of the
+    // running slice product (ping/pong), FP32 copies of it, and their TMA descriptors.
+    int tc_npad, tc_nt;
+    void* tc_F;         // [pieces][Npad][Npad]
+    void* tc_p[2];      // [pieces][max_fields * N][Npad]
+    float* tc_y32[2];   // [max_fields][N][N]
+    CUtensorMap tc_mapF;
+    CUtensorMap tc_mapP[2];
     // Launch accounting and optional per-class event timing (host side).
     long long launches;
     bool prof_on;
@@ -101,6 +113,10 @@ namespace slmc {
 cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s);
 cudaError_t slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s);
 cudaError_t tc_slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s);
+cudaError_t tc_init(slmc_ctx* c, cudaStream_t s);
+cudaError_t slice_scales(slmc_ctx* c, const double* x, int nf, cudaStream_t s);
+void tc_geometry(int N, int precision, int* npad, int* nt, size_t* piece_bytes, int* npieces);
+int tc_launches(int nsl);
 cudaError_t t_update_tiled(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t form_q_blocked(slmc_ctx* c, int nf, cudaStream_t s);

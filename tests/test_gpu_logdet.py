@@ -142,15 +142,18 @@ def test_full_size_16x16_L160_sampled():
 TOL_LNDET_MIXED = 5e-5  # |d ln w| = 2 |d ln det| <= 1e-4
 
 
-def test_fp32_slices_meet_mixed_bar():
-    # FP32 slice products as D_l (Y + F Y), F = E - I (FP64 QR / LU): |d ln w| <= 1e-4.
-    x = inputs.mixed_fields(8, 12, 12, 120, seed=21)
-    ctx = make_ctx(12, 120, 10, precision="fp32", max_fields=8)
-    lndet, sign = ctx.logdet(cuda(x))
-    l_ref, s_ref, _ = oracle_many(HolsteinParams(12, 12, 120, n_s=10), x, want_G=False)
+@pytest.mark.parametrize("Lx,L,n_s,nf", [(12, 120, 10, 8), (16, 160, 8, 4), (24, 48, 8, 1), (4, 40, 10, 8)])
+def test_fp32_slices_meet_mixed_bar(Lx, L, n_s, nf):
+    # FP32 slice products as D_l (Y + F Y), F = E - I split into two FP32 terms, block-compensated
+    # accumulation (FP64 QR / LU): |d ln w| <= 1e-4.
+    x = inputs.mixed_fields(max(nf, 2), Lx, Lx, L, seed=21)[:nf]
+    ctx = make_ctx(Lx, L, n_s, precision="fp32", max_fields=nf)
+    G, lndet, sign = ctx.greens(cuda(x))
+    l_ref, s_ref, G_ref = oracle_many(HolsteinParams(Lx, Lx, L, n_s=n_s), x)
     err = np.abs(lndet.cpu().numpy() - l_ref).max()
     assert err <= TOL_LNDET_MIXED, err
     assert np.array_equal(sign.cpu().numpy(), s_ref)
+    assert np.abs(G.cpu().numpy() - G_ref).max() <= 1e-6
 
 
 def test_nonfinite_field_is_reported():
