@@ -112,7 +112,10 @@ int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign,
             SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q(c, nf, s));
         } else {
             SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_blocked(c, nf, s));
-            SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q_blocked(c, nf, s));
+            // Q enters the next reduced-precision slice group (rounded to FP32 there anyway) except
+            // after the last group, where it enters the FP64 final step.
+            const bool q32 = c->p.precision != SLMC_PREC_FP64 && l0 + nsl < c->L;
+            SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q_blocked(c, nf, q32, s));
         }
         SLMC_LAUNCH(SLMC_PROF_TUPDATE, 1, s, slmc::t_update_tiled(c, nf, s));
     }

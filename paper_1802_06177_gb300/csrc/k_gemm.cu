@@ -137,19 +137,59 @@ cudaError_t dispatch_panel(const T* A, size_t a_stride, const double* B, const i
 //   Y' = D_l (Y + F Y),  F = F_hi + F_lo (two FP32 terms of E - I),
 // with the products of one block of 32 k accumulated in FP32 and the block sums combined by
 // TwoSum (Knuth) into a compensated pair, so small far-field contributions are not rounded
-// away against the large running sum; the F_lo term is accumulated separately. Thread t owns
-// output rows t, t+256, ... and all NB columns of the CTA's panel (F is read once per CTA and
-// slice); the panel sits in shared memory k-major, so four columns arrive per 128-bit load.
-template <int RPT, int NB>
-__global__ void __launch_bounds__(256) k_slice_f32(const float* __restrict__ Fhi, const float* __restrict__ Flo,
+// away against the large running sum; the F_lo term is accumulated separately. Thread
+// (row i, column group) owns rows i, i+256, ... and NBT columns of the CTA's panel; the panel
+// sits in shared memory k-major (four columns per 128-bit load) and the rows k0..k0+31 of
+// F_hi and F_lo (contiguous in global memory) are double-buffered into shared memory with
+// cp.async while the previous block is being multiplied.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// rows [k0, k0 + nk) of F_hi and F_lo into Fs[2][KB][N]
+template <int KB>
+__device__ __forceinline__ void stage_F(float* Fs, const float* __restrict__ Fhi, const float* __restrict__ Flo, int N,
+                                        int k0, int nk) {
+    const size_t n = (size_t)nk * N;
+    const float* gh = Fhi + (size_t)k0 * N;
+    const float* gl = Flo + (size_t)k0 * N;
+    float* sl = Fs + (size_t)KB * N;
+    if ((N & 3) == 0) {
+        for (size_t q = threadIdx.x; q < n / 4; q += blockDim.x) {
+            cp_async16(Fs + 4 * q, gh + 4 * q);
+            cp_async16(sl + 4 * q, gl + 4 * q);
+        }
+    } else {
+        for (size_t q = threadIdx.x; q < n; q += blockDim.x) {
+            cp_async4(Fs + q, gh + q);
+            cp_async4(sl + q, gl + q);
+        }
+    }
+}
+
+template <int RPT, int NBT, int KB>
+__global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi, const float* __restrict__ Flo,
                                                    const double* __restrict__ U, double* __restrict__ out,
                                                    const float* __restrict__ sc32, int N, int L, int l0, int nsl) {
+    constexpr int NB = 2 * NBT;  // two column groups of NBT columns; thread = (row, group)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* P0 = reinterpret_cast<float*>(smem_raw);  // [N][NB]
     float* P1 = P0 + (size_t)N * NB;
-    const int f = blockIdx.y, j0 = blockIdx.x * NB, tid = threadIdx.x;
+    float* Fs0 = P1 + (size_t)N * NB;  // two stages of [2][KB][N]
+    float* Fs1 = Fs0 + (size_t)2 * KB * N;
+    const int f = blockIdx.y, j0 = blockIdx.x * NB, tid = threadIdx.x & 255, cg = (threadIdx.x >> 8) * NBT;
     const size_t NN = (size_t)N * N;
-    for (int idx = tid; idx < NB * N; idx += 256) {
+    const int nblk = (N + KB - 1) / KB;
+    for (int idx = threadIdx.x; idx < NB * N; idx += 512) {
         const int jj = idx / N, k = idx - jj * N, j = j0 + jj;
         P0[k * NB + jj] = (j < N) ? (float)U[(size_t)f * NN + (size_t)j * N + k] : 0.f;
     }
@@ -157,18 +197,28 @@ __global__ void __launch_bounds__(256) k_slice_f32(const float* __restrict__ Fhi
     float* Pout = P1;
     for (int s = 0; s < nsl; ++s) {
         __syncthreads();
-        float hi[RPT][NB], cp[RPT][NB], blk[RPT][NB], lo[RPT][NB];
+        stage_F<KB>(Fs0, Fhi, Flo, N, 0, min(KB, N));
+        cp_async_commit();
+        float hi[RPT][NBT], cp[RPT][NBT], blk[RPT][NBT], lo[RPT][NBT];
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
-            for (int c = 0; c < NB; ++c) hi[r][c] = cp[r][c] = blk[r][c] = lo[r][c] = 0.f;
-        for (int k0 = 0; k0 < N; k0 += 32) {
-            const int k1 = min(N, k0 + 32);
-            for (int k = k0; k < k1; ++k) {
-                float pv[NB];
+            for (int c = 0; c < NBT; ++c) hi[r][c] = cp[r][c] = blk[r][c] = lo[r][c] = 0.f;
+        for (int b = 0; b < nblk; ++b) {
+            float* Fcur = (b & 1) ? Fs1 : Fs0;
+            if (b + 1 < nblk) stage_F<KB>((b & 1) ? Fs0 : Fs1, Fhi, Flo, N, (b + 1) * KB, min(KB, N - (b + 1) * KB));
+            cp_async_commit();
+            cp_async_wait1();
+            __syncthreads();
+            const int k0 = b * KB, nk = min(KB, N - k0);
+            const float* Fh = Fcur;
+            const float* Fl = Fcur + (size_t)KB * N;
+            for (int kk = 0; kk < nk; ++kk) {
+                const int k = k0 + kk;
+                float pv[NBT];
 #pragma unroll
-                for (int c = 0; c < NB; c += 4) {
-                    const float4 q = *reinterpret_cast<const float4*>(Pin + k * NB + c);
+                for (int c = 0; c < NBT; c += 4) {
+                    const float4 q = *reinterpret_cast<const float4*>(Pin + k * NB + cg + c);
                     pv[c] = q.x;
                     pv[c + 1] = q.y;
                     pv[c + 2] = q.z;
@@ -177,10 +227,10 @@ __global__ void __launch_bounds__(256) k_slice_f32(const float* __restrict__ Fhi
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
                     const int i = tid + 256 * r;
-                    const float ah = (i < N) ? __ldg(Fhi + (size_t)k * N + i) : 0.f;
-                    const float al = (i < N) ? __ldg(Flo + (size_t)k * N + i) : 0.f;
+                    const float ah = (i < N) ? Fh[kk * N + i] : 0.f;
+                    const float al = (i < N) ? Fl[kk * N + i] : 0.f;
 #pragma unroll
-                    for (int c = 0; c < NB; ++c) {
+                    for (int c = 0; c < NBT; ++c) {
                         blk[r][c] = fmaf(ah, pv[c], blk[r][c]);
                         lo[r][c] = fmaf(al, pv[c], lo[r][c]);
                     }
@@ -189,7 +239,7 @@ __global__ void __launch_bounds__(256) k_slice_f32(const float* __restrict__ Fhi
 #pragma unroll
             for (int r = 0; r < RPT; ++r)
 #pragma unroll
-                for (int c = 0; c < NB; ++c) {  // TwoSum(hi, blk) -> hi + error into cp
+                for (int c = 0; c < NBT; ++c) {  // TwoSum(hi, blk) -> hi + error into cp
                     const float t = __fadd_rn(hi[r][c], blk[r][c]);
                     const float bp = __fsub_rn(t, hi[r][c]);
                     const float e = __fadd_rn(__fsub_rn(hi[r][c], __fsub_rn(t, bp)), __fsub_rn(blk[r][c], bp));
@@ -197,6 +247,7 @@ __global__ void __launch_bounds__(256) k_slice_f32(const float* __restrict__ Fhi
                     hi[r][c] = t;
                     blk[r][c] = 0.f;
                 }
+            __syncthreads();  // the stage just read is refilled two blocks later
         }
         const bool last = (s == nsl - 1);
         const float* scl = sc32 + ((size_t)f * L + l0 + s) * N;
@@ -206,13 +257,13 @@ __global__ void __launch_bounds__(256) k_slice_f32(const float* __restrict__ Fhi
             if (i >= N) continue;
             const float sc = scl[i];
 #pragma unroll
-            for (int c = 0; c < NB; ++c) {
+            for (int c = 0; c < NBT; ++c) {
                 const float fy = __fadd_rn(hi[r][c], __fadd_rn(cp[r][c], lo[r][c]));
-                const float v = __fmul_rn(__fadd_rn(Pin[i * NB + c], fy), sc);
+                const float v = __fmul_rn(__fadd_rn(Pin[i * NB + cg + c], fy), sc);
                 if (last) {
-                    if (j0 + c < N) out[(size_t)f * NN + (size_t)(j0 + c) * N + i] = (double)v;
+                    if (j0 + cg + c < N) out[(size_t)f * NN + (size_t)(j0 + cg + c) * N + i] = (double)v;
                 } else {
-                    Pout[i * NB + c] = v;
+                    Pout[i * NB + cg + c] = v;
                 }
             }
         }
@@ -222,16 +273,29 @@ __global__ void __launch_bounds__(256) k_slice_f32(const float* __restrict__ Fhi
     }
 }
 
-template <int RPT, int NB>
-cudaError_t launch_slice_f32(const slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s) {
+constexpr size_t kSmemBudget = 220 * 1024;
+
+template <int RPT, int NBT, int KB>
+cudaError_t launch_slice_f32_kb(const slmc_ctx* c, int nf, int l0, int nsl, cudaStream_t s) {
     const int N = c->N;
-    const size_t smem = (size_t)2 * N * NB * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_slice_f32<RPT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr int NB = 2 * NBT;
+    const size_t smem = ((size_t)2 * N * NB + (size_t)4 * KB * N) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_slice_f32<RPT, NBT, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((N + NB - 1) / NB, nf);
-    (void)x;
-    k_slice_f32<RPT, NB><<<grid, 256, smem, s>>>(c->F32, c->F32lo, c->U, c->Y, c->sc32, N, c->L, l0, nsl);
+    k_slice_f32<RPT, NBT, KB><<<grid, 512, smem, s>>>(c->F32, c->F32lo, c->U, c->Y, c->sc32, N, c->L, l0, nsl);
     return cudaGetLastError();
+}
+
+// Largest staged block (32, 16 or 8 rows of F) that fits the shared-memory budget.
+template <int RPT, int NBT>
+cudaError_t launch_slice_f32(const slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s) {
+    (void)x;
+    const size_t panel = (size_t)2 * c->N * 2 * NBT * sizeof(float);
+    const size_t per_row = (size_t)4 * c->N * sizeof(float);
+    if (panel + 32 * per_row <= kSmemBudget) return launch_slice_f32_kb<RPT, NBT, 32>(c, nf, l0, nsl, s);
+    if (panel + 16 * per_row <= kSmemBudget) return launch_slice_f32_kb<RPT, NBT, 16>(c, nf, l0, nsl, s);
+    return launch_slice_f32_kb<RPT, NBT, 8>(c, nf, l0, nsl, s);
 }
 
 // exp(-dtau lambda x[f][i][l]) in FP64, rounded once to FP32, stored [f][l][i]: the slice

@@ -39,12 +39,12 @@ struct QrSmem {
 // stored at col(j)): A <- (I - V op(S) V^T) A, op(S) = S^T for the QR trailing update
 // (Q_p^T A) and S for the backward formation of Q (Q_p A). V is the clean panel in shared
 // memory (rows p..N-1, unit diagonal, zeros above), row stride BP+1.
-template <int BP, bool TRANS, typename ColFn>
-__device__ __forceinline__ void wy_update(const double* __restrict__ Vp, const double* __restrict__ Ssm,
-                                          double* __restrict__ Wsm, int N, int p, int nb, int j_begin, ColFn col) {
+template <int BP, bool TRANS, typename T, typename ColFn>
+__device__ __forceinline__ void wy_update(const T* __restrict__ Vp, const T* __restrict__ Ssm, T* __restrict__ Wsm,
+                                          int N, int p, int nb, int j_begin, ColFn col) {
     constexpr int BPS = BP + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double* W = Wsm + warp * BP * kCT;
+    T* W = Wsm + warp * BP * kCT;
     const int ncols = N - j_begin;
     for (int g = warp * kCT; g < ncols; g += kWarps * kCT) {
         double* cptr[kCT];
@@ -57,33 +57,33 @@ __device__ __forceinline__ void wy_update(const double* __restrict__ Vp, const d
         double* mine[CPL];
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc) mine[cc] = (h == 0) ? cptr[cc] : cptr[(CPL < kCT ? CPL : 0) + cc];
-        double acc[CPL];
+        T acc[CPL];
 #pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) acc[cc] = 0.0;
+        for (int cc = 0; cc < CPL; ++cc) acc[cc] = T(0);
         for (int r = p; r < N; ++r) {
-            const double v = Vp[r * BPS + m];
+            const T v = Vp[r * BPS + m];
 #pragma unroll
             for (int cc = 0; cc < CPL; ++cc)
-                if (mine[cc]) acc[cc] = fma(v, mine[cc][r], acc[cc]);
+                if (mine[cc]) acc[cc] = fma(v, (T)mine[cc][r], acc[cc]);
         }
         __syncwarp();
 #pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) W[m * kCT + h * CPL + cc] = (m < nb) ? acc[cc] : 0.0;
+        for (int cc = 0; cc < CPL; ++cc) W[m * kCT + h * CPL + cc] = (m < nb) ? acc[cc] : T(0);
         __syncwarp();
         // W' = op(S) W   (same lane ownership)
-        double w2[CPL];
+        T w2[CPL];
 #pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) w2[cc] = 0.0;
+        for (int cc = 0; cc < CPL; ++cc) w2[cc] = T(0);
         if (m < nb) {
             if (TRANS) {
                 for (int q = 0; q <= m; ++q) {
-                    const double sv = Ssm[q * BP + m];
+                    const T sv = Ssm[q * BP + m];
 #pragma unroll
                     for (int cc = 0; cc < CPL; ++cc) w2[cc] = fma(sv, W[q * kCT + h * CPL + cc], w2[cc]);
                 }
             } else {
                 for (int q = m; q < nb; ++q) {
-                    const double sv = Ssm[m * BP + q];
+                    const T sv = Ssm[m * BP + q];
 #pragma unroll
                     for (int cc = 0; cc < CPL; ++cc) w2[cc] = fma(sv, W[q * kCT + h * CPL + cc], w2[cc]);
                 }
@@ -95,21 +95,21 @@ __device__ __forceinline__ void wy_update(const double* __restrict__ Vp, const d
         __syncwarp();
         // A[r][c] -= sum_m V[r][m] W'[m][c]   (lanes over rows)
         for (int r0 = p; r0 < N; r0 += 32 * kRC) {
-            double y[kRC][kCT];
+            T y[kRC][kCT];
 #pragma unroll
             for (int q = 0; q < kRC; ++q) {
                 const int r = r0 + lane + 32 * q;
 #pragma unroll
-                for (int c = 0; c < kCT; ++c) y[q][c] = (r < N && cptr[c]) ? cptr[c][r] : 0.0;
+                for (int c = 0; c < kCT; ++c) y[q][c] = (r < N && cptr[c]) ? (T)cptr[c][r] : T(0);
             }
             for (int mm = 0; mm < nb; ++mm) {
-                double wv[kCT];
+                T wv[kCT];
 #pragma unroll
                 for (int c = 0; c < kCT; ++c) wv[c] = W[mm * kCT + c];
 #pragma unroll
                 for (int q = 0; q < kRC; ++q) {
                     const int r = r0 + lane + 32 * q;
-                    const double v = (r < N) ? Vp[r * BPS + mm] : 0.0;
+                    const T v = (r < N) ? Vp[r * BPS + mm] : T(0);
 #pragma unroll
                     for (int c = 0; c < kCT; ++c) y[q][c] = fma(-v, wv[c], y[q][c]);
                 }
@@ -120,7 +120,7 @@ __device__ __forceinline__ void wy_update(const double* __restrict__ Vp, const d
                 if (r < N) {
 #pragma unroll
                     for (int c = 0; c < kCT; ++c)
-                        if (cptr[c]) cptr[c][r] = y[q][c];
+                        if (cptr[c]) cptr[c][r] = (double)y[q][c];
                 }
             }
         }
@@ -323,8 +323,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
     if (bad) atomicOr(err, SLMC_EBIT_NONFINITE);
 }
 
-// Q = Q_0 Q_1 ... (Q_p = I - V_p S_p V_p^T), accumulated backwards into U (column-major).
-template <int BP>
+// Q = Q_0 Q_1 ... (Q_p = I - V_p S_p V_p^T), accumulated backwards into U (column-major),
+// computed in T: FP64, or FP32 when Q only feeds reduced-precision slice products (which round
+// it to FP32 on entry anyway).
+template <int BP, typename T>
 __global__ void __launch_bounds__(kThreads, 2) k_formq_b(const double* __restrict__ QRall, const double* __restrict__ Sall,
                                                       double* __restrict__ Uall, int N) {
     constexpr int BPS = BP + 1;
@@ -333,9 +335,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_formq_b(const double* __restric
     const double* __restrict__ QR = QRall + f * NN;
     double* __restrict__ U = Uall + f * NN;
     extern __shared__ __align__(16) unsigned char smraw[];
-    double* Vp = reinterpret_cast<double*>(smraw);
-    double* Ssm = Vp + (size_t)N * BPS;
-    double* Wsm = Ssm + BP * BP;
+    T* Vp = reinterpret_cast<T*>(smraw);
+    T* Ssm = Vp + (size_t)N * BPS;
+    T* Wsm = Ssm + BP * BP;
     const int tid = threadIdx.x;
     for (size_t idx = tid; idx < NN; idx += kThreads) U[idx] = (idx % (N + 1) == 0) ? 1.0 : 0.0;
     for (int p = ((N - 1) / BP) * BP; p >= 0; p -= BP) {
@@ -344,11 +346,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_formq_b(const double* __restric
         for (int idx = tid; idx < nb * (N - p); idx += kThreads) {
             const int c = idx / (N - p), r = p + idx - c * (N - p);
             const int k = p + c;
-            Vp[r * BPS + c] = (r > k) ? QR[(size_t)k * N + r] : (r == k ? 1.0 : 0.0);
+            Vp[r * BPS + c] = (T)((r > k) ? QR[(size_t)k * N + r] : (r == k ? 1.0 : 0.0));
         }
         for (int idx = tid; idx < nb * BP; idx += kThreads) {
             const int a = idx / BP, b = idx - a * BP;
-            Ssm[a * BP + b] = Sall[(size_t)f * N * BP + (size_t)(p + a) * BP + b];
+            Ssm[a * BP + b] = (T)Sall[(size_t)f * N * BP + (size_t)(p + a) * BP + b];
         }
         __syncthreads();
         wy_update<BP, false>(Vp, Ssm, Wsm, N, p, nb, p, [&](int j) { return U + (size_t)j * N; });
@@ -419,12 +421,12 @@ cudaError_t launch_qrb(slmc_ctx* c, int nf, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int BP>
+template <int BP, typename T>
 cudaError_t launch_formq_b(slmc_ctx* c, int nf, cudaStream_t s) {
-    const size_t smem = sizeof(double) * ((size_t)c->N * (BP + 1) + BP * BP + kWarps * BP * kCT);
-    cudaError_t e = cudaFuncSetAttribute(k_formq_b<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sizeof(T) * ((size_t)c->N * (BP + 1) + BP * BP + kWarps * BP * kCT);
+    cudaError_t e = cudaFuncSetAttribute(k_formq_b<BP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_formq_b<BP><<<nf, kThreads, smem, s>>>(c->QR, c->Sws, c->U, c->N);
+    k_formq_b<BP, T><<<nf, kThreads, smem, s>>>(c->QR, c->Sws, c->U, c->N);
     return cudaGetLastError();
 }
 
@@ -438,8 +440,9 @@ cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s) {
     return qr_panel_width(c->N) == 32 ? launch_qrb<32>(c, nf, s) : launch_qrb<16>(c, nf, s);
 }
 
-cudaError_t form_q_blocked(slmc_ctx* c, int nf, cudaStream_t s) {
-    return qr_panel_width(c->N) == 32 ? launch_formq_b<32>(c, nf, s) : launch_formq_b<16>(c, nf, s);
+cudaError_t form_q_blocked(slmc_ctx* c, int nf, bool fp32, cudaStream_t s) {
+    if (fp32) return qr_panel_width(c->N) == 32 ? launch_formq_b<32, float>(c, nf, s) : launch_formq_b<16, float>(c, nf, s);
+    return qr_panel_width(c->N) == 32 ? launch_formq_b<32, double>(c, nf, s) : launch_formq_b<16, double>(c, nf, s);
 }
 
 cudaError_t t_update_tiled(slmc_ctx* c, int nf, cudaStream_t s) {

@@ -119,7 +119,7 @@ void tc_geometry(int N, int precision, int* npad, int* nt, size_t* piece_bytes, 
 int tc_launches(int nsl);
 cudaError_t t_update_tiled(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s);
-cudaError_t form_q_blocked(slmc_ctx* c, int nf, cudaStream_t s);
+cudaError_t form_q_blocked(slmc_ctx* c, int nf, bool fp32, cudaStream_t s);
 int qr_panel_width(int N);
 cudaError_t qr_pivoted(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t form_q(slmc_ctx* c, int nf, cudaStream_t s);
