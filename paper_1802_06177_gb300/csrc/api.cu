@@ -110,6 +110,8 @@ int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign,
         if (c->p.qr_mode == SLMC_QR_PIVOTED) {
             SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_pivoted(c, nf, s));
             SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q(c, nf, s));
+            if (c->p.precision != SLMC_PREC_FP64 && l0 + nsl < c->L)
+                SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::u_to_f32(c, nf, s));
         } else {
             SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_blocked(c, nf, s));
             // Q enters the next reduced-precision slice group (rounded to FP32 there anyway) except
@@ -136,7 +138,7 @@ int for_batches(slmc_ctx* c, int n, F&& fn) {
 void free_ctx(slmc_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
-    void* bufs[] = {c->E64, c->F32, c->F32lo, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->Ta, c->Tb, c->lnD, c->tau,
+    void* bufs[] = {c->E64, c->F32, c->F32lo, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
                     c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err,
                     c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
     for (void* b : bufs)
@@ -201,6 +203,7 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     alloc(&c->Y, F * NN * sizeof(double));
     alloc(&c->QR, F * NN * sizeof(double));
     alloc(&c->U, F * NN * sizeof(double));
+    if (p->precision != SLMC_PREC_FP64) alloc(&c->U32, F * NN * sizeof(float));
     alloc(&c->Ta, F * NN * sizeof(double));
     alloc(&c->Tb, F * NN * sizeof(double));
     alloc(&c->lnD, F * N * sizeof(double));

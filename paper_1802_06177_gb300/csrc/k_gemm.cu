@@ -178,7 +178,7 @@ __device__ __forceinline__ void stage_F(float* Fs, const float* __restrict__ Fhi
 
 template <int RPT, int NBT, int KB>
 __global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi, const float* __restrict__ Flo,
-                                                   const double* __restrict__ U, double* __restrict__ out,
+                                                   const float* __restrict__ U, double* __restrict__ out,
                                                    const float* __restrict__ sc32, int N, int L, int l0, int nsl) {
     constexpr int NB = 2 * NBT;  // two column groups of NBT columns; thread = (row, group)
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi
     const int nblk = (N + KB - 1) / KB;
     for (int idx = threadIdx.x; idx < NB * N; idx += 512) {
         const int jj = idx / N, k = idx - jj * N, j = j0 + jj;
-        P0[k * NB + jj] = (j < N) ? (float)U[(size_t)f * NN + (size_t)j * N + k] : 0.f;
+        P0[k * NB + jj] = (j < N) ? U[(size_t)f * NN + (size_t)j * N + k] : 0.f;
     }
     float* Pin = P0;
     float* Pout = P1;
@@ -283,7 +283,7 @@ cudaError_t launch_slice_f32_kb(const slmc_ctx* c, int nf, int l0, int nsl, cuda
     cudaError_t e = cudaFuncSetAttribute(k_slice_f32<RPT, NBT, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((N + NB - 1) / NB, nf);
-    k_slice_f32<RPT, NBT, KB><<<grid, 512, smem, s>>>(c->F32, c->F32lo, c->U, c->Y, c->sc32, N, c->L, l0, nsl);
+    k_slice_f32<RPT, NBT, KB><<<grid, 512, smem, s>>>(c->F32, c->F32lo, c->U32, c->Y, c->sc32, N, c->L, l0, nsl);
     return cudaGetLastError();
 }
 
@@ -311,12 +311,19 @@ __global__ void k_scales(const double* __restrict__ x, float* __restrict__ sc, i
     }
 }
 
-__global__ void k_identity(double* __restrict__ U, double* __restrict__ T, double* __restrict__ lnD, int N) {
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, size_t total) {
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x)
+        b[idx] = (float)a[idx];
+}
+
+__global__ void k_identity(double* __restrict__ U, float* __restrict__ U32, double* __restrict__ T,
+                           double* __restrict__ lnD, int N) {
     const int f = blockIdx.y;
     const size_t NN = (size_t)N * N;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
         const double v = (idx % (N + 1) == 0) ? 1.0 : 0.0;
         U[(size_t)f * NN + idx] = v;
+        if (U32) U32[(size_t)f * NN + idx] = (float)v;
         T[(size_t)f * NN + idx] = v;
         if (idx < (size_t)N) lnD[(size_t)f * N + idx] = 0.0;
     }
@@ -345,9 +352,15 @@ cudaError_t slice_scales(slmc_ctx* c, const double* x, int nf, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t u_to_f32(slmc_ctx* c, int nf, cudaStream_t s) {
+    const size_t total = (size_t)nf * c->N * c->N;
+    k_to_f32<<<(unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096), 256, 0, s>>>(c->U, c->U32, total);
+    return cudaGetLastError();
+}
+
 cudaError_t set_identity(slmc_ctx* c, int nf, cudaStream_t s) {
     dim3 grid(64, nf);
-    k_identity<<<grid, 256, 0, s>>>(c->U, c->Ta, c->lnD, c->N);
+    k_identity<<<grid, 256, 0, s>>>(c->U, c->U32, c->Ta, c->lnD, c->N);
     return cudaGetLastError();
 }
 

@@ -35,9 +35,10 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t fixed_bytes(size_t N) {
     return align256(N * N * sizeof(double)) + 2 * align256(N * N * sizeof(float)) + 256;
 }
+// L > 0 (FP32 mode): also the FP32 slice scales and the FP32 orthogonal factor.
 size_t field_bytes(size_t N, size_t L) {
     return 5 * N * N * sizeof(double) + 32 * N * sizeof(double) + 2 * N * sizeof(double) + 2 * N * sizeof(int) +
-           sizeof(int) + L * N * sizeof(float);
+           sizeof(int) + L * N * sizeof(float) + (L ? N * N * sizeof(float) : 0);
 }
 
 int scratch_address(int device, unsigned char** out) {
@@ -102,6 +103,7 @@ int slmc_logdet_noalloc(const slmc_params* p, const double* x, int n, double* ln
     c.piv = c.perm + F * N;
     c.sgnU = c.piv + F * N;
     c.sc32 = Lz ? reinterpret_cast<float*>(c.sgnU + F) : nullptr;
+    c.U32 = Lz ? c.sc32 + F * Lz * N : nullptr;
 
     if (cudaMemsetAsync(c.err, 0, sizeof(unsigned int), s) != cudaSuccess) return SLMC_ERR_CUDA;
     if (slmc::build_hopping_exp(&c, s) != cudaSuccess) return SLMC_ERR_CUDA;

@@ -45,16 +45,17 @@ __device__ __forceinline__ void wy_update(const T* __restrict__ Vp, const T* __r
     constexpr int BPS = BP + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T* W = Wsm + warp * BP * kCT;
+    using CT = decltype(col(0));  // column pointer: same precision as T (no conversions in the loops)
     const int ncols = N - j_begin;
     for (int g = warp * kCT; g < ncols; g += kWarps * kCT) {
-        double* cptr[kCT];
+        CT cptr[kCT];
 #pragma unroll
         for (int c = 0; c < kCT; ++c) cptr[c] = (j_begin + g + c < N) ? col(j_begin + g + c) : nullptr;
         // W[m][c] = sum_r V[r][m] A[r][c]: lane (m, h) owns reflector m = lane % BP and the
         // CPL columns of half h = lane / BP (A rows are broadcast to the warp)
         constexpr int CPL = kCT * BP / 32;
         const int m = lane % BP, h = lane / BP;
-        double* mine[CPL];
+        CT mine[CPL];
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc) mine[cc] = (h == 0) ? cptr[cc] : cptr[(CPL < kCT ? CPL : 0) + cc];
         T acc[CPL];
@@ -64,7 +65,7 @@ __device__ __forceinline__ void wy_update(const T* __restrict__ Vp, const T* __r
             const T v = Vp[r * BPS + m];
 #pragma unroll
             for (int cc = 0; cc < CPL; ++cc)
-                if (mine[cc]) acc[cc] = fma(v, (T)mine[cc][r], acc[cc]);
+                if (mine[cc]) acc[cc] = fma(v, mine[cc][r], acc[cc]);
         }
         __syncwarp();
 #pragma unroll
@@ -100,7 +101,7 @@ __device__ __forceinline__ void wy_update(const T* __restrict__ Vp, const T* __r
             for (int q = 0; q < kRC; ++q) {
                 const int r = r0 + lane + 32 * q;
 #pragma unroll
-                for (int c = 0; c < kCT; ++c) y[q][c] = (r < N && cptr[c]) ? (T)cptr[c][r] : T(0);
+                for (int c = 0; c < kCT; ++c) y[q][c] = (r < N && cptr[c]) ? cptr[c][r] : T(0);
             }
             for (int mm = 0; mm < nb; ++mm) {
                 T wv[kCT];
@@ -120,7 +121,7 @@ __device__ __forceinline__ void wy_update(const T* __restrict__ Vp, const T* __r
                 if (r < N) {
 #pragma unroll
                     for (int c = 0; c < kCT; ++c)
-                        if (cptr[c]) cptr[c][r] = (double)y[q][c];
+                        if (cptr[c]) cptr[c][r] = y[q][c];
                 }
             }
         }
@@ -328,18 +329,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
 // it to FP32 on entry anyway).
 template <int BP, typename T>
 __global__ void __launch_bounds__(kThreads, 2) k_formq_b(const double* __restrict__ QRall, const double* __restrict__ Sall,
-                                                      double* __restrict__ Uall, int N) {
+                                                      T* __restrict__ Uall, int N) {
     constexpr int BPS = BP + 1;
     const int f = blockIdx.x;
     const size_t NN = (size_t)N * N;
     const double* __restrict__ QR = QRall + f * NN;
-    double* __restrict__ U = Uall + f * NN;
+    T* __restrict__ U = Uall + f * NN;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* Vp = reinterpret_cast<T*>(smraw);
     T* Ssm = Vp + (size_t)N * BPS;
     T* Wsm = Ssm + BP * BP;
     const int tid = threadIdx.x;
-    for (size_t idx = tid; idx < NN; idx += kThreads) U[idx] = (idx % (N + 1) == 0) ? 1.0 : 0.0;
+    for (size_t idx = tid; idx < NN; idx += kThreads) U[idx] = (idx % (N + 1) == 0) ? T(1) : T(0);
     for (int p = ((N - 1) / BP) * BP; p >= 0; p -= BP) {
         const int nb = min(BP, N - p);
         __syncthreads();
@@ -426,7 +427,10 @@ cudaError_t launch_formq_b(slmc_ctx* c, int nf, cudaStream_t s) {
     const size_t smem = sizeof(T) * ((size_t)c->N * (BP + 1) + BP * BP + kWarps * BP * kCT);
     cudaError_t e = cudaFuncSetAttribute(k_formq_b<BP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_formq_b<BP, T><<<nf, kThreads, smem, s>>>(c->QR, c->Sws, c->U, c->N);
+    T* U;
+    if constexpr (sizeof(T) == 4) U = c->U32;
+    else U = c->U;
+    k_formq_b<BP, T><<<nf, kThreads, smem, s>>>(c->QR, c->Sws, U, c->N);
     return cudaGetLastError();
 }
 

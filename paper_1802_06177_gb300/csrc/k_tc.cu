@@ -283,15 +283,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// U (FP64, column-major per field) -> FP32 copy and pieces: the first slice's operand.
+// U (FP32, column-major per field) -> FP32 copy and pieces: the first slice's operand.
 template <int MODE>
-__global__ void k_tc_split_in(const double* __restrict__ U, float* __restrict__ y32, void* __restrict__ P, int N,
+__global__ void k_tc_split_in(const float* __restrict__ U, float* __restrict__ y32, void* __restrict__ P, int N,
                               int Npad, int nfmax, size_t total) {
     const size_t pstride = (size_t)nfmax * N * Npad;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
         const size_t col = idx / N;
         const int i = (int)(idx - col * N);
-        const float v = (float)U[idx];
+        const float v = U[idx];
         y32[idx] = v;
         store_pieces<MODE>(P, pstride, col * Npad + i, v);
     }
@@ -351,7 +351,7 @@ cudaError_t run_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cud
     using C = Cfg<MODE>;
     const int N = c->N, Npad = c->tc_npad, NT = c->tc_nt;
     const size_t total = (size_t)nf * N * N;
-    k_tc_split_in<MODE><<<1024, 256, 0, s>>>(c->U, c->tc_y32[0], c->tc_p[0], N, Npad, c->max_fields, total);
+    k_tc_split_in<MODE><<<1024, 256, 0, s>>>(c->U32, c->tc_y32[0], c->tc_p[0], N, Npad, c->max_fields, total);
     const size_t smem = 1024 + (size_t)kStages * C::NP * (128 * kAtom + (size_t)NT * kAtom);
     cudaError_t e = cudaFuncSetAttribute(k_tc_slice<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

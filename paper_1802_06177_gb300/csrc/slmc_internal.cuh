@@ -31,6 +31,7 @@ struct slmc_ctx {
     double* Y;       // slice-group product; reused for M in the final step
     double* QR;      // packed pivoted-QR output; reused for G in the cumulative update
     double* U;       // orthogonal factor
+    float* U32;      // FP32 orthogonal factor feeding reduced-precision slice groups (mixed modes)
     double* Ta;      // T factor (ping), row-major
     double* Tb;      // T factor (pong), row-major
     double* lnD;     // [max_fields][N] ln of the D scales
@@ -124,6 +125,7 @@ int qr_panel_width(int N);
 cudaError_t qr_pivoted(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t form_q(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t set_identity(slmc_ctx* c, int nf, cudaStream_t s);
+cudaError_t u_to_f32(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t final_logdet(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s);
 cudaError_t final_greens(slmc_ctx* c, int nf, double* G, cudaStream_t s);
 cudaError_t bose_log_weight(slmc_ctx* c, const double* x, int nf, const double* lndet, double* lnw,

@@ -184,3 +184,13 @@ def test_both_qr_modes(qr_mode, Lx, Ly, L, n_s, nf):
     assert np.abs(lndet.cpu().numpy() - l_ref).max() <= TOL_LNDET_FP64
     assert np.array_equal(sign.cpu().numpy(), s_ref)
     assert np.abs(G.cpu().numpy() - G_ref).max() <= TOL_G_FP64
+
+
+@pytest.mark.parametrize("qr_mode", ["prepivot", "pivoted"])
+def test_mixed_both_qr_modes(qr_mode):
+    x = inputs.mixed_fields(4, 12, 12, 120, seed=5)
+    ctx = make_ctx(12, 120, 10, precision="fp32", max_fields=4, qr_mode=qr_mode)
+    lndet, sign = ctx.logdet(cuda(x))
+    l_ref, s_ref, _ = oracle_many(HolsteinParams(12, 12, 120, n_s=10), x, want_G=False)
+    assert np.abs(lndet.cpu().numpy() - l_ref).max() <= TOL_LNDET_MIXED
+    assert np.array_equal(sign.cpu().numpy(), s_ref)
