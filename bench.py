@@ -368,6 +368,8 @@ def run_gpu(args):
         c64.close()
     args.mode = old_mode
 
+    batched = None if args.no_batch else run_uneven_batch(args, dev, seed)
+
     if rank != 0:
         return 0
 
@@ -426,9 +428,57 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
             "fp64_value": fp64_value, "logdet_only_evals_per_s": rates, "accuracy_max_abs_dlndet": acc,
-            "time_shares": shares, "mode": args.mode}
+            "time_shares": shares, "mode": args.mode, "batched_uneven": batched}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_uneven_batch(args, dev, seed):
+    """Uneven batch: 64 chains each of 8x8/L=80, 10x10/L=100, 12x12/L=120, 16x16/L=160 (beta = L dtau),
+    FP32 slices, n_s and tiles autotuned per class, advanced round by round (one cumulative update of
+    every chain per round, 20 E_eff sweeps each) by replaying one captured CUDA graph."""
+    import torch
+
+    from paper_1802_06177_gb300 import inputs
+    from paper_1802_06177_gb300.slmc import Batch, autotune
+    from paper_1802_06177_gb300.workloads import UNEVEN_BATCH
+    tuned, classes = {}, []
+    for Lx, L, n in UNEVEN_BATCH:
+        r = autotune(Lx, Lx, L, precision="fp32", ntune=16, tol=5e-5, seed=seed)
+        tuned["%dx%d_L%d" % (Lx, Lx, L)] = {"n_s": r["n_s"], "qr_panel": r["qr_panel"],
+                                            "slice_cols": r["slice_cols"], "max_abs_dlndet": r["max_abs_dlndet"]}
+        classes.append(dict(Lx=Lx, L=L, nchains=n, n_s=r["n_s"], precision="fp32", seed=seed, sweep_delta=0.3,
+                            tuning=(r["qr_panel"], r["slice_cols"])))
+    b = Batch([{k: v for k, v in cl.items() if k != "tuning"} for cl in classes], device=dev)
+    keep = []
+    with torch.cuda.stream(b.stream):
+        for q, cl in enumerate(classes):
+            ctx = b.context(q)
+            ctx.set_tuning(*cl["tuning"])
+            x = torch.from_numpy(inputs.gaussian_fields(cl["nchains"], cl["Lx"], cl["Lx"], cl["L"],
+                                                        seed=seed + 17 * q)).to(dev)
+            lnw0, _, _ = ctx.log_weight(x)
+            J, _ = ctx.fit_eff(x, lnw0)
+            lnw, s = ctx.chain_init(x)
+            n_acc = torch.zeros(cl["nchains"], dtype=torch.int64, device=dev)
+            ctx.set_update_counter(0)
+            b.bind(q, x, J, lnw, s, n_acc)
+            keep.append((x, J, lnw, s, n_acc))
+    b.stream.synchronize()
+    b.capture(args.nsweeps, 1)
+    b.launch(2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.launch(args.batch_rounds)
+    e1.record(b.stream)
+    b.stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    nch = sum(cl["nchains"] for cl in classes)
+    acc = sum(int(k[4].sum().item()) for k in keep) / float(nch * (args.batch_rounds + 2))
+    b.close()
+    return {"evals_per_s": nch * args.batch_rounds / (ms / 1e3), "chains": nch, "rounds_timed": args.batch_rounds,
+            "ms_per_round": ms / args.batch_rounds, "graph_launch_per_round": 1, "nsweeps": args.nsweeps,
+            "acceptance": acc, "tuned": tuned}
 
 
 def main():
@@ -445,6 +495,8 @@ def main():
     ap.add_argument("--acc-fields", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-rounds", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "slmc":
         args.warmup = 3

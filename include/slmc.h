@@ -160,12 +160,18 @@ SLMC_API int slmc_eff_sweep(slmc_ctx* ctx, double* x, int n, const double* J, in
  * NULL, s_cdw[n] = S(pi,pi) of each configuration. */
 SLMC_API int slmc_chain_init(slmc_ctx* ctx, const double* x, int n, double* lnw, double* s_cdw, void* stream);
 
-/* nupdates cumulative updates of n independent chains [Eq. (6)]. Update u (global index
- * update0 + u) of chain c draws Philox block (update0 + u, 0, c, 1): bit 0 of word 0 is
- * the first colour, words 2-3 the acceptance uniform. It then runs nsweeps effective-
- * model sweeps with sweep counters (update0 + u) * nsweeps + s, evaluates the exact
- * ln w(x') and accepts with min{1, [w(x')/w(x)] [w_eff(x)/w_eff(x')]}; on rejection x is
- * restored. The random starting colour makes the proposal reversible w.r.t. w_eff.
+/* Passing this as update0 continues from the context's device-side update counter. */
+#define SLMC_UPDATE_CONTINUE UINT64_MAX
+
+/* nupdates cumulative updates of n independent chains [Eq. (6)]. The context keeps a
+ * device-side update counter U: unless update0 is SLMC_UPDATE_CONTINUE it is first set to
+ * update0, and it advances by nupdates at the end (so a call captured into a CUDA graph
+ * draws fresh random numbers on every replay). Update u of chain c (global index U + u)
+ * draws Philox block (U + u, 0, c, 1): bit 0 of word 0 is the first colour, words 2-3 the
+ * acceptance uniform. It then runs nsweeps effective-model sweeps with sweep counters
+ * (U + u) * nsweeps + s, evaluates the exact ln w(x') and accepts with
+ * min{1, [w(x')/w(x)] [w_eff(x)/w_eff(x')]}; on rejection x is restored. The random starting
+ * colour makes the proposal reversible w.r.t. w_eff.
  *   x            [n][N][L] in/out chain states
  *   J            [6] device couplings of E_eff
  *   lnw          [n] in/out cached exact ln w of the current states
@@ -177,6 +183,19 @@ SLMC_API int slmc_chain_init(slmc_ctx* ctx, const double* x, int n, double* lnw,
 SLMC_API int slmc_cumulative_update(slmc_ctx* ctx, double* x, int n, const double* J, int nsweeps,
                            int nupdates, uint64_t update0, double* lnw, double* s_cdw,
                            long long* n_acc, long long* n_sweep_acc, double* obs, void* stream);
+
+/* Sets the device-side cumulative-update counter to `value` (enqueued on `stream`); with
+ * slmc_get_update_counter and the chain state it is all a checkpoint needs to resume the
+ * identical random stream. */
+SLMC_API int slmc_set_update_counter(slmc_ctx* ctx, uint64_t value, void* stream);
+
+/* Synchronises `stream` and returns the device-side cumulative-update counter. */
+SLMC_API int slmc_get_update_counter(slmc_ctx* ctx, uint64_t* value, void* stream);
+
+/* Kernel tile choices (found by slmc_autotune): qr_panel = width of the blocked-QR panels
+ * (0 = by N, 16 or 32); slice_cols = columns per thread of the FP32 slice kernel (0 = by N,
+ * 8 or 16; 16 is used only for N <= 256). Results do not depend on them beyond rounding. */
+SLMC_API int slmc_set_tuning(slmc_ctx* ctx, int qr_panel, int slice_cols);
 
 /* Multi-linear regression of the effective model [Eq. (5)]: least squares of
  * lnw[c] on [1, F(xs[c])] over nconf configurations (Givens-rotation QR in FP64), then
@@ -221,6 +240,43 @@ SLMC_API int slmc_profile_enable(slmc_ctx* ctx, int on);
  * and the number of timed launch calls in calls[c] (arrays of SLMC_PROF_NCLASS entries;
  * calls may be NULL). A call covers the kernels of one class enqueued together. */
 SLMC_API int slmc_profile_read(slmc_ctx* ctx, double* ms, long long* calls, void* stream);
+
+/* ---- Batches of chains of uneven size in one CUDA graph ----------------------------------
+ * A batch owns one context per lattice class (nclasses parameter sets, nchains[c] chains
+ * each) and one non-blocking stream per class. After the chain buffers of every class are
+ * bound, slmc_batch_capture records one round -- nupdates cumulative updates of every class,
+ * the classes as concurrent branches forked from and joined back to `stream` -- into a CUDA
+ * graph; slmc_batch_launch replays it. Each round continues every class's device-side update
+ * counter, so replays reproduce exactly the random streams of successive direct calls to
+ * slmc_cumulative_update with SLMC_UPDATE_CONTINUE. `stream` must be a created stream (not the
+ * legacy default stream). Buffer layouts and ownership are those of slmc_cumulative_update. */
+typedef struct slmc_batch slmc_batch;
+SLMC_API int slmc_batch_create(const slmc_params* classes, const int* nchains, int nclasses, slmc_batch** out);
+SLMC_API int slmc_batch_destroy(slmc_batch* batch);
+/* The context of class cls (owned by the batch), for slmc_chain_init, counters, tuning. */
+SLMC_API slmc_ctx* slmc_batch_context(slmc_batch* batch, int cls);
+SLMC_API int slmc_batch_bind(slmc_batch* batch, int cls, double* x, const double* J, double* lnw, double* s_cdw,
+                             long long* n_acc, long long* n_sweep_acc);
+SLMC_API int slmc_batch_capture(slmc_batch* batch, int nsweeps, int nupdates, void* stream);
+SLMC_API int slmc_batch_launch(slmc_batch* batch, int nrounds, void* stream);
+
+/* ---- Autotuner ------------------------------------------------------------------------------
+ * For the class described by *p (its precision and qr_mode), times slmc_logdet on ntune
+ * synthetic Gaussian fields for every candidate stabilisation interval n_s in
+ * {4, 6, 8, 10, 12, 16, 20, 24, 32} (<= L), blocked-QR panel width {16, 32} and FP32 slice
+ * tile {8, 16}, and returns the fastest candidate whose max |d ln det| against the library's
+ * FP64 path (n_s = 4) on the same fields is <= tol. Allocates and frees its own buffers and
+ * synchronises the device (an initialisation-time call). SLMC_ERR_UNSUPPORTED if no candidate
+ * meets tol. */
+typedef struct slmc_tune_result {
+    int n_s;
+    int qr_panel;          /* pass to slmc_set_tuning */
+    int slice_cols;        /* pass to slmc_set_tuning */
+    double sec_per_eval;   /* measured seconds per field evaluation */
+    double max_abs_dlndet; /* against the FP64 path */
+    int candidates;        /* candidates timed */
+} slmc_tune_result;
+SLMC_API int slmc_autotune(const slmc_params* p, int ntune, double tol, slmc_tune_result* out);
 
 /* Allocation-free ln|det(I + B_L ... B_1)| (the paper has no counterpart; this is a library
  * service). For callers that cannot allocate device memory where they need the result:

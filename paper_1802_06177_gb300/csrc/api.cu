@@ -139,7 +139,7 @@ void free_ctx(slmc_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
     void* bufs[] = {c->E64, c->F32, c->F32lo, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
-                    c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err,
+                    c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err, c->dctr,
                     c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -218,6 +218,8 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     alloc(&c->feat, 8 * F * sizeof(double));
     alloc(&c->fitR, 64 * sizeof(double));
     alloc(&c->err, sizeof(unsigned int));
+    alloc(&c->dctr, sizeof(unsigned long long));
+    if (ok && cudaMemset(c->dctr, 0, sizeof(unsigned long long)) != cudaSuccess) ok = false;
     const bool tc = p->precision == SLMC_PREC_TF32X3 || p->precision == SLMC_PREC_BF16X9;
     if (tc) {
         size_t es = 0;
@@ -345,18 +347,18 @@ int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int n
     if (!checkerboard_ok(c)) return SLMC_ERR_UNSUPPORTED;
     const size_t NL = (size_t)c->N * c->L;
     cudaStream_t s = as_stream(stream);
-    return for_batches(c, n, [&](int f0, int nf) {
+    if (update0 != SLMC_UPDATE_CONTINUE) SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::counter_op(c, update0, false, s));
+    SLMC_TRY(for_batches(c, n, [&](int f0, int nf) {
         double* xc = x + f0 * NL;
         for (int u = 0; u < nupdates; ++u) {
-            const uint64_t upd = update0 + (uint64_t)u;
-            SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::update_draws(c, nf, f0, upd, iscal(c, 1), scal(c, 4), s));
+            SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::update_draws(c, nf, f0, (uint64_t)u, iscal(c, 1), scal(c, 4), s));
             SLMC_CK(cudaMemcpyAsync(c->x_old, xc, nf * NL * sizeof(double), cudaMemcpyDeviceToDevice, s));
             SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, xc, nf, J, nullptr, 0, scal(c, 1), s));
             for (int sw = 0; sw < nsweeps; ++sw)
                 for (int h = 0; h < 2; ++h)
                     SLMC_LAUNCH(SLMC_PROF_SWEEP, 1, s,
-                                slmc::eff_half_sweep(c, xc, nf, f0, J, upd * (uint64_t)nsweeps + sw, 0, iscal(c, 1), h,
-                                                     n_sweep_acc ? n_sweep_acc + f0 : nullptr, s));
+                                slmc::eff_half_sweep(c, xc, nf, f0, J, (uint64_t)u * nsweeps + sw, 0, iscal(c, 1), h,
+                                                     n_sweep_acc ? n_sweep_acc + f0 : nullptr, s, c->dctr, nsweeps));
             SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, xc, nf, J, nullptr, 0, scal(c, 2), s));
             SLMC_TRY(logdet_batch(c, xc, nf, scal(c, 0), iscal(c, 0), s_cdw ? c->QR : nullptr, s));
             SLMC_LAUNCH(SLMC_PROF_BOSE, 1, s, slmc::bose_log_weight(c, xc, nf, scal(c, 0), scal(c, 3), s));
@@ -369,7 +371,35 @@ int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int n
                                               obs ? obs + (size_t)u * n + f0 : nullptr, s));
         }
         return SLMC_OK;
-    });
+    }));
+    if (nupdates > 0) SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::counter_op(c, (uint64_t)nupdates, true, s));
+    return SLMC_OK;
+}
+
+int slmc_set_update_counter(slmc_ctx* c, uint64_t value, void* stream) {
+    if (!c) return SLMC_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::counter_op(c, value, false, s));
+    return SLMC_OK;
+}
+
+int slmc_get_update_counter(slmc_ctx* c, uint64_t* value, void* stream) {
+    if (!c || !value) return SLMC_ERR_ARG;
+    unsigned long long v = 0;
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess ||
+        cudaMemcpy(&v, c->dctr, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SLMC_ERR_CUDA;
+    *value = v;
+    return SLMC_OK;
+}
+
+int slmc_set_tuning(slmc_ctx* c, int qr_panel, int slice_cols) {
+    if (!c || (qr_panel != 0 && qr_panel != 16 && qr_panel != 32) ||
+        (slice_cols != 0 && slice_cols != 8 && slice_cols != 16))
+        return SLMC_ERR_ARG;
+    c->tune_qr_panel = qr_panel;
+    c->tune_slice_cols = slice_cols;
+    return SLMC_OK;
 }
 
 int slmc_fit_eff(slmc_ctx* c, const double* xs, const double* lnw, int nconf, double* J_out, double* resid,

@@ -100,9 +100,10 @@ __device__ __forceinline__ double local_energy(const double* J, double a2, doubl
 // and the slice l of the requested colour in the pair (2 (s mod L/2), 2 (s mod L/2) + 1).
 __global__ void __launch_bounds__(kThreads) k_half_sweep(double* __restrict__ x, int Lx, int Ly, int L,
                                                          const double* __restrict__ Jg, double dtau, double a2,
-                                                         double delta, uint32_t key0, uint32_t key1, uint32_t sweep,
+                                                         double delta, uint32_t key0, uint32_t key1, uint32_t sweep_arg,
                                                          int colour, const int* __restrict__ colour_pc, int cxor,
-                                                         int chain0, unsigned long long* __restrict__ n_acc) {
+                                                         int chain0, unsigned long long* __restrict__ n_acc,
+                                                         const unsigned long long* __restrict__ dctr, int nsweeps) {
     __shared__ double J[6];
     __shared__ int s_cnt;
     if (threadIdx.x < 6) J[threadIdx.x] = Jg[threadIdx.x];
@@ -111,27 +112,67 @@ __global__ void __launch_bounds__(kThreads) k_half_sweep(double* __restrict__ x,
     const int f = blockIdx.y;
     const int N = Lx * Ly, half = L / 2;
     const int s = blockIdx.x * kThreads + threadIdx.x;
+    // cumulative updates: sweep counter (update * nsweeps + sweep_arg), update from the device counter
+    const uint32_t sweep = dctr ? (uint32_t)((*dctr) * (unsigned long long)nsweeps + sweep_arg) : sweep_arg;
     int accepted = 0;
     if (s < N * half) {
         const int c = colour_pc ? (colour_pc[f] ^ cxor) : colour;
         const int i = s / half, lp = s - i * half;
         const int ix = i % Lx, iy = i / Lx;
         const int l = 2 * lp + ((ix + iy + c) & 1);
-        double* xf = x + (size_t)f * N * L;
-        const double v = xf[(size_t)i * L + l];
-        const double up = xf[(size_t)i * L + (l + 1 == L ? 0 : l + 1)];
-        const double dn = xf[(size_t)i * L + (l == 0 ? L - 1 : l - 1)];
+        double* xfield = x + (size_t)f * N * L;
+        const double v = xfield[(size_t)i * L + l];
+        const double up = xfield[(size_t)i * L + (l + 1 == L ? 0 : l + 1)];
+        const double dn = xfield[(size_t)i * L + (l == 0 ? L - 1 : l - 1)];
         const int xp = (ix + 1 == Lx ? 0 : ix + 1) + Lx * iy, xm = (ix == 0 ? Lx - 1 : ix - 1) + Lx * iy;
         const int yp = ix + Lx * (iy + 1 == Ly ? 0 : iy + 1), ym = ix + Lx * (iy == 0 ? Ly - 1 : iy - 1);
-        const double nb = xf[(size_t)xp * L + l] + xf[(size_t)xm * L + l] + xf[(size_t)yp * L + l] + xf[(size_t)ym * L + l];
+        const double nb = xfield[(size_t)xp * L + l] + xfield[(size_t)xm * L + l] + xfield[(size_t)yp * L + l] +
+                          xfield[(size_t)ym * L + l];
         const slmc::u32x4 w = slmc::philox4x32_10(slmc::u32x4{(uint32_t)(i * L + l), sweep, (uint32_t)(chain0 + f), 0u}, key0, key1);
-        const double u1 = slmc::uniform53(w.x, w.y), u2 = slmc::uniform53(w.z, w.w);
+        const double u1 = slmc::uniform53(w.x, w.y);
         // x' = x + delta (2 u1 - 1), rounded step by step (no contraction) as in the oracle
         const double xn = __dadd_rn(v, __dmul_rn(delta, __dadd_rn(__dmul_rn(2.0, u1), -1.0)));
-        const double dE = local_energy(J, a2, xn, up, dn, nb) - local_energy(J, a2, v, up, dn, nb);
-        const double dlnw = -dtau * dE;
-        if (dlnw >= 0.0 || u2 < exp(dlnw)) {
-            xf[(size_t)i * L + l] = xn;
+        // Fast decision in FP32: dE = d [2 J_k (s - up - dn) + s (J_p ((x'^2 + x^2)/4 - a^2/2)
+        //   + J_p' ((x'^4 + x'^2 x^2 + x^4)/6 - a^2 (x'^2 + x^2)/4)) + J_nn nb + J_nn' (up + dn)],
+        // d = x' - x, s = x' + x (the exact difference of the local energies, factored). The FP32
+        // verdict is used only when the log-ratio is further from log u than a margin bounding
+        // (i) the FP32 rounding of the bracket (1e-5 of the sum of the magnitudes of its terms,
+        // about 170 units of FP32 rounding), (ii) the rounding of x, x' to FP32, which moves d by
+        // up to 2^-24 (|x| + |x'|), and (iii) the truncation of u to 24 bits (log u is known to
+        // within 2^-24 / u); otherwise the exact FP64 rule of the oracle decides.
+        const float vf = (float)v, xf = (float)xn, upf = (float)up, dnf = (float)dn, nbf = (float)nb;
+        const float d = xf - vf, sm = xf + vf, x2 = xf * xf, v2 = vf * vf, a2f = (float)a2;
+        const float tk = 2.f * (float)J[1] * (sm - upf - dnf);
+        const float tp = sm * (float)J[2] * (0.25f * (x2 + v2) - 0.5f * a2f);
+        const float tpp = sm * (float)J[3] * ((x2 * x2 + x2 * v2 + v2 * v2) * (1.f / 6.f) - 0.25f * a2f * (x2 + v2));
+        const float tn = (float)J[4] * nbf + (float)J[5] * (upf + dnf);
+        const float mag = 2.f * fabsf((float)J[1]) * (fabsf(sm) + fabsf(upf) + fabsf(dnf)) +
+                          fabsf(sm) * (fabsf((float)J[2]) * (x2 + v2 + a2f) +
+                                       fabsf((float)J[3]) * (x2 * x2 + x2 * v2 + v2 * v2 + a2f * (x2 + v2))) +
+                          fabsf((float)J[4] * nbf) + fabsf((float)J[5]) * (fabsf(upf) + fabsf(dnf));
+        const float dlnw32 = -(float)dtau * d * (tk + tp + tpp + tn);
+        const float uf = (float)(w.z >> 8) * 5.9604644775390625e-8f;  // top 24 bits of the acceptance uniform
+        int decided = 0, acc = 0;
+        if (uf > 0.f && isfinite(dlnw32) && isfinite(mag)) {
+            const float lu = logf(uf);
+            const float margin =
+                1e-5f + (float)dtau * mag * (1e-5f * fabsf(d) + 2e-7f * (fabsf(xf) + fabsf(vf))) + 1.2e-7f / uf;
+            if (dlnw32 > lu + margin) {
+                decided = 1;
+                acc = 1;
+            } else if (dlnw32 < lu - margin) {
+                decided = 1;
+                acc = 0;
+            }
+        }
+        if (!decided) {  // exact FP64 rule of the oracle
+            const double u2 = slmc::uniform53(w.z, w.w);
+            const double dE = local_energy(J, a2, xn, up, dn, nb) - local_energy(J, a2, v, up, dn, nb);
+            const double dlnw = -dtau * dE;
+            acc = (dlnw >= 0.0 || u2 < exp(dlnw)) ? 1 : 0;
+        }
+        if (acc) {
+            xfield[(size_t)i * L + l] = xn;
             accepted = 1;
         }
     }
@@ -141,10 +182,11 @@ __global__ void __launch_bounds__(kThreads) k_half_sweep(double* __restrict__ x,
     if (threadIdx.x == 0 && n_acc && s_cnt) atomicAdd(n_acc + f, (unsigned long long)s_cnt);
 }
 
-__global__ void k_update_draws(int nf, int chain0, uint32_t update, uint32_t key0, uint32_t key1,
-                               int* __restrict__ first, double* __restrict__ u) {
+__global__ void k_update_draws(int nf, int chain0, uint32_t u_off, const unsigned long long* __restrict__ dctr,
+                               uint32_t key0, uint32_t key1, int* __restrict__ first, double* __restrict__ u) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
+    const uint32_t update = (uint32_t)(*dctr + u_off);
     const slmc::u32x4 w = slmc::philox4x32_10(slmc::u32x4{update, 0u, (uint32_t)(chain0 + f), 1u}, key0, key1);
     first[f] = (int)(w.x & 1u);
     u[f] = slmc::uniform53(w.z, w.w);
@@ -280,20 +322,21 @@ cudaError_t eff_features(slmc_ctx* c, const double* x, int nf, const double* J, 
 }
 
 cudaError_t eff_half_sweep(slmc_ctx* c, double* x, int nf, int chain0, const double* J, uint64_t sweep, int colour,
-                           const int* colour_per_chain, int colour_xor, long long* n_acc, cudaStream_t s) {
+                           const int* colour_per_chain, int colour_xor, long long* n_acc, cudaStream_t s,
+                           const unsigned long long* dctr, int nsweeps) {
     const double a = c->p.lambda / (c->p.omega0 * c->p.omega0);
     const int sites = c->N * (c->L / 2);
     dim3 grid((sites + kThreads - 1) / kThreads, nf);
     k_half_sweep<<<grid, kThreads, 0, s>>>(x, c->p.Lx, c->p.Ly, c->L, J, c->p.dtau, a * a, c->p.sweep_delta,
                                            (uint32_t)(c->p.seed & 0xffffffffu), (uint32_t)(c->p.seed >> 32),
                                            (uint32_t)sweep, colour, colour_per_chain, colour_xor, chain0,
-                                           reinterpret_cast<unsigned long long*>(n_acc));
+                                           reinterpret_cast<unsigned long long*>(n_acc), dctr, nsweeps);
     return cudaGetLastError();
 }
 
-cudaError_t update_draws(slmc_ctx* c, int nf, int chain0, uint64_t update, int* first_colour, double* u_acc,
+cudaError_t update_draws(slmc_ctx* c, int nf, int chain0, uint64_t u_off, int* first_colour, double* u_acc,
                          cudaStream_t s) {
-    k_update_draws<<<(nf + 127) / 128, 128, 0, s>>>(nf, chain0, (uint32_t)update, (uint32_t)(c->p.seed & 0xffffffffu),
+    k_update_draws<<<(nf + 127) / 128, 128, 0, s>>>(nf, chain0, (uint32_t)u_off, c->dctr, (uint32_t)(c->p.seed & 0xffffffffu),
                                                     (uint32_t)(c->p.seed >> 32), first_colour, u_acc);
     return cudaGetLastError();
 }
@@ -312,6 +355,15 @@ cudaError_t accept_update(slmc_ctx* c, int nf, double* x, const double* x_old, c
 cudaError_t cdw_measure(slmc_ctx* c, const double* G, int nf, double* S, const int* only_if, double* obs,
                         cudaStream_t s) {
     k_cdw<<<nf, kThreads, 0, s>>>(G, c->p.Lx, c->p.Ly, S, only_if, obs);
+    return cudaGetLastError();
+}
+
+__global__ void k_counter(unsigned long long* __restrict__ ctr, unsigned long long v, int add) {
+    if (threadIdx.x == 0) *ctr = add ? *ctr + v : v;
+}
+
+cudaError_t counter_op(slmc_ctx* c, uint64_t v, bool add, cudaStream_t s) {
+    k_counter<<<1, 32, 0, s>>>(c->dctr, (unsigned long long)v, add ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -337,6 +337,7 @@ cudaError_t slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, c
     const double dtlam = c->p.dtau * c->p.lambda;
     if (c->p.precision == SLMC_PREC_FP32) {  // F = E - I as two FP32 terms, identity added in the epilogue
         const int rpt = (c->N + 255) / 256;
+        if (rpt == 1 && c->tune_slice_cols == 8) return launch_slice_f32<1, 8>(c, x, nf, l0, nsl, s);
         if (rpt == 1) return launch_slice_f32<1, 16>(c, x, nf, l0, nsl, s);
         if (rpt == 2) return launch_slice_f32<2, 8>(c, x, nf, l0, nsl, s);
         if (rpt == 3) return launch_slice_f32<3, 8>(c, x, nf, l0, nsl, s);

@@ -438,15 +438,20 @@ cudaError_t launch_formq_b(slmc_ctx* c, int nf, cudaStream_t s) {
 
 namespace slmc {
 
-int qr_panel_width(int N) { return N <= 256 ? 32 : 16; }
+// Panel width: the tuned value if set and its shared memory fits, else 32 up to N = 256 and 16 above.
+int qr_panel_width(const slmc_ctx* c) {
+    const int want = c->tune_qr_panel ? c->tune_qr_panel : (c->N <= 256 ? 32 : 16);
+    if (want == 32 && QrSmem<32>::bytes(c->N) > 220 * 1024) return 16;
+    return want;
+}
 
 cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s) {
-    return qr_panel_width(c->N) == 32 ? launch_qrb<32>(c, nf, s) : launch_qrb<16>(c, nf, s);
+    return qr_panel_width(c) == 32 ? launch_qrb<32>(c, nf, s) : launch_qrb<16>(c, nf, s);
 }
 
 cudaError_t form_q_blocked(slmc_ctx* c, int nf, bool fp32, cudaStream_t s) {
-    if (fp32) return qr_panel_width(c->N) == 32 ? launch_formq_b<32, float>(c, nf, s) : launch_formq_b<16, float>(c, nf, s);
-    return qr_panel_width(c->N) == 32 ? launch_formq_b<32, double>(c, nf, s) : launch_formq_b<16, double>(c, nf, s);
+    if (fp32) return qr_panel_width(c) == 32 ? launch_formq_b<32, float>(c, nf, s) : launch_formq_b<16, float>(c, nf, s);
+    return qr_panel_width(c) == 32 ? launch_formq_b<32, double>(c, nf, s) : launch_formq_b<16, double>(c, nf, s);
 }
 
 cudaError_t t_update_tiled(slmc_ctx* c, int nf, cudaStream_t s) {

@@ -48,6 +48,9 @@ struct slmc_ctx {
     double* feat;    // [max_fields][8]
     double* fitR;    // [64] Givens-QR state of the regression
     unsigned int* err;
+    unsigned long long* dctr;  // device-side cumulative-update counter (Philox stream position)
+    int tune_qr_panel;          // 0: by N; else 16 or 32 (blocked QR panel width)
+    int tune_slice_cols;        // 0: by N; else 8 or 16 (FP32 slice columns per thread)
     // Tensor-core slice path (SLMC_PREC_TF32X3 / BF16X9): operand pieces of F and of the
     // running slice product (ping/pong), FP32 copies of it, and their TMA descriptors.
     int tc_npad, tc_nt;
@@ -121,7 +124,7 @@ int tc_launches(int nsl);
 cudaError_t t_update_tiled(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t form_q_blocked(slmc_ctx* c, int nf, bool fp32, cudaStream_t s);
-int qr_panel_width(int N);
+int qr_panel_width(const slmc_ctx* c);
 cudaError_t qr_pivoted(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t form_q(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t set_identity(slmc_ctx* c, int nf, cudaStream_t s);
@@ -134,9 +137,10 @@ cudaError_t eff_features(slmc_ctx* c, const double* x, int nf, const double* J, 
                          double* lnw_eff, cudaStream_t s);
 cudaError_t eff_half_sweep(slmc_ctx* c, double* x, int nf, int chain0, const double* J, uint64_t sweep,
                            int colour, const int* colour_per_chain, int colour_xor, long long* n_acc,
-                           cudaStream_t s);
-cudaError_t update_draws(slmc_ctx* c, int nf, int chain0, uint64_t update, int* first_colour, double* u_acc,
+                           cudaStream_t s, const unsigned long long* dctr = nullptr, int nsweeps = 0);
+cudaError_t update_draws(slmc_ctx* c, int nf, int chain0, uint64_t u_off, int* first_colour, double* u_acc,
                          cudaStream_t s);
+cudaError_t counter_op(slmc_ctx* c, uint64_t v, bool add, cudaStream_t s);
 cudaError_t accept_update(slmc_ctx* c, int nf, double* x, const double* x_old, const double* lnw_new,
                           const double* lnweff_old, const double* lnweff_new, const double* u_acc,
                           double* lnw, int* accepted, long long* n_acc, cudaStream_t s);

@@ -34,7 +34,16 @@ QR_MODE = {"prepivot": 0, "pivoted": 1}
 EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", "slmc_logdet", "slmc_greens",
            "slmc_log_weight", "slmc_eff_features", "slmc_eff_log_weight", "slmc_eff_sweep", "slmc_chain_init",
            "slmc_cumulative_update", "slmc_fit_eff", "slmc_measure_cdw", "slmc_launch_count", "slmc_profile_enable",
-           "slmc_profile_read", "slmc_logdet_noalloc", "slmc_logdet_noalloc_scratch_bytes")
+           "slmc_profile_read", "slmc_logdet_noalloc", "slmc_logdet_noalloc_scratch_bytes", "slmc_set_update_counter",
+           "slmc_get_update_counter", "slmc_set_tuning", "slmc_batch_create", "slmc_batch_destroy",
+           "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune")
+
+UPDATE_CONTINUE = (1 << 64) - 1
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("n_s", ctypes.c_int), ("qr_panel", ctypes.c_int), ("slice_cols", ctypes.c_int),
+                ("sec_per_eval", ctypes.c_double), ("max_abs_dlndet", ctypes.c_double), ("candidates", ctypes.c_int)]
 
 PROF_CLASSES = ("slice", "qr", "formq", "tupdate", "final", "greens", "sweep", "eff", "bose", "accept", "fit", "cdw")
 
@@ -71,6 +80,16 @@ def load_library(path=LIB_PATH):
         "slmc_profile_read": ([P, P, P, V], I),
         "slmc_logdet_noalloc": ([ctypes.POINTER(Params), P, I, P, P, V], I),
         "slmc_logdet_noalloc_scratch_bytes": ([], ctypes.c_size_t),
+        "slmc_set_update_counter": ([P, U64, V], I),
+        "slmc_get_update_counter": ([P, ctypes.POINTER(ctypes.c_uint64), V], I),
+        "slmc_set_tuning": ([P, I, I], I),
+        "slmc_batch_create": ([ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(P)], I),
+        "slmc_batch_destroy": ([P], I),
+        "slmc_batch_context": ([P, I], P),
+        "slmc_batch_bind": ([P, I, P, P, P, P, P, P], I),
+        "slmc_batch_capture": ([P, I, I, V], I),
+        "slmc_batch_launch": ([P, I, V], I),
+        "slmc_autotune": ([ctypes.POINTER(Params), I, D, ctypes.POINTER(TuneResult)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -236,6 +255,18 @@ class Context:
         self._check("slmc_profile_read", self.lib.slmc_profile_read(self._ctx, ms, calls, _stream(self.device)))
         return {k: (ms[q], calls[q]) for q, k in enumerate(PROF_CLASSES)}
 
+    def set_update_counter(self, value):
+        self._check("slmc_set_update_counter", self.lib.slmc_set_update_counter(self._ctx, value, _stream(self.device)))
+
+    def get_update_counter(self):
+        v = ctypes.c_uint64()
+        self._check("slmc_get_update_counter", self.lib.slmc_get_update_counter(self._ctx, ctypes.byref(v),
+                                                                                _stream(self.device)))
+        return v.value
+
+    def set_tuning(self, qr_panel=0, slice_cols=0):
+        self._check("slmc_set_tuning", self.lib.slmc_set_tuning(self._ctx, qr_panel, slice_cols))
+
     def measure_cdw(self, G):
         n = G.shape[0]
         S = self._empty(n)
@@ -243,6 +274,95 @@ class Context:
             self._ctx, _ptr(G, torch.float64, "G", (n, self.N, self.N)), n, _ptr(S, torch.float64, "S"),
             _stream(self.device)))
         return S
+
+
+class _BorrowedContext(Context):
+    """A context owned by a Batch (not destroyed by this wrapper)."""
+
+    def __init__(self, handle, Lx, Ly, L, device):
+        self.lib = load_library()
+        self._ctx = ctypes.c_void_p(handle)
+        self.device = device
+        self.Lx, self.Ly, self.L, self.N = Lx, Ly, L, Lx * Ly
+
+    def close(self):
+        self._ctx = ctypes.c_void_p()
+
+
+class Batch:
+    """Chains of several lattice classes advanced together through one captured CUDA graph
+    (slmc_batch_*). classes: list of dicts of Context keyword arguments plus "nchains"."""
+
+    def __init__(self, classes, device=None):
+        self.lib = load_library()
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.device = torch.device("cuda", torch.cuda.current_device() if dev.index is None else dev.index)
+        n = len(classes)
+        arr = (Params * n)()
+        nch = (ctypes.c_int * n)()
+        self.shapes = []
+        for q, cl in enumerate(classes):
+            arr[q] = Params(cl["Lx"], cl.get("Ly", cl["Lx"]), cl["L"], cl.get("dtau", 0.1), cl.get("t", 1.0),
+                            cl.get("mu", 0.0), cl.get("omega0", 1.0), cl.get("lam", 1.0), cl.get("n_s", 10),
+                            PRECISION[cl.get("precision", "fp64")], cl.get("sweep_delta", 0.5),
+                            cl.get("seed", 0) & ((1 << 64) - 1), QR_MODE[cl.get("qr_mode", "prepivot")])
+            nch[q] = cl["nchains"]
+            self.shapes.append((cl["Lx"], cl.get("Ly", cl["Lx"]), cl["L"], cl["nchains"]))
+        self._b = ctypes.c_void_p()
+        self._keep = []
+        self.stream = torch.cuda.Stream(device=self.device)
+        with torch.cuda.device(self.device):
+            st = self.lib.slmc_batch_create(arr, nch, n, ctypes.byref(self._b))
+        if st != 0:
+            raise SlmcError("slmc_batch_create", st)
+
+    def context(self, cls):
+        Lx, Ly, L, _ = self.shapes[cls]
+        return _BorrowedContext(self.lib.slmc_batch_context(self._b, cls), Lx, Ly, L, self.device)
+
+    def bind(self, cls, x, J, lnw, s_cdw=None, n_acc=None, n_sweep_acc=None):
+        Lx, Ly, L, nch = self.shapes[cls]
+        self._keep.append((x, J, lnw, s_cdw, n_acc, n_sweep_acc))
+        st = self.lib.slmc_batch_bind(self._b, cls, _ptr(x, torch.float64, "x", (nch, Lx * Ly, L)),
+                                      _ptr(J, torch.float64, "J", (6,)), _ptr(lnw, torch.float64, "lnw", (nch,)),
+                                      _ptr(s_cdw, torch.float64, "s_cdw", (nch,)), _ptr(n_acc, torch.int64, "n_acc", (nch,)),
+                                      _ptr(n_sweep_acc, torch.int64, "n_sweep_acc", (nch,)))
+        if st != 0:
+            raise SlmcError("slmc_batch_bind", st)
+
+    def capture(self, nsweeps, nupdates=1):
+        st = self.lib.slmc_batch_capture(self._b, nsweeps, nupdates, self.stream.cuda_stream)
+        if st != 0:
+            raise SlmcError("slmc_batch_capture", st)
+
+    def launch(self, nrounds=1):
+        st = self.lib.slmc_batch_launch(self._b, nrounds, self.stream.cuda_stream)
+        if st != 0:
+            raise SlmcError("slmc_batch_launch", st)
+
+    def close(self):
+        if self._b:
+            self.lib.slmc_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(Lx, Ly, L, precision="fp32", ntune=32, tol=5e-5, qr_mode="prepivot", dtau=0.1, t=1.0, mu=0.0,
+             omega0=1.0, lam=1.0, seed=0):
+    """slmc_autotune: fastest (n_s, QR panel, FP32 tile) within tol of the FP64 path."""
+    lib = load_library()
+    p = Params(Lx, Ly, L, dtau, t, mu, omega0, lam, 8, PRECISION[precision], 0.0, seed, QR_MODE[qr_mode])
+    r = TuneResult()
+    st = lib.slmc_autotune(ctypes.byref(p), ntune, tol, ctypes.byref(r))
+    if st != 0:
+        raise SlmcError("slmc_autotune", st)
+    return {"n_s": r.n_s, "qr_panel": r.qr_panel, "slice_cols": r.slice_cols, "sec_per_eval": r.sec_per_eval,
+            "max_abs_dlndet": r.max_abs_dlndet, "candidates": r.candidates}
 
 
 def logdet_noalloc(x, Lx, Ly, L, dtau=0.1, t=1.0, mu=0.0, omega0=1.0, lam=1.0, n_s=10, precision="fp64",

@@ -12,7 +12,7 @@ HEADER = os.path.join(ROOT, "include", "slmc.h")
 
 def declared_symbols():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"SLMC_API\s+(?:const\s+char\s*\*|long\s+long|size_t|int)\s+(slmc_\w+)\s*\(", text)))
+    return sorted(set(re.findall(r"SLMC_API\s+(?:const\s+char\s*\*|long\s+long|size_t|slmc_ctx\s*\*|int)\s+(slmc_\w+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
