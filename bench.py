@@ -245,6 +245,7 @@ def run_gpu(args):
     import torch
 
     from paper_1802_06177_gb300 import inputs
+    from paper_1802_06177_gb300.dist import fit_eff_distributed
     from paper_1802_06177_gb300.slmc import Context
     from paper_1802_06177_gb300.workloads import WORKLOADS
 
@@ -280,7 +281,8 @@ def run_gpu(args):
             ctx.logdet(st["x"])
             return
         ctx.cumulative_update(st["x"], st["J"], args.nsweeps, 1, k, st["lnw"], st["s"], st["n_acc"], st["n_sw"])
-        st["J_fit"], _ = ctx.fit_eff(st["x"], st["lnw"])
+        # Eq. (5) over the chains of every process: partial state, all-gather (N > 1), merge
+        st["J_fit"], _ = fit_eff_distributed(ctx, st["x"], st["lnw"])
 
     def timed(ctx, st, steps, warmup, k0, profile=False, clocks=False):
         for k in range(warmup):

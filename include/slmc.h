@@ -207,6 +207,28 @@ SLMC_API int slmc_set_tuning(slmc_ctx* ctx, int qr_panel, int slice_cols);
 SLMC_API int slmc_fit_eff(slmc_ctx* ctx, const double* xs, const double* lnw, int nconf, double* J_out,
                  double* resid, void* stream);
 
+/* The regression of Eq. (5) split over several processes (each holding its own chains):
+ * every process reduces its configurations to a fixed-size state, the states are exchanged
+ * (an all-gather of SLMC_FIT_STATE_DOUBLES doubles per process, done by the caller), and every
+ * process merges all states into the same couplings.
+ * State layout (FP64): [0..48] the 7x7 triangular factor R (row-major) of the rows
+ * [1, (F - F_ref)/(N L), lnw - lnw_ref]; [49..54] F_ref[5], lnw_ref (the first configuration
+ * of the call); [55] 1 if the state holds data, else 0; [56] number of configurations;
+ * [57..63] zero. Configurations are centred for conditioning only: the merge shifts every
+ * state to one reference exactly (a unit upper-triangular change of columns), so the merged
+ * fit equals the fit of all configurations at once up to rounding.
+ *   slmc_fit_eff_state: xs [nconf][N][L], lnw [nconf]; nconf >= 0 (0 gives an empty state);
+ *                       state [SLMC_FIT_STATE_DOUBLES] device output.
+ *   slmc_fit_eff_merge: states [nparts][SLMC_FIT_STATE_DOUBLES] device input (nparts >= 1;
+ *                       empty states are skipped), J_out [6] and resid [1] (may be NULL) as in
+ *                       slmc_fit_eff. Fewer than 6 configurations in total, or linearly
+ *                       dependent features, set the SINGULAR flag (slmc_get_error). */
+#define SLMC_FIT_STATE_DOUBLES 64
+SLMC_API int slmc_fit_eff_state(slmc_ctx* ctx, const double* xs, const double* lnw, int nconf, double* state,
+                                void* stream);
+SLMC_API int slmc_fit_eff_merge(slmc_ctx* ctx, const double* states, int nparts, double* J_out, double* resid,
+                                void* stream);
+
 /* CDW structure factor per configuration [Sec. "Results"] from G [n][N][N] (row-major):
  * S = (1/N) sum_ij s_i s_j [4 (1 - G_ii)(1 - G_jj) + 2 (delta_ij - G_ji) G_ij],
  * s_i = (-1)^(ix+iy). Output S[n]. */

@@ -97,32 +97,88 @@ bool checkerboard_ok(const slmc_ctx* c) { return c->p.Lx % 2 == 0 && c->p.Ly % 2
 double* scal(slmc_ctx* c, int col) { return c->scal + (size_t)col * c->max_fields; }
 int* iscal(slmc_ctx* c, int col) { return c->iscal + (size_t)col * c->max_fields; }
 
-// Stabilised UDT chain + final LU for fields [0, nf) of one batch (nf <= max_fields).
-int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, double* G, cudaStream_t s) {
-    SLMC_LAUNCH(SLMC_PROF_FINAL, 1, s, slmc::set_identity(c, nf, s));
-    if (c->p.precision != SLMC_PREC_FP64) SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_scales(c, x, nf, s));
-    for (int l0 = 0; l0 < c->L; l0 += c->p.n_s) {
-        const int nsl = std::min(c->p.n_s, c->L - l0);
-        if (c->p.precision == SLMC_PREC_TF32X3 || c->p.precision == SLMC_PREC_BF16X9)
-            SLMC_LAUNCH(SLMC_PROF_SLICE, slmc::tc_launches(nsl), s, slmc::tc_slice_group(c, x, nf, l0, nsl, s));
+// Stabilised UDT chain + final LU for fields [0, nf) of the context (or view) v; launches are
+// accounted on `c` (the owning context).
+int logdet_run(slmc_ctx* c, slmc_ctx* v, const double* x, int nf, double* lndet, int* sign, double* G,
+               cudaStream_t s) {
+    SLMC_LAUNCH(SLMC_PROF_FINAL, 1, s, slmc::set_identity(v, nf, s));
+    if (v->p.precision != SLMC_PREC_FP64) SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_scales(v, x, nf, s));
+    for (int l0 = 0; l0 < v->L; l0 += v->p.n_s) {
+        const int nsl = std::min(v->p.n_s, v->L - l0);
+        if (v->p.precision == SLMC_PREC_TF32X3 || v->p.precision == SLMC_PREC_BF16X9)
+            SLMC_LAUNCH(SLMC_PROF_SLICE, slmc::tc_launches(nsl), s, slmc::tc_slice_group(v, x, nf, l0, nsl, s));
         else
-            SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_group(c, x, nf, l0, nsl, s));
-        if (c->p.qr_mode == SLMC_QR_PIVOTED) {
-            SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_pivoted(c, nf, s));
-            SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q(c, nf, s));
-            if (c->p.precision != SLMC_PREC_FP64 && l0 + nsl < c->L)
-                SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::u_to_f32(c, nf, s));
+            SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_group(v, x, nf, l0, nsl, s));
+        if (v->p.qr_mode == SLMC_QR_PIVOTED) {
+            SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_pivoted(v, nf, s));
+            SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q(v, nf, s));
+            if (v->p.precision != SLMC_PREC_FP64 && l0 + nsl < v->L)
+                SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::u_to_f32(v, nf, s));
         } else {
-            SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_blocked(c, nf, s));
+            SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_blocked(v, nf, s));
             // Q enters the next reduced-precision slice group (rounded to FP32 there anyway) except
             // after the last group, where it enters the FP64 final step.
-            const bool q32 = c->p.precision != SLMC_PREC_FP64 && l0 + nsl < c->L;
-            SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q_blocked(c, nf, q32, s));
+            const bool q32 = v->p.precision != SLMC_PREC_FP64 && l0 + nsl < v->L;
+            SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q_blocked(v, nf, q32, s));
         }
-        SLMC_LAUNCH(SLMC_PROF_TUPDATE, 1, s, slmc::t_update_tiled(c, nf, s));
+        SLMC_LAUNCH(SLMC_PROF_TUPDATE, 1, s, slmc::t_update_tiled(v, nf, s));
     }
-    SLMC_LAUNCH(SLMC_PROF_FINAL, 2, s, slmc::final_logdet(c, nf, lndet, sign, s));
-    if (G) SLMC_LAUNCH(SLMC_PROF_GREENS, 1, s, slmc::final_greens(c, nf, G, s));
+    SLMC_LAUNCH(SLMC_PROF_FINAL, 2, s, slmc::final_logdet(v, nf, lndet, sign, s));
+    if (G) SLMC_LAUNCH(SLMC_PROF_GREENS, 1, s, slmc::final_greens(v, nf, G, s));
+    return SLMC_OK;
+}
+
+
+constexpr int kMinSubFields = 32;
+
+// A view of context c for fields [f0, ...): per-field workspace pointers offset by f0.
+slmc_ctx make_view(slmc_ctx* c, int f0) {
+    slmc_ctx v{};
+    v.p = c->p;
+    v.N = c->N;
+    v.L = c->L;
+    v.max_fields = c->max_fields;
+    v.device = c->device;
+    const size_t N = c->N, NN = N * N, F0 = (size_t)f0;
+    v.E64 = c->E64;
+    v.F32 = c->F32;
+    v.F32lo = c->F32lo;
+    v.sc32 = c->sc32 ? c->sc32 + F0 * c->L * N : nullptr;
+    v.Y = c->Y + F0 * NN;
+    v.QR = c->QR + F0 * NN;
+    v.U = c->U + F0 * NN;
+    v.U32 = c->U32 ? c->U32 + F0 * NN : nullptr;
+    v.Ta = c->Ta + F0 * NN;
+    v.Tb = c->Tb + F0 * NN;
+    v.lnD = c->lnD + F0 * N;
+    v.tau = c->tau + F0 * N;
+    v.perm = c->perm + F0 * N;
+    v.piv = c->piv + F0 * N;
+    v.sgnU = c->sgnU + F0;
+    v.Sws = c->Sws + F0 * N * 32;
+    v.err = c->err;
+    v.dctr = c->dctr;
+    v.tune_qr_panel = c->tune_qr_panel;
+    v.tune_slice_cols = c->tune_slice_cols;
+    v.nsub = 0;
+    v.parent = c;
+    return v;
+}
+
+int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, double* G, cudaStream_t s) {
+    const bool tc = c->p.precision == SLMC_PREC_TF32X3 || c->p.precision == SLMC_PREC_BF16X9;
+    if (c->nsub < 2 || tc || nf < 2 * kMinSubFields) return logdet_run(c, c, x, nf, lndet, sign, G, s);
+    const size_t NL = (size_t)c->N * c->L, NN = (size_t)c->N * c->N;
+    SLMC_CK(cudaEventRecord(c->sub_fork, s));
+    for (int k = 0; k < c->nsub; ++k) {
+        const int f0 = (int)((long long)k * nf / c->nsub), f1 = (int)((long long)(k + 1) * nf / c->nsub);
+        SLMC_CK(cudaStreamWaitEvent(c->sub_stream[k], c->sub_fork, 0));
+        slmc_ctx v = make_view(c, f0);
+        SLMC_TRY(logdet_run(c, &v, x + f0 * NL, f1 - f0, lndet + f0, sign + f0, G ? G + f0 * NN : nullptr,
+                            c->sub_stream[k]));
+        SLMC_CK(cudaEventRecord(c->sub_join[k], c->sub_stream[k]));
+        SLMC_CK(cudaStreamWaitEvent(s, c->sub_join[k], 0));
+    }
     return SLMC_OK;
 }
 
@@ -136,6 +192,11 @@ int for_batches(slmc_ctx* c, int n, F&& fn) {
 }
 
 void free_ctx(slmc_ctx* c) {
+    for (int k = 0; k < slmc_ctx::kMaxSub; ++k) {
+        if (c->sub_stream[k]) cudaStreamDestroy(c->sub_stream[k]);
+        if (c->sub_join[k]) cudaEventDestroy(c->sub_join[k]);
+    }
+    if (c->sub_fork) cudaEventDestroy(c->sub_fork);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
     void* bufs[] = {c->E64, c->F32, c->F32lo, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
@@ -237,6 +298,15 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
         cudaGetLastError();
         free_ctx(c);
         return SLMC_ERR_NOMEM;
+    }
+    c->nsub = 0;
+    if (max_fields >= 2 * kMinSubFields) {
+        bool sok = cudaEventCreateWithFlags(&c->sub_fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; k < slmc_ctx::kMaxSub && sok; ++k)
+            sok = cudaStreamCreateWithFlags(&c->sub_stream[k], cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->sub_join[k], cudaEventDisableTiming) == cudaSuccess;
+        if (sok) c->nsub = slmc_ctx::kMaxSub;
+        else cudaGetLastError();
     }
     if (cudaMemset(c->err, 0, sizeof(unsigned int)) != cudaSuccess ||
         slmc::build_hopping_exp(c, nullptr) != cudaSuccess || (tc && slmc::tc_init(c, nullptr) != cudaSuccess) ||
@@ -407,13 +477,34 @@ int slmc_fit_eff(slmc_ctx* c, const double* xs, const double* lnw, int nconf, do
     if (!c || nconf < 6 || !xs || !lnw || !J_out) return SLMC_ERR_ARG;
     const size_t NL = (size_t)c->N * c->L;
     cudaStream_t s = as_stream(stream);
-    SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_begin(c, s));
+    SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_begin(c, c->fitR, s));
     SLMC_TRY(for_batches(c, nconf, [&](int f0, int nf) {
         SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, xs + f0 * NL, nf, nullptr, c->feat, 8, nullptr, s));
-        SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_accumulate(c, c->feat, lnw + f0, nf, s));
+        SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_accumulate(c, c->fitR, c->feat, lnw + f0, nf, s));
         return SLMC_OK;
     }));
     SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_finish(c, nconf, J_out, resid, s));
+    return SLMC_OK;
+}
+
+int slmc_fit_eff_state(slmc_ctx* c, const double* xs, const double* lnw, int nconf, double* state, void* stream) {
+    if (!c || nconf < 0 || !state || (nconf > 0 && (!xs || !lnw))) return SLMC_ERR_ARG;
+    const size_t NL = (size_t)c->N * c->L;
+    cudaStream_t s = as_stream(stream);
+    SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_begin(c, state, s));
+    SLMC_TRY(for_batches(c, nconf, [&](int f0, int nf) {
+        SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, xs + f0 * NL, nf, nullptr, c->feat, 8, nullptr, s));
+        SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_accumulate(c, state, c->feat, lnw + f0, nf, s));
+        return SLMC_OK;
+    }));
+    return SLMC_OK;
+}
+
+int slmc_fit_eff_merge(slmc_ctx* c, const double* states, int nparts, double* J_out, double* resid, void* stream) {
+    if (!c || !states || nparts < 1 || !J_out) return SLMC_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_merge(c, states, nparts, s));
+    SLMC_LAUNCH(SLMC_PROF_FIT, 1, s, slmc::fit_finish(c, 0, J_out, resid, s));
     return SLMC_OK;
 }
 

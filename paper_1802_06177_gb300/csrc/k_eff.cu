@@ -247,6 +247,26 @@ __global__ void k_fit_begin(double* __restrict__ R) {
     for (int q = threadIdx.x; q < 64; q += blockDim.x) R[q] = 0.0;
 }
 
+// Absorbs one row (lane m < 7 holds its element m) into the triangular factor held by the warp
+// (lane m holds column m of every row of R) with Givens rotations.
+__device__ __forceinline__ void givens_absorb(double (&Rrow)[7], double a, int lane) {
+    for (int k = 0; k < 7; ++k) {
+        const double ak = __shfl_sync(0xffffffffu, a, k);
+        const double rkk = __shfl_sync(0xffffffffu, Rrow[k], k);
+        if (ak == 0.0) continue;
+        const double r = hypot(rkk, ak);
+        const double cs = rkk / r, sn = ak / r;
+        if (lane == k) {
+            Rrow[k] = r;
+            a = 0.0;
+        } else if (lane > k && lane < 7) {
+            const double rk = Rrow[k];
+            Rrow[k] = cs * rk + sn * a;
+            a = -sn * rk + cs * a;
+        }
+    }
+}
+
 __global__ void k_fit_accumulate(double* __restrict__ R, const double* __restrict__ feat, int ldF,
                                  const double* __restrict__ lnw, int nconf, double sc) {
     // one warp: lane m < 7 holds column m of the current row and of R's rows
@@ -265,25 +285,50 @@ __global__ void k_fit_accumulate(double* __restrict__ R, const double* __restric
         else if (lane < 6) a = (feat[(size_t)c * ldF + lane - 1] - R[49 + lane - 1]) / sc;
         else if (lane == 6) a = lnw[c] - R[54];
         else a = 0.0;
-        for (int k = 0; k < 7; ++k) {
-            const double ak = __shfl_sync(0xffffffffu, a, k);
-            const double rkk = __shfl_sync(0xffffffffu, Rrow[k], k);
-            if (ak == 0.0) continue;
-            const double r = hypot(rkk, ak);
-            const double cs = rkk / r, sn = ak / r;
-            if (lane == k) {
-                Rrow[k] = r;
-                a = 0.0;
-            } else if (lane > k && lane < 7) {
-                const double rk = Rrow[k];
-                Rrow[k] = cs * rk + sn * a;
-                a = -sn * rk + cs * a;
-            }
-        }
+        givens_absorb(Rrow, a, lane);
     }
     for (int k = 0; k < 7; ++k)
         if (lane < 7) R[k * 7 + lane] = Rrow[k];
     if (lane == 0) R[56] += nconf;
+}
+
+// Merges partial states (same layout as R) into R. Each state's factor is first moved to the
+// reference of the first non-empty state: its rows [1, (F - F_b)/sc, y - y_b] equal the rows
+// [1, (F - F_c)/sc, y - y_c] minus row 0 times d, d = ((F_b - F_c)/sc, y_b - y_c), i.e. the
+// columns change by a unit upper-triangular matrix, which touches only row 0 of R.
+__global__ void k_fit_merge(const double* __restrict__ states, int nparts, double* __restrict__ R, double sc) {
+    const int lane = threadIdx.x;
+    int ref = -1;
+    for (int p = 0; p < nparts; ++p)
+        if (states[(size_t)p * SLMC_FIT_STATE_DOUBLES + 55] != 0.0) {
+            ref = p;
+            break;
+        }
+    const double* C = states + (size_t)(ref < 0 ? 0 : ref) * SLMC_FIT_STATE_DOUBLES;
+    double Rrow[7];
+    for (int k = 0; k < 7; ++k) Rrow[k] = 0.0;
+    double count = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+        const double* S = states + (size_t)p * SLMC_FIT_STATE_DOUBLES;
+        if (S[55] == 0.0) continue;
+        count += S[56];
+        for (int k = 0; k < 7; ++k) {
+            double a = (lane < 7) ? S[k * 7 + lane] : 0.0;
+            if (k == 0 && lane >= 1 && lane < 7) {
+                const double d = (lane < 6) ? (S[49 + lane - 1] - C[49 + lane - 1]) / sc : S[54] - C[54];
+                a = fma(S[0], d, a);
+            }
+            givens_absorb(Rrow, a, lane);
+        }
+    }
+    for (int k = 0; k < 7; ++k)
+        if (lane < 7) R[k * 7 + lane] = Rrow[k];
+    if (lane < 6) R[49 + lane] = (ref < 0) ? 0.0 : C[49 + lane];
+    if (lane == 0) {
+        R[55] = (ref < 0) ? 0.0 : 1.0;
+        R[56] = count;
+    }
+    if (lane >= 7 && lane < 14) R[57 + lane - 7] = 0.0;
 }
 
 __global__ void k_fit_finish(const double* __restrict__ R, double dtau, double sc, double* __restrict__ J,
@@ -367,13 +412,19 @@ cudaError_t counter_op(slmc_ctx* c, uint64_t v, bool add, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t fit_begin(slmc_ctx* c, cudaStream_t s) {
-    k_fit_begin<<<1, 64, 0, s>>>(c->fitR);
+cudaError_t fit_begin(slmc_ctx* c, double* R, cudaStream_t s) {
+    (void)c;
+    k_fit_begin<<<1, 64, 0, s>>>(R);
     return cudaGetLastError();
 }
 
-cudaError_t fit_accumulate(slmc_ctx* c, const double* feat, const double* lnw, int nconf, cudaStream_t s) {
-    k_fit_accumulate<<<1, 32, 0, s>>>(c->fitR, feat, 8, lnw, nconf, (double)c->N * c->L);
+cudaError_t fit_accumulate(slmc_ctx* c, double* R, const double* feat, const double* lnw, int nconf, cudaStream_t s) {
+    k_fit_accumulate<<<1, 32, 0, s>>>(R, feat, 8, lnw, nconf, (double)c->N * c->L);
+    return cudaGetLastError();
+}
+
+cudaError_t fit_merge(slmc_ctx* c, const double* states, int nparts, cudaStream_t s) {
+    k_fit_merge<<<1, 32, 0, s>>>(states, nparts, c->fitR, (double)c->N * c->L);
     return cudaGetLastError();
 }
 

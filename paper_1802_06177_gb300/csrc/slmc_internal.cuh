@@ -59,6 +59,14 @@ struct slmc_ctx {
     float* tc_y32[2];   // [max_fields][N][N]
     CUtensorMap tc_mapF;
     CUtensorMap tc_mapP[2];
+    // Sub-batches: a large logdet batch is split over nsub forked streams so that the
+    // kernels of one sub-batch fill the tails of the other's. A view is a shallow copy of the
+    // context with the per-field workspace pointers offset; parent points to the owner.
+    static constexpr int kMaxSub = 2;
+    int nsub;
+    cudaStream_t sub_stream[kMaxSub];
+    cudaEvent_t sub_fork, sub_join[kMaxSub];
+    slmc_ctx* parent;
     // Launch accounting and optional per-class event timing (host side).
     long long launches;
     bool prof_on;
@@ -146,9 +154,10 @@ cudaError_t accept_update(slmc_ctx* c, int nf, double* x, const double* x_old, c
                           double* lnw, int* accepted, long long* n_acc, cudaStream_t s);
 cudaError_t cdw_measure(slmc_ctx* c, const double* G, int nf, double* S, const int* only_if,
                         double* obs, cudaStream_t s);
-cudaError_t fit_begin(slmc_ctx* c, cudaStream_t s);
-cudaError_t fit_accumulate(slmc_ctx* c, const double* feat, const double* lnw, int nconf,
+cudaError_t fit_begin(slmc_ctx* c, double* R, cudaStream_t s);
+cudaError_t fit_accumulate(slmc_ctx* c, double* R, const double* feat, const double* lnw, int nconf,
                            cudaStream_t s);
+cudaError_t fit_merge(slmc_ctx* c, const double* states, int nparts, cudaStream_t s);
 cudaError_t fit_finish(slmc_ctx* c, int nconf, double* J_out, double* resid, cudaStream_t s);
 int validate_params(const slmc_params* p);
 int logdet_fields(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, cudaStream_t s);

@@ -11,6 +11,9 @@ Steps (Sec. "SLMC" and Suppl. Sec. "SLMC for the Holstein model"):
   3. production: cumulative updates (Eq. (6)) with the learned couplings, measuring the CDW
      structure factor S(pi, pi) after every update and counting acceptances.
 Error bars: the per-chain time series are averaged over chains, then binned in time.
+Under torchrun every process runs its own chains on its own GPU (Philox key = seed + rank);
+the regression is fitted over all processes' configurations (paper_1802_06177_gb300.dist)
+and the measurements are summed over processes; rank 0 prints the result.
 
 python -m paper_1802_06177_gb300.pipeline --Lx 24 --L 240 --n-s 8 --chains 32 --train 2000 \
     --updates 500 --sweeps 100 --precision fp32
@@ -24,6 +27,7 @@ import numpy as np
 import torch
 
 from . import inputs
+from .dist import fit_eff_distributed, sum_over_processes
 from .slmc import UPDATE_CONTINUE, Context
 
 
@@ -37,8 +41,9 @@ def binned_error(series, nbins=10):
 
 
 def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision="fp32", dtau=0.1, lam=1.0,
-        omega0=1.0, sweep_delta=0.3, seed=0x1802061774, rounds=2, device="cuda"):
+        omega0=1.0, sweep_delta=0.3, seed=0x1802061774, rounds=2, device="cuda", rank=0, world=1):
     dev = torch.device(device)
+    seed = seed + rank
     ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
                   sweep_delta=sweep_delta, seed=seed, max_fields=chains, device=dev)
     N = Lx * Lx
@@ -49,7 +54,7 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
     lnw, s = ctx.chain_init(x)
     ctx.set_update_counter(0)
     # ---- self-learning rounds: generate configurations with the current couplings, refit ----
-    per_round = max(1, math.ceil(train / chains))
+    per_round = max(1, math.ceil(train / (chains * world)))
     history = []
     sweep_ctr = 1 << 30  # training proposals use Philox sweep counters far from the production ones
     for r in range(rounds):
@@ -62,11 +67,13 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
             lw_p, _, _ = ctx.log_weight(xp)
             xs.append(xp.clone())
             ys.append(lw_p)
-        X = torch.cat(xs)[:train]
-        Y = torch.cat(ys)[:train]
-        J, resid = ctx.fit_eff(X.contiguous(), Y.contiguous())
-        history.append({"round": r, "configs": int(X.shape[0]), "sweep_acceptance": float(n_sw.sum().item()) /
-                        (chains * per_round * sweeps * N * L), "J": J.cpu().tolist(), "rms_resid": float(resid.item())})
+        X = torch.cat(xs)
+        Y = torch.cat(ys)
+        J, resid = fit_eff_distributed(ctx, X.contiguous(), Y.contiguous())
+        sw = sum_over_processes(torch.stack([n_sw.sum(), torch.tensor(X.shape[0], device=dev)]))
+        history.append({"round": r, "configs": int(sw[1].item()), "sweep_acceptance": float(sw[0].item()) /
+                        (chains * world * per_round * sweeps * N * L), "J": J.cpu().tolist(),
+                        "rms_resid": float(resid.item())})
         del xs, ys, X, Y
         if r < rounds - 1:
             del xp
@@ -86,18 +93,20 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
     torch.cuda.synchronize()
     ctx.get_error()
     ms = e0.elapsed_time(e1)
-    S = obs.cpu().numpy()  # [updates][chains]
+    S_sum = sum_over_processes(obs.sum(dim=1))  # [updates], summed over every process's chains
+    acc = sum_over_processes(torch.stack([n_acc.sum(), n_sw.sum()]))
     therm = updates // 5
-    series = S[therm:].mean(axis=1)
+    series = (S_sum / (chains * world)).cpu().numpy()[therm:]
     res = {
         "lattice": "%dx%d" % (Lx, Lx), "N": N, "L": L, "beta": L * dtau, "n_s": n_s, "precision": precision,
-        "chains": chains, "training_configs": history[-1]["configs"], "training_rounds": history,
+        "chains": chains * world, "processes": world, "training_configs": history[-1]["configs"],
+        "training_rounds": history,
         "updates": updates, "sweeps_per_update": sweeps,
         "S_pipi_mean": float(series.mean()), "S_pipi_err": binned_error(series),
-        "acceptance": float(n_acc.sum().item()) / (chains * updates),
-        "sweep_acceptance": float(n_sw.sum().item()) / (chains * updates * sweeps * N * L),
+        "acceptance": float(acc[0].item()) / (chains * world * updates),
+        "sweep_acceptance": float(acc[1].item()) / (chains * world * updates * sweeps * N * L),
         "production_seconds": ms / 1e3, "training_seconds": t_train,
-        "evals_per_s": chains * updates / (ms / 1e3), "J_final": J.cpu().tolist(),
+        "evals_per_s": chains * world * updates / (ms / 1e3), "J_final": J.cpu().tolist(),
     }
     ctx.close()
     return res
@@ -115,7 +124,20 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--rounds", type=int, default=2)
     a = ap.parse_args()
-    print(json.dumps(run(a.Lx, a.L, a.n_s, a.chains, a.train, a.updates, a.sweeps, a.precision, rounds=a.rounds)))
+    import os
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    res = run(a.Lx, a.L, a.n_s, a.chains, a.train, a.updates, a.sweeps, a.precision, rounds=a.rounds,
+              device="cuda:%d" % local, rank=rank, world=world)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

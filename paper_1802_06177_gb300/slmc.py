@@ -36,9 +36,11 @@ EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", 
            "slmc_cumulative_update", "slmc_fit_eff", "slmc_measure_cdw", "slmc_launch_count", "slmc_profile_enable",
            "slmc_profile_read", "slmc_logdet_noalloc", "slmc_logdet_noalloc_scratch_bytes", "slmc_set_update_counter",
            "slmc_get_update_counter", "slmc_set_tuning", "slmc_batch_create", "slmc_batch_destroy",
-           "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune")
+           "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune",
+           "slmc_fit_eff_state", "slmc_fit_eff_merge")
 
 UPDATE_CONTINUE = (1 << 64) - 1
+FIT_STATE_DOUBLES = 64
 
 
 class TuneResult(ctypes.Structure):
@@ -90,6 +92,8 @@ def load_library(path=LIB_PATH):
         "slmc_batch_capture": ([P, I, I, V], I),
         "slmc_batch_launch": ([P, I, V], I),
         "slmc_autotune": ([ctypes.POINTER(Params), I, D, ctypes.POINTER(TuneResult)], I),
+        "slmc_fit_eff_state": ([P, P, P, I, P, V], I),
+        "slmc_fit_eff_merge": ([P, P, I, P, P, V], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -238,6 +242,26 @@ class Context:
         self._check("slmc_fit_eff", self.lib.slmc_fit_eff(self._ctx, px, _ptr(lnw, torch.float64, "lnw", (n,)), n,
                                                           _ptr(J, torch.float64, "J"), _ptr(resid, torch.float64, "r"),
                                                           _stream(self.device)))
+        return J, resid
+
+    def fit_eff_state(self, xs, lnw):
+        """Partial regression state [FIT_STATE_DOUBLES] of this process's configurations (Eq. (5))."""
+        px, n = self._fields(xs, "xs")
+        state = self._empty(FIT_STATE_DOUBLES)
+        self._check("slmc_fit_eff_state", self.lib.slmc_fit_eff_state(
+            self._ctx, px if n else None, _ptr(lnw, torch.float64, "lnw", (n,)) if n else None, n,
+            _ptr(state, torch.float64, "state"), _stream(self.device)))
+        return state
+
+    def fit_eff_merge(self, states):
+        """Couplings from partial states [nparts, FIT_STATE_DOUBLES] (all processes' states)."""
+        if states.dim() != 2 or states.shape[1] != FIT_STATE_DOUBLES:
+            raise ValueError("states must have shape [nparts, %d]" % FIT_STATE_DOUBLES)
+        J = self._empty(6)
+        resid = self._empty(1)
+        self._check("slmc_fit_eff_merge", self.lib.slmc_fit_eff_merge(
+            self._ctx, _ptr(states, torch.float64, "states"), states.shape[0], _ptr(J, torch.float64, "J"),
+            _ptr(resid, torch.float64, "r"), _stream(self.device)))
         return J, resid
 
     def launch_count(self):
