@@ -147,6 +147,28 @@ def class_work(cls, wl, nsl_mean):
     return None, None
 
 
+# DRAM traffic per field of the dominant kernel, from the committed ncu summary of that
+# kernel; valid only while the kernel source is the one the counters were taken on.
+TRAFFIC_SOURCES = {"qr": ("profiles/k_qrb_16x16_L160.md", "paper_1802_06177_gb300/csrc/k_qrb.cu")}
+
+
+def kernel_traffic(cls, fields_per_call):
+    import hashlib
+    import re
+    if cls not in TRAFFIC_SOURCES:
+        return None
+    prof_md, src = (os.path.join(ROOT, q) for q in TRAFFIC_SOURCES[cls])
+    if not (os.path.exists(prof_md) and os.path.exists(src)):
+        return None
+    m = re.search(r"traffic-per-field: ([0-9.eE+]+) bytes \(source sha256 ([0-9a-f]+)\)", open(prof_md).read())
+    if not m:
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if not digest.startswith(m.group(2)):
+        return None  # the kernel changed since the counters were taken
+    return float(m.group(1)) * fields_per_call
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -234,6 +256,7 @@ def time_oracle_step(pool, nproc, wl_name, nsweeps):
 def config_of(wl, args, precision):
     return {"workload": wl.name, "model": "holstein_2d", "N": wl.N, "Lx": wl.Lx, "L": wl.L, "beta": wl.beta,
             "n_s": wl.n_s, "chains_per_gpu": args.fields or wl.nfields, "nsweeps": args.nsweeps,
+            "sub_batches": getattr(args, "sub_batches", 0) or 2,
             "precision": precision, "global_batch": (args.fields or wl.nfields) * args.gpus,
             "parallelism": "replicas x%d" % args.gpus,
             "l2": "inputs larger than L2 (fields %.0f MB + workspace), no flush" % (
@@ -264,8 +287,11 @@ def run_gpu(args):
     x0 = torch.from_numpy(xh).to(dev)
 
     def make(prec):
-        return Context(wl.Lx, wl.Lx, wl.L, n_s=wl.n_s, precision=prec, max_fields=nf, seed=seed, sweep_delta=0.3,
-                       device=dev)
+        c = Context(wl.Lx, wl.Lx, wl.L, n_s=wl.n_s, precision=prec, max_fields=nf, seed=seed, sweep_delta=0.3,
+                    device=dev)
+        if args.sub_batches:
+            c.set_sub_batches(args.sub_batches)
+        return c
 
     def setup(ctx):
         x = x0.clone()
@@ -302,7 +328,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         launches = ctx.launch_count() - n0
-        prof = ctx.profile_read() if profile else None
+        prof = ctx.profile_read_detail() if profile else None
         if profile:
             ctx.profile(False)
         clk = sampler.stop() if sampler else None
@@ -379,33 +405,40 @@ def run_gpu(args):
     peaks = load_peaks()
     ngroups = math.ceil(wl.L / wl.n_s)
     nsl_mean = wl.L / ngroups
-    dom = max(prof, key=lambda k: prof[k][0])
-    dom_ms, dom_calls = prof[dom]
+    # calls of one class on concurrent sub-batch streams overlap: rank classes by busy time
+    # (union of their call intervals) and divide the class's work by it
+    dom = max(prof, key=lambda k: prof[k][2])
+    dom_ms, dom_calls, dom_busy, dom_units = prof[dom]
     work, kind = class_work(dom, wl, nsl_mean)
     roof = None
     if work:
-        per_call = work * nf
-        avg_s = dom_ms / dom_calls / 1e3
+        fields_per_call = dom_units / max(dom_calls, 1)
+        per_call = work * fields_per_call
+        busy_s = dom_busy / 1e3
         fp64_cls = dom in ("qr", "formq", "tupdate", "greens") or (dom == "slice" and args.precision == "fp64")
+        traffic = kernel_traffic(dom, fields_per_call)
+        common = {"kernel_class": dom, "algorithmic_per_launch": per_call, "fields_per_launch": fields_per_call,
+                  "launches_timed": dom_calls, "busy_ms": dom_busy, "sum_launch_ms": dom_ms,
+                  "avg_launch_ms": dom_ms / max(dom_calls, 1),
+                  "timing": "achieved = work of all timed launches / their busy time (union of launch "
+                            "intervals on the sub-batch streams, CUDA events on the launching streams)"}
         if kind == "flop":
-            achieved = per_call / avg_s / 1e12
+            achieved = work * dom_units / busy_s / 1e12
             if fp64_cls:
-                peak, pk = NOMINAL["fp64_tflops"], PROBED["fp64_tflops"]
+                peak, pk, src = NOMINAL["fp64_tflops"], PROBED["fp64_tflops"], \
+                    "nominal FP64 1.25 TFLOP/s (alu, not in MEASURED_PEAKS.json); probed DFMA rate beside it"
             else:
-                peak, pk = NOMINAL["fp32_tflops"], PROBED["fp32_tflops"]
-            roof = {"bound": "alu", "pipe": "fp64" if fp64_cls else "fp32", "kernel_class": dom,
-                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "peak_probed": pk, "frac_of_probed": achieved / pk, "traffic": None,
-                    "algorithmic_per_launch": per_call, "launches_timed": dom_calls, "avg_launch_ms": avg_s * 1e3,
-                    "peak_source": "nominal FP64 1.25 TFLOP/s (alu); probed DFMA rate beside it"}
+                peak, pk, src = NOMINAL["fp32_tflops"], PROBED["fp32_tflops"], \
+                    "nominal FP32 SIMT rate 152 SM x 128 lanes x 2 x 2.07 GHz (alu); probed FFMA rate beside it"
+            roof = dict(common, bound="alu", pipe="fp64" if fp64_cls else "fp32", achieved=achieved, peak=peak,
+                        unit="TFLOP/s", frac=achieved / peak, peak_probed=pk, frac_of_probed=achieved / pk,
+                        traffic=traffic, peak_source=src)
         else:
-            achieved = per_call / avg_s / 1e9
-            roof = {"bound": "hbm", "kernel_class": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                    "algorithmic_per_launch": per_call, "launches_timed": dom_calls, "avg_launch_ms": avg_s * 1e3,
-                    "peak_source": peaks["source"]}
-    total_prof = sum(v[0] for v in prof.values())
-    shares = {k: round(v[0] / total_prof, 4) for k, v in prof.items() if v[0] > 0}
+            achieved = work * dom_units / busy_s / 1e9
+            roof = dict(common, bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
+                        frac=achieved / peaks["hbm_gbs"], traffic=traffic, peak_source=peaks["source"])
+    total_prof = sum(v[2] for v in prof.values())
+    shares = {k: round(v[2] / total_prof, 4) for k, v in prof.items() if v[2] > 0}
 
     # ---- accuracy against the FP64 oracle and CPU baseline ----------------------------
     acc = None
@@ -422,6 +455,17 @@ def run_gpu(args):
                          % (nproc, args.nsweeps, wl.name)}
         pool.close()
 
+    # FP64 work of one evaluation of the step (QR and T update per group, Q of the final group
+    # (FP64 in every mode; the other groups' Q is FP64 only in FP64 mode), final LU, G) against the
+    # step time: how close the whole step runs to the FP64 roof while the FP32 work overlaps it
+    N3 = float(wl.N) ** 3
+    w64 = ngroups * (4.0 / 3.0 + 1.0) * N3 + (4.0 / 3.0) * N3 * (ngroups if args.precision == "fp64" else 1) \
+        + (2.0 / 3.0 + (2.0 if args.mode == "step" else 0.0)) * N3
+    if args.precision == "fp64":
+        w64 += 2.0 * N3 * wl.L
+    ach64 = w64 * nf * world / (ms_step / 1e3) / 1e12 / world
+    fp64_step = {"flop_per_eval": w64, "achieved_per_gpu": ach64, "unit": "TFLOP/s",
+                 "frac_of_nominal": ach64 / NOMINAL["fp64_tflops"], "frac_of_probed": ach64 / PROBED["fp64_tflops"]}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 slices + f64 stabilisation" if args.precision != "fp64" else "f64",
@@ -430,7 +474,7 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
             "fp64_value": fp64_value, "logdet_only_evals_per_s": rates, "accuracy_max_abs_dlndet": acc,
-            "time_shares": shares, "mode": args.mode, "batched_uneven": batched}
+            "fp64_step": fp64_step, "time_shares": shares, "mode": args.mode, "batched_uneven": batched}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -499,6 +543,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-rounds", type=int, default=20)
+    ap.add_argument("--sub-batches", type=int, default=0, help="forked streams per batch (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "slmc":
         args.warmup = 3

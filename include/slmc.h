@@ -197,6 +197,12 @@ SLMC_API int slmc_get_update_counter(slmc_ctx* ctx, uint64_t* value, void* strea
  * 8 or 16; 16 is used only for N <= 256). Results do not depend on them beyond rounding. */
 SLMC_API int slmc_set_tuning(slmc_ctx* ctx, int qr_panel, int slice_cols);
 
+/* Number of sub-batches (1..4) a determinant batch of at least 32 fields per sub-batch is
+ * split into; each runs on its own forked stream so that the kernels of one fill the SMs
+ * the others leave idle (default 2; 1 = no split). Results do not depend on it. Contexts
+ * created with max_fields < 64 have no forked streams (SLMC_ERR_UNSUPPORTED for n > 1). */
+SLMC_API int slmc_set_sub_batches(slmc_ctx* ctx, int n);
+
 /* Multi-linear regression of the effective model [Eq. (5)]: least squares of
  * lnw[c] on [1, F(xs[c])] over nconf configurations (Givens-rotation QR in FP64), then
  * (E0, J) = -coefficients / dtau.
@@ -262,6 +268,13 @@ SLMC_API int slmc_profile_enable(slmc_ctx* ctx, int on);
  * and the number of timed launch calls in calls[c] (arrays of SLMC_PROF_NCLASS entries;
  * calls may be NULL). A call covers the kernels of one class enqueued together. */
 SLMC_API int slmc_profile_read(slmc_ctx* ctx, double* ms, long long* calls, void* stream);
+
+/* As slmc_profile_read, plus per class: busy_ms[c], the union of the class's call intervals
+ * (the wall time during which at least one call of the class was running; calls of one class
+ * on concurrent sub-batch streams overlap, so busy_ms <= ms), and units[c], the number of
+ * fields (or chains) the timed calls processed in total. busy_ms and units may be NULL. */
+SLMC_API int slmc_profile_read_detail(slmc_ctx* ctx, double* ms, long long* calls, double* busy_ms,
+                                      long long* units, void* stream);
 
 /* ---- Batches of chains of uneven size in one CUDA graph ----------------------------------
  * A batch owns one context per lattice class (nclasses parameter sets, nchains[c] chains

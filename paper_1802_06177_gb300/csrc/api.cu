@@ -52,19 +52,45 @@ cudaEvent_t take_event(slmc_ctx* c) {
     return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
 }
 
+// Drains the recorded event pairs into the per-class totals: summed call durations, and the
+// union of the call intervals (calls of one class on concurrent streams overlap in time; the
+// union is the wall time during which at least one call of the class was running).
 int flush_profile(slmc_ctx* c) {
+    std::vector<std::pair<float, float>> iv[SLMC_PROF_NCLASS];
     for (size_t q = 0; q < c->ev_cls.size(); ++q) {
         cudaEvent_t b = c->ev_rec[2 * q], e = c->ev_rec[2 * q + 1];
-        float ms = 0.f;
-        if (cudaEventSynchronize(e) != cudaSuccess || cudaEventElapsedTime(&ms, b, e) != cudaSuccess)
+        float ms = 0.f, t0 = 0.f, t1 = 0.f;
+        if (cudaEventSynchronize(e) != cudaSuccess || cudaEventElapsedTime(&ms, b, e) != cudaSuccess ||
+            cudaEventElapsedTime(&t0, c->prof_base, b) != cudaSuccess ||
+            cudaEventElapsedTime(&t1, c->prof_base, e) != cudaSuccess)
             return SLMC_ERR_CUDA;
-        c->prof_ms[c->ev_cls[q]] += ms;
-        c->prof_calls[c->ev_cls[q]] += 1;
+        const int cls = c->ev_cls[q];
+        c->prof_ms[cls] += ms;
+        c->prof_calls[cls] += 1;
+        c->prof_units[cls] += c->ev_units[q];
+        iv[cls].emplace_back(t0, t1);
         c->ev_pool.push_back(b);
         c->ev_pool.push_back(e);
     }
+    for (int cls = 0; cls < SLMC_PROF_NCLASS; ++cls) {
+        auto& v = iv[cls];
+        std::sort(v.begin(), v.end());
+        double busy = 0.0, lo = 0.0, hi = -1.0;
+        for (const auto& w : v) {
+            if (w.first > hi) {
+                if (hi > lo) busy += hi - lo;
+                lo = w.first;
+                hi = w.second;
+            } else if (w.second > hi) {
+                hi = w.second;
+            }
+        }
+        if (hi > lo) busy += hi - lo;
+        c->prof_busy[cls] += busy;
+    }
     c->ev_cls.clear();
     c->ev_rec.clear();
+    c->ev_units.clear();
     return SLMC_OK;
 }
 
@@ -84,6 +110,7 @@ int launch(slmc_ctx* c, int cls, int nkernels, cudaStream_t s, Fn&& fn) {
         c->ev_rec.push_back(b);
         c->ev_rec.push_back(e);
         c->ev_cls.push_back(cls);
+        c->ev_units.push_back(c->cur_units);
         if (c->ev_cls.size() >= 4096) return flush_profile(c);  // bounded pool: drains recorded pairs
     }
     return SLMC_OK;
@@ -101,6 +128,7 @@ int* iscal(slmc_ctx* c, int col) { return c->iscal + (size_t)col * c->max_fields
 // accounted on `c` (the owning context).
 int logdet_run(slmc_ctx* c, slmc_ctx* v, const double* x, int nf, double* lndet, int* sign, double* G,
                cudaStream_t s) {
+    c->cur_units = nf;
     SLMC_LAUNCH(SLMC_PROF_FINAL, 1, s, slmc::set_identity(v, nf, s));
     if (v->p.precision != SLMC_PREC_FP64) SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_scales(v, x, nf, s));
     for (int l0 = 0; l0 < v->L; l0 += v->p.n_s) {
@@ -142,7 +170,9 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
     const size_t N = c->N, NN = N * N, F0 = (size_t)f0;
     v.E64 = c->E64;
     v.F32 = c->F32;
-    v.F32lo = c->F32lo;
+    v.lo_kidx = c->lo_kidx;
+    v.lo_val = c->lo_val;
+    v.lo_S = c->lo_S;
     v.sc32 = c->sc32 ? c->sc32 + F0 * c->L * N : nullptr;
     v.Y = c->Y + F0 * NN;
     v.QR = c->QR + F0 * NN;
@@ -167,11 +197,12 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
 
 int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, double* G, cudaStream_t s) {
     const bool tc = c->p.precision == SLMC_PREC_TF32X3 || c->p.precision == SLMC_PREC_BF16X9;
-    if (c->nsub < 2 || tc || nf < 2 * kMinSubFields) return logdet_run(c, c, x, nf, lndet, sign, G, s);
+    const int nsub = std::min(c->nsub, nf / kMinSubFields);
+    if (nsub < 2 || tc) return logdet_run(c, c, x, nf, lndet, sign, G, s);
     const size_t NL = (size_t)c->N * c->L, NN = (size_t)c->N * c->N;
     SLMC_CK(cudaEventRecord(c->sub_fork, s));
-    for (int k = 0; k < c->nsub; ++k) {
-        const int f0 = (int)((long long)k * nf / c->nsub), f1 = (int)((long long)(k + 1) * nf / c->nsub);
+    for (int k = 0; k < nsub; ++k) {
+        const int f0 = (int)((long long)k * nf / nsub), f1 = (int)((long long)(k + 1) * nf / nsub);
         SLMC_CK(cudaStreamWaitEvent(c->sub_stream[k], c->sub_fork, 0));
         slmc_ctx v = make_view(c, f0);
         SLMC_TRY(logdet_run(c, &v, x + f0 * NL, f1 - f0, lndet + f0, sign + f0, G ? G + f0 * NN : nullptr,
@@ -186,6 +217,7 @@ template <typename F>
 int for_batches(slmc_ctx* c, int n, F&& fn) {
     for (int f0 = 0; f0 < n; f0 += c->max_fields) {
         const int nf = std::min(c->max_fields, n - f0);
+        c->cur_units = nf;
         SLMC_TRY(fn(f0, nf));
     }
     return SLMC_OK;
@@ -199,7 +231,8 @@ void free_ctx(slmc_ctx* c) {
     if (c->sub_fork) cudaEventDestroy(c->sub_fork);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
-    void* bufs[] = {c->E64, c->F32, c->F32lo, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
+    if (c->prof_base) cudaEventDestroy(c->prof_base);
+    void* bufs[] = {c->E64, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
                     c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err, c->dctr,
                     c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
     for (void* b : bufs)
@@ -257,7 +290,11 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     };
     alloc(&c->E64, NN * sizeof(double));
     alloc(&c->F32, NN * sizeof(float));
-    alloc(&c->F32lo, NN * sizeof(float));
+    if (p->precision == SLMC_PREC_FP32) {
+        c->lo_S = std::min(slmc::kLoStencil, (int)N);
+        alloc(&c->lo_kidx, ((size_t)c->lo_S * N + c->lo_S) * sizeof(int));
+        alloc(&c->lo_val, (size_t)c->lo_S * sizeof(float));
+    }
     if (p->precision != SLMC_PREC_FP64) alloc(&c->sc32, F * L * N * sizeof(float));
     if (p->precision == SLMC_PREC_TF32X3) alloc(&c->Ftf, 2 * NN * sizeof(uint32_t));
     if (p->precision == SLMC_PREC_BF16X9) alloc(&c->Fbf, 3 * NN * sizeof(uint16_t));
@@ -305,8 +342,12 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
         for (int k = 0; k < slmc_ctx::kMaxSub && sok; ++k)
             sok = cudaStreamCreateWithFlags(&c->sub_stream[k], cudaStreamNonBlocking) == cudaSuccess &&
                   cudaEventCreateWithFlags(&c->sub_join[k], cudaEventDisableTiming) == cudaSuccess;
-        if (sok) c->nsub = slmc_ctx::kMaxSub;
-        else cudaGetLastError();
+        if (sok) {
+            c->nsub_avail = slmc_ctx::kMaxSub;
+            c->nsub = 2;
+        } else {
+            cudaGetLastError();
+        }
     }
     if (cudaMemset(c->err, 0, sizeof(unsigned int)) != cudaSuccess ||
         slmc::build_hopping_exp(c, nullptr) != cudaSuccess || (tc && slmc::tc_init(c, nullptr) != cudaSuccess) ||
@@ -472,6 +513,13 @@ int slmc_set_tuning(slmc_ctx* c, int qr_panel, int slice_cols) {
     return SLMC_OK;
 }
 
+int slmc_set_sub_batches(slmc_ctx* c, int n) {
+    if (!c || n < 1 || n > slmc_ctx::kMaxSub) return SLMC_ERR_ARG;
+    if (n > 1 && c->nsub_avail < n) return SLMC_ERR_UNSUPPORTED;
+    c->nsub = n;
+    return SLMC_OK;
+}
+
 int slmc_fit_eff(slmc_ctx* c, const double* xs, const double* lnw, int nconf, double* J_out, double* resid,
                  void* stream) {
     if (!c || nconf < 6 || !xs || !lnw || !J_out) return SLMC_ERR_ARG;
@@ -525,19 +573,32 @@ int slmc_profile_enable(slmc_ctx* c, int on) {
         for (int q = 0; q < SLMC_PROF_NCLASS; ++q) {
             c->prof_ms[q] = 0.0;
             c->prof_calls[q] = 0;
+            c->prof_busy[q] = 0.0;
+            c->prof_units[q] = 0;
         }
+        // time origin: recorded and completed before any call timed from now on
+        if (!c->prof_base && cudaEventCreate(&c->prof_base) != cudaSuccess) return SLMC_ERR_CUDA;
+        if (cudaEventRecord(c->prof_base, 0) != cudaSuccess || cudaEventSynchronize(c->prof_base) != cudaSuccess)
+            return SLMC_ERR_CUDA;
     }
     c->prof_on = on != 0;
     return SLMC_OK;
 }
 
 int slmc_profile_read(slmc_ctx* c, double* ms, long long* calls, void* stream) {
+    return slmc_profile_read_detail(c, ms, calls, nullptr, nullptr, stream);
+}
+
+int slmc_profile_read_detail(slmc_ctx* c, double* ms, long long* calls, double* busy_ms, long long* units,
+                             void* stream) {
     if (!c || !ms) return SLMC_ERR_ARG;
     if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return SLMC_ERR_CUDA;
     SLMC_TRY(flush_profile(c));
     for (int q = 0; q < SLMC_PROF_NCLASS; ++q) {
         ms[q] = c->prof_ms[q];
         if (calls) calls[q] = c->prof_calls[q];
+        if (busy_ms) busy_ms[q] = c->prof_busy[q];
+        if (units) units[q] = c->prof_units[q];
     }
     return SLMC_OK;
 }

@@ -3,7 +3,8 @@
 //   E_ij = (1/N) sum_k cos(k . (r_i - r_j)) exp(-dtau eps_k),  eps_k = -2t (cos kx + cos ky) - mu,
 // k = 2 pi (nx/Lx, ny/Ly). Phases are formed as exact rationals and evaluated with cospi.
 // Reduced-precision modes multiply by F = E - I (identity added exactly afterwards); its
-// FP32 copy and tensor-core operand splits are derived from the FP64 matrix.
+// FP32 copy, the stencil of its FP32 rounding residual and the tensor-core operand splits are
+// derived from the FP64 matrix.
 #include <cuda_bf16.h>
 
 #include "slmc_internal.cuh"
@@ -35,15 +36,14 @@ __device__ __forceinline__ uint32_t to_tf32(float v) {
     return r;
 }
 
-__global__ void k_split_F(const double* __restrict__ E, float* __restrict__ F32, float* __restrict__ F32lo,
-                          uint32_t* __restrict__ Ftf, uint16_t* __restrict__ Fbf, int N) {
+__global__ void k_split_F(const double* __restrict__ E, float* __restrict__ F32, uint32_t* __restrict__ Ftf,
+                          uint16_t* __restrict__ Fbf, int N) {
     const int NN = N * N;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= NN) return;
     const double fd = E[idx] - ((idx % (N + 1) == 0) ? 1.0 : 0.0);
     const float v = (float)fd;
     F32[idx] = v;
-    if (F32lo) F32lo[idx] = (float)(fd - (double)v);
     if (Ftf) {
         const uint32_t hi = to_tf32(v);
         const uint32_t lo = to_tf32(v - __uint_as_float(hi));
@@ -62,6 +62,37 @@ __global__ void k_split_F(const double* __restrict__ E, float* __restrict__ F32,
     }
 }
 
+// F is translation invariant on the periodic lattice (E_ij depends on r_i - r_j only), so its
+// FP32 rounding residual F_lo = F - fl32(F) is a stencil: F_lo(i, k) = F_lo(0, j) for
+// r_k = r_i + r_j. The S displacements j with the largest |F(0, j)| are kept (rank by |F|,
+// ties to the lower index; slot = rank); on the others |F_lo| <= 2^-24 |F| is below
+// 2^-24 of the S-th largest entry and is dropped.
+__global__ void k_lo_select(const double* __restrict__ E, int N, int S, int* __restrict__ sel,
+                            float* __restrict__ lo_val) {
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const double fd = E[j] - (j == 0 ? 1.0 : 0.0);
+        const double a = fabs(fd);
+        int r = 0;
+        for (int q = 0; q < N; ++q) {
+            const double b = fabs(E[q] - (q == 0 ? 1.0 : 0.0));
+            r += (b > a) || (b == a && q < j);
+        }
+        if (r < S) {
+            sel[r] = j;
+            lo_val[r] = (float)(fd - (double)(float)fd);
+        }
+    }
+}
+
+__global__ void k_lo_fill(const int* __restrict__ sel, int Lx, int Ly, int S, int* __restrict__ kidx) {
+    const int N = Lx * Ly;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= S * N) return;
+    const int s = idx / N, i = idx - s * N, j = sel[s];
+    const int kx = (i % Lx + j % Lx) % Lx, ky = (i / Lx + j / Lx) % Ly;
+    kidx[idx] = kx + Lx * ky;
+}
+
 }  // namespace
 
 namespace slmc {
@@ -70,7 +101,12 @@ cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s) {
     const int N = c->N;
     const int NN = N * N;
     k_hopping_exp<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->p.Lx, c->p.Ly, c->p.dtau, c->p.t, c->p.mu);
-    k_split_F<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->F32, c->F32lo, c->Ftf, c->Fbf, N);
+    k_split_F<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->F32, c->Ftf, c->Fbf, N);
+    if (c->lo_kidx) {
+        int* sel = c->lo_kidx + (size_t)c->lo_S * N;
+        k_lo_select<<<1, 1024, 0, s>>>(c->E64, N, c->lo_S, sel, c->lo_val);
+        k_lo_fill<<<(c->lo_S * N + 255) / 256, 256, 0, s>>>(sel, c->p.Lx, c->p.Ly, c->lo_S, c->lo_kidx);
+    }
     return cudaGetLastError();
 }
 

@@ -4,7 +4,8 @@
 //   ln|det(I + B_L ... B_1)| = sum ln D_b + ln|det M|,  sign = det(U) sign(det M),
 //   G = (I + B_L ... B_1)^-1 = M^-1 D_b^-1 U^T.
 // M is factored by a right-looking LU with partial pivoting (one CTA per field); G is
-// solved column by column (one warp per column, no block synchronisation).
+// solved by blocked triangular solves, 32 right-hand sides per CTA (for N > 842, whose
+// right-hand sides do not fit in shared memory, one warp per column).
 #include <cfloat>
 #include <climits>
 
@@ -203,6 +204,140 @@ __global__ void __launch_bounds__(256) k_greens(const double* __restrict__ LUall
     for (int i = lane; i < N; i += 32) Gout[f * NN + (size_t)i * N + j] = b[i];
 }
 
+// G[:, j0..j0+31] = M^-1 (D_b^-1 U^T)[:, j0..j0+31] with the LU factors of M (P M = L U'),
+// blocked over rows in blocks of 32. One CTA owns 32 right-hand-side columns of one field,
+// held in shared memory row-major with a padded row stride (X[i][c] at i * 33 + c):
+//   forward (unit L):  for each row block: solve the 32 x 32 diagonal block (warp w owns
+//                      columns 4w..4w+3, lane = row, values in registers, shuffles only), then
+//                      subtract its contribution from every row below (a rank-32 update, each
+//                      thread one row and 8 columns: plain FMAs, no reductions);
+//   backward (U'):     the same from the bottom block up, with the diagonal reciprocals.
+// Output row-major G[f][i][j].
+constexpr int kGB = 32;   // rows per block = right-hand sides per CTA
+constexpr int kGS = 33;   // padded row stride of X (doubles)
+
+__global__ void __launch_bounds__(256) k_greens_blk(const double* __restrict__ LUall, const int* __restrict__ piv_all,
+                                                    const double* __restrict__ Uall, const double* __restrict__ lnD_all,
+                                                    double* __restrict__ Gout, int N) {
+    const int f = blockIdx.y, j0 = blockIdx.x * kGB;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t NN = (size_t)N * N;
+    const double* __restrict__ LU = LUall + f * NN;
+    const double* __restrict__ U = Uall + f * NN;
+    const double* __restrict__ lnD = lnD_all + (size_t)f * N;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* X = reinterpret_cast<double*>(smraw);          // [N][kGS]
+    double* rdiag = X + (size_t)N * kGS;                    // [N]
+    int* src = reinterpret_cast<int*>(rdiag + N);           // [N] row of B that lands in row i of P B
+    if (tid == 0) {
+        for (int i = 0; i < N; ++i) src[i] = i;
+        const int* piv = piv_all + (size_t)f * N;
+        for (int k = 0; k < N; ++k) {
+            const int p = piv[k];
+            if (p != k) {
+                const int a = src[k];
+                src[k] = src[p];
+                src[p] = a;
+            }
+        }
+    }
+    for (int i = tid; i < N; i += 256) rdiag[i] = 1.0 / LU[(size_t)i * N + i];
+    __syncthreads();
+    // X = P D_b^-1 U^T restricted to the CTA's columns (columns beyond N are zero)
+    for (int idx = tid; idx < N * kGB; idx += 256) {
+        const int i = idx / kGB, c = idx - i * kGB, j = j0 + c;
+        const int r = src[i];
+        X[i * kGS + c] = (j < N) ? exp(-fmax(lnD[r], 0.0)) * U[(size_t)r * N + j] : 0.0;
+    }
+    __syncthreads();
+    const int nblk = (N + kGB - 1) / kGB;
+    // ---- forward substitution with the unit lower factor ----
+    for (int b = 0; b < nblk; ++b) {
+        const int kb = b * kGB, nb = min(kGB, N - kb);
+        {   // diagonal block: warp w owns columns 4w..4w+3, lane = row kb + lane
+            const int i = kb + lane;
+            double x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = (lane < nb) ? X[i * kGS + 4 * warp + q] : 0.0;
+            for (int k = 0; k < nb - 1; ++k) {
+                const double l = (lane > k && lane < nb) ? LU[(size_t)(kb + k) * N + i] : 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const double xk = __shfl_sync(0xffffffffu, x[q], k);
+                    if (lane > k) x[q] = fma(-l, xk, x[q]);
+                }
+            }
+            if (lane < nb) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) X[i * kGS + 4 * warp + q] = x[q];
+            }
+        }
+        __syncthreads();
+        // rows below the block: X[i][:] -= L[i][kb:kb+nb] X[kb:kb+nb][:]; item = (row, 8 columns)
+        const int r0 = kb + nb, nrows = N - r0;
+        for (int item = tid; item < nrows * 4; item += 256) {
+            const int i = r0 + (item >> 2), c0 = (item & 3) * 8;
+            double acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = X[i * kGS + c0 + q];
+            for (int k = 0; k < nb; ++k) {
+                const double l = LU[(size_t)(kb + k) * N + i];
+                const double* xk = X + (kb + k) * kGS + c0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] = fma(-l, xk[q], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) X[i * kGS + c0 + q] = acc[q];
+        }
+        __syncthreads();
+    }
+    // ---- backward substitution with the upper factor ----
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int kb = b * kGB, nb = min(kGB, N - kb);
+        {
+            const int i = kb + lane;
+            double x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = (lane < nb) ? X[i * kGS + 4 * warp + q] : 0.0;
+            const double rd = (lane < nb) ? rdiag[i] : 0.0;
+            for (int k = nb - 1; k >= 0; --k) {
+                const double u = (lane < k) ? LU[(size_t)(kb + k) * N + i] : 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (lane == k) x[q] *= rd;
+                    const double xk = __shfl_sync(0xffffffffu, x[q], k);
+                    if (lane < k) x[q] = fma(-u, xk, x[q]);
+                }
+            }
+            if (lane < nb) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) X[i * kGS + 4 * warp + q] = x[q];
+            }
+        }
+        __syncthreads();
+        // rows above the block: X[i][:] -= U'[i][kb:kb+nb] X[kb:kb+nb][:]
+        for (int item = tid; item < kb * 4; item += 256) {
+            const int i = item >> 2, c0 = (item & 3) * 8;
+            double acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = X[i * kGS + c0 + q];
+            for (int k = 0; k < nb; ++k) {
+                const double u = LU[(size_t)(kb + k) * N + i];
+                const double* xk = X + (kb + k) * kGS + c0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] = fma(-u, xk[q], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) X[i * kGS + c0 + q] = acc[q];
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < N * kGB; idx += 256) {
+        const int i = idx / kGB, c = idx - i * kGB, j = j0 + c;
+        if (j < N) Gout[f * NN + (size_t)i * N + j] = X[i * kGS + c];
+    }
+}
+
 template <int MAXR>
 cudaError_t launch_final(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s) {
     const int N = c->N;
@@ -240,6 +375,15 @@ cudaError_t final_logdet(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStre
 }
 
 cudaError_t final_greens(slmc_ctx* c, int nf, double* G, cudaStream_t s) {
+    const int N = c->N;
+    const size_t smem = (size_t)N * kGS * sizeof(double) + (size_t)N * (sizeof(double) + sizeof(int));
+    if (smem <= 227 * 1024) {  // blocked solve (the column-per-warp kernel below covers larger N)
+        cudaError_t e = cudaFuncSetAttribute(k_greens_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((N + kGB - 1) / kGB, nf);
+        k_greens_blk<<<grid, 256, smem, s>>>(c->Y, c->piv, c->U, c->lnD, G, N);
+        return cudaGetLastError();
+    }
     switch (rows_per_lane_class(c->N)) {
         case 1: return launch_greens<1>(c, nf, G, s);
         case 2: return launch_greens<2>(c, nf, G, s);

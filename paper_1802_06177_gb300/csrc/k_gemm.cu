@@ -23,10 +23,6 @@ template <typename T>
 __device__ __forceinline__ T slice_scale(double xv, double dtlam);
 template <>
 __device__ __forceinline__ double slice_scale<double>(double xv, double dtlam) { return exp(-dtlam * xv); }
-template <>
-__device__ __forceinline__ float slice_scale<float>(double xv, double dtlam) {
-    return expf(-(float)dtlam * (float)xv);
-}
 
 template <typename T, int MAXR, int CPT, bool TRI>
 __global__ void __launch_bounds__(256) k_panel(const T* __restrict__ A, size_t a_stride,
@@ -137,11 +133,15 @@ cudaError_t dispatch_panel(const T* A, size_t a_stride, const double* B, const i
 //   Y' = D_l (Y + F Y),  F = F_hi + F_lo (two FP32 terms of E - I),
 // with the products of one block of 32 k accumulated in FP32 and the block sums combined by
 // TwoSum (Knuth) into a compensated pair, so small far-field contributions are not rounded
-// away against the large running sum; the F_lo term is accumulated separately. Thread
-// (row i, column group) owns rows i, i+256, ... and NBT columns of the CTA's panel; the panel
-// sits in shared memory k-major (four columns per 128-bit load) and the rows k0..k0+31 of
-// F_hi and F_lo (contiguous in global memory) are double-buffered into shared memory with
-// cp.async while the previous block is being multiplied.
+// away against the large running sum. The F_lo products (2^-24 smaller) are accumulated into
+// the compensation term, on the S displacements of the translation-invariant F where |F| is
+// largest (a stencil: F_lo(i, k) for r_k = r_i + r_j; the dropped part of F_lo is below
+// 2^-24 of the S-th largest |F| entry, far below the FP32 rounding of the kept terms).
+// Thread (row i, column group) owns rows i, i+256, ... and NBT columns of the CTA's panel;
+// the panel sits in shared memory k-major with a row stride of NB + 4 floats (four columns
+// per 128-bit load; rows of consecutive threads fall in distinct bank groups), and the rows
+// k0..k0+KB-1 of F_hi (contiguous in global memory) are double-buffered into shared memory
+// with cp.async while the previous block is multiplied.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
                  "l"(gmem)
@@ -155,70 +155,61 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// rows [k0, k0 + nk) of F_hi and F_lo into Fs[2][KB][N]
-template <int KB>
-__device__ __forceinline__ void stage_F(float* Fs, const float* __restrict__ Fhi, const float* __restrict__ Flo, int N,
-                                        int k0, int nk) {
+// rows [k0, k0 + nk) of F_hi into Fs[KB][N]
+__device__ __forceinline__ void stage_F(float* Fs, const float* __restrict__ Fhi, int N, int k0, int nk) {
     const size_t n = (size_t)nk * N;
     const float* gh = Fhi + (size_t)k0 * N;
-    const float* gl = Flo + (size_t)k0 * N;
-    float* sl = Fs + (size_t)KB * N;
     if ((N & 3) == 0) {
-        for (size_t q = threadIdx.x; q < n / 4; q += blockDim.x) {
-            cp_async16(Fs + 4 * q, gh + 4 * q);
-            cp_async16(sl + 4 * q, gl + 4 * q);
-        }
+        for (size_t q = threadIdx.x; q < n / 4; q += blockDim.x) cp_async16(Fs + 4 * q, gh + 4 * q);
     } else {
-        for (size_t q = threadIdx.x; q < n; q += blockDim.x) {
-            cp_async4(Fs + q, gh + q);
-            cp_async4(sl + q, gl + q);
-        }
+        for (size_t q = threadIdx.x; q < n; q += blockDim.x) cp_async4(Fs + q, gh + q);
     }
 }
 
 template <int RPT, int NBT, int KB>
-__global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi, const float* __restrict__ Flo,
+__global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi, const int* __restrict__ lo_kidx,
+                                                   const float* __restrict__ lo_val, int S,
                                                    const float* __restrict__ U, double* __restrict__ out,
                                                    const float* __restrict__ sc32, int N, int L, int l0, int nsl) {
     constexpr int NB = 2 * NBT;  // two column groups of NBT columns; thread = (row, group)
+    constexpr int NBP = NB + 4;  // padded row stride of the panel
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* P0 = reinterpret_cast<float*>(smem_raw);  // [N][NB]
-    float* P1 = P0 + (size_t)N * NB;
-    float* Fs0 = P1 + (size_t)N * NB;  // two stages of [2][KB][N]
-    float* Fs1 = Fs0 + (size_t)2 * KB * N;
+    float* P0 = reinterpret_cast<float*>(smem_raw);  // [N][NBP]
+    float* P1 = P0 + (size_t)N * NBP;
+    float* Fs0 = P1 + (size_t)N * NBP;  // two stages of [KB][N]
+    float* Fs1 = Fs0 + (size_t)KB * N;
     const int f = blockIdx.y, j0 = blockIdx.x * NB, tid = threadIdx.x & 255, cg = (threadIdx.x >> 8) * NBT;
     const size_t NN = (size_t)N * N;
     const int nblk = (N + KB - 1) / KB;
     for (int idx = threadIdx.x; idx < NB * N; idx += 512) {
         const int jj = idx / N, k = idx - jj * N, j = j0 + jj;
-        P0[k * NB + jj] = (j < N) ? U[(size_t)f * NN + (size_t)j * N + k] : 0.f;
+        P0[k * NBP + jj] = (j < N) ? U[(size_t)f * NN + (size_t)j * N + k] : 0.f;
     }
     float* Pin = P0;
     float* Pout = P1;
     for (int s = 0; s < nsl; ++s) {
         __syncthreads();
-        stage_F<KB>(Fs0, Fhi, Flo, N, 0, min(KB, N));
+        stage_F(Fs0, Fhi, N, 0, min(KB, N));
         cp_async_commit();
-        float hi[RPT][NBT], cp[RPT][NBT], blk[RPT][NBT], lo[RPT][NBT];
+        float hi[RPT][NBT], cp[RPT][NBT], blk[RPT][NBT];
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
-            for (int c = 0; c < NBT; ++c) hi[r][c] = cp[r][c] = blk[r][c] = lo[r][c] = 0.f;
+            for (int c = 0; c < NBT; ++c) hi[r][c] = cp[r][c] = blk[r][c] = 0.f;
         for (int b = 0; b < nblk; ++b) {
             float* Fcur = (b & 1) ? Fs1 : Fs0;
-            if (b + 1 < nblk) stage_F<KB>((b & 1) ? Fs0 : Fs1, Fhi, Flo, N, (b + 1) * KB, min(KB, N - (b + 1) * KB));
+            if (b + 1 < nblk) stage_F((b & 1) ? Fs0 : Fs1, Fhi, N, (b + 1) * KB, min(KB, N - (b + 1) * KB));
             cp_async_commit();
             cp_async_wait1();
             __syncthreads();
             const int k0 = b * KB, nk = min(KB, N - k0);
             const float* Fh = Fcur;
-            const float* Fl = Fcur + (size_t)KB * N;
             for (int kk = 0; kk < nk; ++kk) {
                 const int k = k0 + kk;
                 float pv[NBT];
 #pragma unroll
                 for (int c = 0; c < NBT; c += 4) {
-                    const float4 q = *reinterpret_cast<const float4*>(Pin + k * NB + cg + c);
+                    const float4 q = *reinterpret_cast<const float4*>(Pin + k * NBP + cg + c);
                     pv[c] = q.x;
                     pv[c + 1] = q.y;
                     pv[c + 2] = q.z;
@@ -228,12 +219,8 @@ __global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi
                 for (int r = 0; r < RPT; ++r) {
                     const int i = tid + 256 * r;
                     const float ah = (i < N) ? Fh[kk * N + i] : 0.f;
-                    const float al = (i < N) ? Fl[kk * N + i] : 0.f;
 #pragma unroll
-                    for (int c = 0; c < NBT; ++c) {
-                        blk[r][c] = fmaf(ah, pv[c], blk[r][c]);
-                        lo[r][c] = fmaf(al, pv[c], lo[r][c]);
-                    }
+                    for (int c = 0; c < NBT; ++c) blk[r][c] = fmaf(ah, pv[c], blk[r][c]);
                 }
             }
 #pragma unroll
@@ -249,6 +236,25 @@ __global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi
                 }
             __syncthreads();  // the stage just read is refilled two blocks later
         }
+        // F_lo on its stencil (rows of the panel already in shared memory)
+        for (int q = 0; q < S; ++q) {
+            const float v = __ldg(lo_val + q);
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int i = tid + 256 * r;
+                if (i < N) {
+                    const int k = __ldg(lo_kidx + (size_t)q * N + i);
+#pragma unroll
+                    for (int c = 0; c < NBT; c += 4) {
+                        const float4 y = *reinterpret_cast<const float4*>(Pin + k * NBP + cg + c);
+                        cp[r][c] = fmaf(v, y.x, cp[r][c]);
+                        cp[r][c + 1] = fmaf(v, y.y, cp[r][c + 1]);
+                        cp[r][c + 2] = fmaf(v, y.z, cp[r][c + 2]);
+                        cp[r][c + 3] = fmaf(v, y.w, cp[r][c + 3]);
+                    }
+                }
+            }
+        }
         const bool last = (s == nsl - 1);
         const float* scl = sc32 + ((size_t)f * L + l0 + s) * N;
 #pragma unroll
@@ -257,13 +263,20 @@ __global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi
             if (i >= N) continue;
             const float sc = scl[i];
 #pragma unroll
-            for (int c = 0; c < NBT; ++c) {
-                const float fy = __fadd_rn(hi[r][c], __fadd_rn(cp[r][c], lo[r][c]));
-                const float v = __fmul_rn(__fadd_rn(Pin[i * NB + cg + c], fy), sc);
+            for (int c = 0; c < NBT; c += 4) {
+                const float4 y = *reinterpret_cast<const float4*>(Pin + i * NBP + cg + c);
+                float4 v;
+                v.x = __fmul_rn(__fadd_rn(y.x, __fadd_rn(hi[r][c], cp[r][c])), sc);
+                v.y = __fmul_rn(__fadd_rn(y.y, __fadd_rn(hi[r][c + 1], cp[r][c + 1])), sc);
+                v.z = __fmul_rn(__fadd_rn(y.z, __fadd_rn(hi[r][c + 2], cp[r][c + 2])), sc);
+                v.w = __fmul_rn(__fadd_rn(y.w, __fadd_rn(hi[r][c + 3], cp[r][c + 3])), sc);
                 if (last) {
-                    if (j0 + cg + c < N) out[(size_t)f * NN + (size_t)(j0 + cg + c) * N + i] = (double)v;
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (j0 + cg + c + q < N) out[(size_t)f * NN + (size_t)(j0 + cg + c + q) * N + i] = (double)vv[q];
                 } else {
-                    Pout[i * NB + cg + c] = v;
+                    *reinterpret_cast<float4*>(Pout + i * NBP + cg + c) = v;
                 }
             }
         }
@@ -278,12 +291,14 @@ constexpr size_t kSmemBudget = 220 * 1024;
 template <int RPT, int NBT, int KB>
 cudaError_t launch_slice_f32_kb(const slmc_ctx* c, int nf, int l0, int nsl, cudaStream_t s) {
     const int N = c->N;
-    constexpr int NB = 2 * NBT;
-    const size_t smem = ((size_t)2 * N * NB + (size_t)4 * KB * N) * sizeof(float);
+    constexpr int NBP = 2 * NBT + 4;
+    const size_t smem = ((size_t)2 * N * NBP + (size_t)2 * KB * N) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_slice_f32<RPT, NBT, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    constexpr int NB = 2 * NBT;
     dim3 grid((N + NB - 1) / NB, nf);
-    k_slice_f32<RPT, NBT, KB><<<grid, 512, smem, s>>>(c->F32, c->F32lo, c->U32, c->Y, c->sc32, N, c->L, l0, nsl);
+    k_slice_f32<RPT, NBT, KB><<<grid, 512, smem, s>>>(c->F32, c->lo_kidx, c->lo_val, c->lo_S, c->U32, c->Y, c->sc32, N,
+                                                      c->L, l0, nsl);
     return cudaGetLastError();
 }
 
@@ -291,8 +306,8 @@ cudaError_t launch_slice_f32_kb(const slmc_ctx* c, int nf, int l0, int nsl, cuda
 template <int RPT, int NBT>
 cudaError_t launch_slice_f32(const slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s) {
     (void)x;
-    const size_t panel = (size_t)2 * c->N * 2 * NBT * sizeof(float);
-    const size_t per_row = (size_t)4 * c->N * sizeof(float);
+    const size_t panel = (size_t)2 * c->N * (2 * NBT + 4) * sizeof(float);
+    const size_t per_row = (size_t)2 * c->N * sizeof(float);
     if (panel + 32 * per_row <= kSmemBudget) return launch_slice_f32_kb<RPT, NBT, 32>(c, nf, l0, nsl, s);
     if (panel + 16 * per_row <= kSmemBudget) return launch_slice_f32_kb<RPT, NBT, 16>(c, nf, l0, nsl, s);
     return launch_slice_f32_kb<RPT, NBT, 8>(c, nf, l0, nsl, s);

@@ -33,7 +33,9 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Bytes of the per-context part (E, F, error word) and of one field's workspace.
 size_t fixed_bytes(size_t N) {
-    return align256(N * N * sizeof(double)) + 2 * align256(N * N * sizeof(float)) + 256;
+    const size_t S = N < (size_t)slmc::kLoStencil ? N : (size_t)slmc::kLoStencil;
+    return align256(N * N * sizeof(double)) + align256(N * N * sizeof(float)) +
+           align256((S * N + S) * sizeof(int)) + align256(S * sizeof(float)) + 256;
 }
 // L > 0 (FP32 mode): also the FP32 slice scales and the FP32 orthogonal factor.
 size_t field_bytes(size_t N, size_t L) {
@@ -89,7 +91,11 @@ int slmc_logdet_noalloc(const slmc_params* p, const double* x, int n, double* ln
     auto take = [&](size_t bytes) { unsigned char* r = q; q += align256(bytes); return r; };
     c.E64 = reinterpret_cast<double*>(take(NN * sizeof(double)));
     c.F32 = reinterpret_cast<float*>(take(NN * sizeof(float)));
-    c.F32lo = reinterpret_cast<float*>(take(NN * sizeof(float)));
+    if (Lz) {  // stencil of F's FP32 rounding residual (FP32 mode)
+        c.lo_S = (int)(N < (size_t)slmc::kLoStencil ? N : (size_t)slmc::kLoStencil);
+        c.lo_kidx = reinterpret_cast<int*>(take(((size_t)c.lo_S * N + c.lo_S) * sizeof(int)));
+        c.lo_val = reinterpret_cast<float*>(take((size_t)c.lo_S * sizeof(float)));
+    }
     c.err = reinterpret_cast<unsigned int*>(take(sizeof(unsigned int)));
     c.Y = reinterpret_cast<double*>(q);
     c.QR = c.Y + F * NN;

@@ -35,6 +35,41 @@ struct QrSmem {
     }
 };
 
+// Rows r0 + lane + 32 q (q < RC) of the kCT columns cptr: y -= V[r][0:nb] W'[0:nb][c].
+template <int RC, int BP, typename T, typename CT>
+__device__ __forceinline__ void wy_rows(const T* __restrict__ Vp, const T* __restrict__ W, const CT (&cptr)[kCT], int N,
+                                        int r0, int nb, int lane) {
+    constexpr int BPS = BP + 1;
+    T y[RC][kCT];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) {
+        const int r = r0 + lane + 32 * q;
+#pragma unroll
+        for (int c = 0; c < kCT; ++c) y[q][c] = (r < N && cptr[c]) ? cptr[c][r] : T(0);
+    }
+    for (int mm = 0; mm < nb; ++mm) {
+        T wv[kCT];
+#pragma unroll
+        for (int c = 0; c < kCT; ++c) wv[c] = W[mm * kCT + c];
+#pragma unroll
+        for (int q = 0; q < RC; ++q) {
+            const int r = r0 + lane + 32 * q;
+            const T v = (r < N) ? Vp[r * BPS + mm] : T(0);
+#pragma unroll
+            for (int c = 0; c < kCT; ++c) y[q][c] = fma(-v, wv[c], y[q][c]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RC; ++q) {
+        const int r = r0 + lane + 32 * q;
+        if (r < N) {
+#pragma unroll
+            for (int c = 0; c < kCT; ++c)
+                if (cptr[c]) cptr[c][r] = y[q][c];
+        }
+    }
+}
+
 // Rank-BP update of columns [j_begin, N) rows [p, N) of the column-major matrix A (column j
 // stored at col(j)): A <- (I - V op(S) V^T) A, op(S) = S^T for the QR trailing update
 // (Q_p^T A) and S for the backward formation of Q (Q_p A). V is the clean panel in shared
@@ -71,60 +106,35 @@ __device__ __forceinline__ void wy_update(const T* __restrict__ Vp, const T* __r
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc) W[m * kCT + h * CPL + cc] = (m < nb) ? acc[cc] : T(0);
         __syncwarp();
-        // W' = op(S) W   (same lane ownership)
-        T w2[CPL];
+        // W' = op(S) W, op(S) triangular. Lane (c = lane % kCT, g = lane / kCT) owns the
+        // reflectors m = g + 4 t: the four lane groups then run nearly equal triangular loops
+        // (a lane-per-reflector layout would idle half the lanes on average).
+        {
+            constexpr int MT = BP / 4;
+            const int c = lane % kCT, g = lane / kCT;
+            T w2[MT];
 #pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) w2[cc] = T(0);
-        if (m < nb) {
-            if (TRANS) {
-                for (int q = 0; q <= m; ++q) {
-                    const T sv = Ssm[q * BP + m];
-#pragma unroll
-                    for (int cc = 0; cc < CPL; ++cc) w2[cc] = fma(sv, W[q * kCT + h * CPL + cc], w2[cc]);
+            for (int t = 0; t < MT; ++t) {
+                const int mr = g + 4 * t;
+                T a = T(0);
+                if (mr < nb) {
+                    if (TRANS) {
+                        for (int q = 0; q <= mr; ++q) a = fma(Ssm[q * BP + mr], W[q * kCT + c], a);
+                    } else {
+                        for (int q = mr; q < nb; ++q) a = fma(Ssm[mr * BP + q], W[q * kCT + c], a);
+                    }
                 }
-            } else {
-                for (int q = m; q < nb; ++q) {
-                    const T sv = Ssm[m * BP + q];
-#pragma unroll
-                    for (int cc = 0; cc < CPL; ++cc) w2[cc] = fma(sv, W[q * kCT + h * CPL + cc], w2[cc]);
-                }
+                w2[t] = a;
             }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < MT; ++t) W[(g + 4 * t) * kCT + c] = w2[t];
+            __syncwarp();
         }
-        __syncwarp();
-#pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) W[m * kCT + h * CPL + cc] = w2[cc];
-        __syncwarp();
-        // A[r][c] -= sum_m V[r][m] W'[m][c]   (lanes over rows)
-        for (int r0 = p; r0 < N; r0 += 32 * kRC) {
-            T y[kRC][kCT];
-#pragma unroll
-            for (int q = 0; q < kRC; ++q) {
-                const int r = r0 + lane + 32 * q;
-#pragma unroll
-                for (int c = 0; c < kCT; ++c) y[q][c] = (r < N && cptr[c]) ? cptr[c][r] : T(0);
-            }
-            for (int mm = 0; mm < nb; ++mm) {
-                T wv[kCT];
-#pragma unroll
-                for (int c = 0; c < kCT; ++c) wv[c] = W[mm * kCT + c];
-#pragma unroll
-                for (int q = 0; q < kRC; ++q) {
-                    const int r = r0 + lane + 32 * q;
-                    const T v = (r < N) ? Vp[r * BPS + mm] : T(0);
-#pragma unroll
-                    for (int c = 0; c < kCT; ++c) y[q][c] = fma(-v, wv[c], y[q][c]);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < kRC; ++q) {
-                const int r = r0 + lane + 32 * q;
-                if (r < N) {
-#pragma unroll
-                    for (int c = 0; c < kCT; ++c)
-                        if (cptr[c]) cptr[c][r] = y[q][c];
-                }
-            }
-        }
+        // A[r][c] -= sum_m V[r][m] W'[m][c]   (lanes over rows; chunks of 64 rows, then 32)
+        int r0 = p;
+        for (; r0 + 32 * kRC <= N; r0 += 32 * kRC) wy_rows<kRC, BP>(Vp, W, cptr, N, r0, nb, lane);
+        for (; r0 < N; r0 += 32) wy_rows<1, BP>(Vp, W, cptr, N, r0, nb, lane);
         __syncwarp();
     }
 }

@@ -22,7 +22,9 @@ struct slmc_ctx {
     // exp(-dtau K), built on the device from the plane-wave eigenbasis of K.
     double* E64;
     float* F32;      // F = E - I rounded to FP32 (reduced-precision slices use Y + F Y)
-    float* F32lo;    // FP32 rounding residual of F (F ~ F32 + F32lo)
+    int* lo_kidx;    // FP32 modes: [S][N] column of the S-th stencil entry of row i, then sel[S]
+    float* lo_val;   // [S] FP32 rounding residual of F on the S largest-|F| displacements
+    int lo_S;        // stencil size min(kLoStencil, N)
     float* sc32;     // [max_fields][L][N] slice scales exp(-dtau lambda x), FP64-computed, rounded to FP32
     // tensor-core operand splits of F (filled only in the matching precision modes)
     uint32_t* Ftf;   // [2][N][N] TF32 hi / lo bit patterns
@@ -62,8 +64,9 @@ struct slmc_ctx {
     // Sub-batches: a large logdet batch is split over nsub forked streams so that the
     // kernels of one sub-batch fill the tails of the other's. A view is a shallow copy of the
     // context with the per-field workspace pointers offset; parent points to the owner.
-    static constexpr int kMaxSub = 2;
-    int nsub;
+    static constexpr int kMaxSub = 4;
+    int nsub;       // sub-batches used for large batches (1 = no split)
+    int nsub_avail; // forked streams created at init (0 or kMaxSub)
     cudaStream_t sub_stream[kMaxSub];
     cudaEvent_t sub_fork, sub_join[kMaxSub];
     slmc_ctx* parent;
@@ -73,13 +76,21 @@ struct slmc_ctx {
     std::vector<cudaEvent_t> ev_pool;            // free events
     std::vector<int> ev_cls;                      // class of each recorded pair
     std::vector<cudaEvent_t> ev_rec;             // recorded begin/end pairs
+    std::vector<int> ev_units;                    // fields processed by each recorded call
+    cudaEvent_t prof_base;                        // time origin of the recorded intervals
+    int cur_units;                                // fields of the calls being enqueued
     double prof_ms[SLMC_PROF_NCLASS];
     long long prof_calls[SLMC_PROF_NCLASS];
+    double prof_busy[SLMC_PROF_NCLASS];           // union of the class's call intervals (ms)
+    long long prof_units[SLMC_PROF_NCLASS];
 };
 
 namespace slmc {
 
 // ---- launch helpers ---------------------------------------------------------------
+// Stencil size of the FP32 rounding residual of F in the FP32 slice products.
+constexpr int kLoStencil = 32;
+
 inline int rows_per_lane_class(int N) {
     const int r = (N + 31) / 32;
     if (r <= 1) return 1;

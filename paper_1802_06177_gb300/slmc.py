@@ -37,7 +37,8 @@ EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", 
            "slmc_profile_read", "slmc_logdet_noalloc", "slmc_logdet_noalloc_scratch_bytes", "slmc_set_update_counter",
            "slmc_get_update_counter", "slmc_set_tuning", "slmc_batch_create", "slmc_batch_destroy",
            "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune",
-           "slmc_fit_eff_state", "slmc_fit_eff_merge")
+           "slmc_fit_eff_state", "slmc_fit_eff_merge", "slmc_profile_read_detail",
+           "slmc_set_sub_batches")
 
 UPDATE_CONTINUE = (1 << 64) - 1
 FIT_STATE_DOUBLES = 64
@@ -94,6 +95,8 @@ def load_library(path=LIB_PATH):
         "slmc_autotune": ([ctypes.POINTER(Params), I, D, ctypes.POINTER(TuneResult)], I),
         "slmc_fit_eff_state": ([P, P, P, I, P, V], I),
         "slmc_fit_eff_merge": ([P, P, I, P, P, V], I),
+        "slmc_profile_read_detail": ([P, P, P, P, P, V], I),
+        "slmc_set_sub_batches": ([P, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -273,11 +276,18 @@ class Context:
 
     def profile_read(self):
         """{class: (total ms, timed calls)} of the event-timed launches since profile(True)."""
+        return {k: v[:2] for k, v in self.profile_read_detail().items()}
+
+    def profile_read_detail(self):
+        """{class: (summed call ms, calls, busy ms = union of call intervals, fields processed)}."""
         n = len(PROF_CLASSES)
         ms = (ctypes.c_double * n)()
         calls = (ctypes.c_longlong * n)()
-        self._check("slmc_profile_read", self.lib.slmc_profile_read(self._ctx, ms, calls, _stream(self.device)))
-        return {k: (ms[q], calls[q]) for q, k in enumerate(PROF_CLASSES)}
+        busy = (ctypes.c_double * n)()
+        units = (ctypes.c_longlong * n)()
+        self._check("slmc_profile_read_detail", self.lib.slmc_profile_read_detail(
+            self._ctx, ms, calls, busy, units, _stream(self.device)))
+        return {k: (ms[q], calls[q], busy[q], units[q]) for q, k in enumerate(PROF_CLASSES)}
 
     def set_update_counter(self, value):
         self._check("slmc_set_update_counter", self.lib.slmc_set_update_counter(self._ctx, value, _stream(self.device)))
@@ -290,6 +300,10 @@ class Context:
 
     def set_tuning(self, qr_panel=0, slice_cols=0):
         self._check("slmc_set_tuning", self.lib.slmc_set_tuning(self._ctx, qr_panel, slice_cols))
+
+    def set_sub_batches(self, n):
+        """Sub-batches (forked streams) a large determinant batch is split into (1..4)."""
+        self._check("slmc_set_sub_batches", self.lib.slmc_set_sub_batches(self._ctx, n))
 
     def measure_cdw(self, G):
         n = G.shape[0]

@@ -194,3 +194,35 @@ def test_mixed_both_qr_modes(qr_mode):
     l_ref, s_ref, _ = oracle_many(HolsteinParams(12, 12, 120, n_s=10), x, want_G=False)
     assert np.abs(lndet.cpu().numpy() - l_ref).max() <= TOL_LNDET_MIXED
     assert np.array_equal(sign.cpu().numpy(), s_ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sub_batch_split_is_bit_identical_and_profiled(precision):
+    """Splitting a batch over 1-4 forked streams changes only which stream runs a field:
+    ln det, sign and G are bit-identical; the profiler counts every field once per launch
+    class and the busy time of a class (union of its launch intervals) never exceeds the
+    summed launch time."""
+    Lx, L, n_s, nf = 6, 24, 6, 130
+    x = inputs.mixed_fields(nf, Lx, Lx, L, seed=77)
+    ctx = make_ctx(Lx, L, n_s, precision=precision, max_fields=nf)
+    out = []
+    for nsub in (1, 2, 3, 4):
+        ctx.set_sub_batches(nsub)
+        ctx.profile(True)
+        G, ld, sg = ctx.greens(cuda(x))
+        prof = ctx.profile_read_detail()
+        ctx.profile(False)
+        out.append((G.cpu().numpy(), ld.cpu().numpy(), sg.cpu().numpy()))
+        groups = -(-L // n_s)
+        ms, calls, busy, units = prof["qr"]
+        assert units == nf * groups and calls == groups * nsub
+        assert 0.0 < busy <= ms * (1 + 1e-6) + 1e-3
+        assert prof["greens"][3] == nf
+    for G, ld, sg in out[1:]:
+        assert np.array_equal(G, out[0][0]) and np.array_equal(ld, out[0][1]) and np.array_equal(sg, out[0][2])
+    p = HolsteinParams(Lx, Lx, L, n_s=n_s)
+    E = exp_hopping(Lx, Lx, 1.0, 0.0, 0.1)
+    tol = 1e-8 if precision == "fp64" else 5e-5
+    for f in (0, 64, 129):
+        ref = fermion_logdet(p, x[f], E=E, want_G=False)[0]
+        assert abs(out[0][1][f] - ref) <= tol
