@@ -256,7 +256,8 @@ def time_oracle_step(pool, nproc, wl_name, nsweeps):
 def config_of(wl, args, precision):
     return {"workload": wl.name, "model": "holstein_2d", "N": wl.N, "Lx": wl.Lx, "L": wl.L, "beta": wl.beta,
             "n_s": wl.n_s, "chains_per_gpu": args.fields or wl.nfields, "nsweeps": args.nsweeps,
-            "sub_batches": getattr(args, "sub_batches", 0) or 2,
+            "sub_batches": getattr(args, "sub_batches", 0) or 3,
+            "slice_groups": getattr(args, "slice_groups", 0) or 1,
             "precision": precision, "global_batch": (args.fields or wl.nfields) * args.gpus,
             "parallelism": "replicas x%d" % args.gpus,
             "l2": "inputs larger than L2 (fields %.0f MB + workspace), no flush" % (
@@ -291,6 +292,8 @@ def run_gpu(args):
                     device=dev)
         if args.sub_batches:
             c.set_sub_batches(args.sub_batches)
+        if args.slice_groups:
+            c.set_slice_groups(args.slice_groups)
         return c
 
     def setup(ctx):
@@ -544,6 +547,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-rounds", type=int, default=20)
     ap.add_argument("--sub-batches", type=int, default=0, help="forked streams per batch (0 = library default)")
+    ap.add_argument("--slice-groups", type=int, default=0, help="FP32 slice kernel column groups (0 = default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "slmc":
         args.warmup = 3

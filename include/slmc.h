@@ -199,9 +199,15 @@ SLMC_API int slmc_set_tuning(slmc_ctx* ctx, int qr_panel, int slice_cols);
 
 /* Number of sub-batches (1..4) a determinant batch of at least 32 fields per sub-batch is
  * split into; each runs on its own forked stream so that the kernels of one fill the SMs
- * the others leave idle (default 2; 1 = no split). Results do not depend on it. Contexts
+ * the others leave idle (default 3; 1 = no split). Results do not depend on it. Contexts
  * created with max_fields < 64 have no forked streams (SLMC_ERR_UNSUPPORTED for n > 1). */
 SLMC_API int slmc_set_sub_batches(slmc_ctx* ctx, int n);
+
+/* Column groups per CTA of the FP32 slice kernel: 1 (default, 0 selects it) or 2. One group
+ * (256 threads, about 104 KB of shared memory at N = 256) leaves room on the SM for a CTA of
+ * another sub-batch's FP64 stabilisation, so the FP32 and FP64 pipes work at the same time;
+ * two groups (512 threads) fill the SM alone. Results do not depend on it. */
+SLMC_API int slmc_set_slice_groups(slmc_ctx* ctx, int groups);
 
 /* Multi-linear regression of the effective model [Eq. (5)]: least squares of
  * lnw[c] on [1, F(xs[c])] over nconf configurations (Givens-rotation QR in FP64), then

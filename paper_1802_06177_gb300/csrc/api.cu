@@ -190,6 +190,7 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
     v.dctr = c->dctr;
     v.tune_qr_panel = c->tune_qr_panel;
     v.tune_slice_cols = c->tune_slice_cols;
+    v.tune_slice_groups = c->tune_slice_groups;
     v.nsub = 0;
     v.parent = c;
     return v;
@@ -344,7 +345,7 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
                   cudaEventCreateWithFlags(&c->sub_join[k], cudaEventDisableTiming) == cudaSuccess;
         if (sok) {
             c->nsub_avail = slmc_ctx::kMaxSub;
-            c->nsub = 2;
+            c->nsub = 3;
         } else {
             cudaGetLastError();
         }
@@ -510,6 +511,12 @@ int slmc_set_tuning(slmc_ctx* c, int qr_panel, int slice_cols) {
         return SLMC_ERR_ARG;
     c->tune_qr_panel = qr_panel;
     c->tune_slice_cols = slice_cols;
+    return SLMC_OK;
+}
+
+int slmc_set_slice_groups(slmc_ctx* c, int groups) {
+    if (!c || groups < 0 || groups > 2) return SLMC_ERR_ARG;
+    c->tune_slice_groups = groups;
     return SLMC_OK;
 }
 

@@ -166,13 +166,13 @@ __device__ __forceinline__ void stage_F(float* Fs, const float* __restrict__ Fhi
     }
 }
 
-template <int RPT, int NBT, int KB>
-__global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi, const int* __restrict__ lo_kidx,
+template <int RPT, int NBT, int KB, int NCG>
+__global__ void __launch_bounds__(256 * NCG) k_slice_f32(const float* __restrict__ Fhi, const int* __restrict__ lo_kidx,
                                                    const float* __restrict__ lo_val, int S,
                                                    const float* __restrict__ U, double* __restrict__ out,
                                                    const float* __restrict__ sc32, int N, int L, int l0, int nsl) {
-    constexpr int NB = 2 * NBT;  // two column groups of NBT columns; thread = (row, group)
-    constexpr int NBP = NB + 4;  // padded row stride of the panel
+    constexpr int NB = NCG * NBT;  // NCG column groups of NBT columns; thread = (row, group)
+    constexpr int NBP = NB + 4;    // padded row stride of the panel
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* P0 = reinterpret_cast<float*>(smem_raw);  // [N][NBP]
     float* P1 = P0 + (size_t)N * NBP;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi
     const int f = blockIdx.y, j0 = blockIdx.x * NB, tid = threadIdx.x & 255, cg = (threadIdx.x >> 8) * NBT;
     const size_t NN = (size_t)N * N;
     const int nblk = (N + KB - 1) / KB;
-    for (int idx = threadIdx.x; idx < NB * N; idx += 512) {
+    for (int idx = threadIdx.x; idx < NB * N; idx += 256 * NCG) {
         const int jj = idx / N, k = idx - jj * N, j = j0 + jj;
         P0[k * NBP + jj] = (j < N) ? U[(size_t)f * NN + (size_t)j * N + k] : 0.f;
     }
@@ -288,29 +288,39 @@ __global__ void __launch_bounds__(512) k_slice_f32(const float* __restrict__ Fhi
 
 constexpr size_t kSmemBudget = 220 * 1024;
 
-template <int RPT, int NBT, int KB>
+template <int RPT, int NBT, int KB, int NCG>
 cudaError_t launch_slice_f32_kb(const slmc_ctx* c, int nf, int l0, int nsl, cudaStream_t s) {
     const int N = c->N;
-    constexpr int NBP = 2 * NBT + 4;
+    constexpr int NBP = NCG * NBT + 4;
     const size_t smem = ((size_t)2 * N * NBP + (size_t)2 * KB * N) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_slice_f32<RPT, NBT, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_slice_f32<RPT, NBT, KB, NCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    constexpr int NB = 2 * NBT;
+    constexpr int NB = NCG * NBT;
     dim3 grid((N + NB - 1) / NB, nf);
-    k_slice_f32<RPT, NBT, KB><<<grid, 512, smem, s>>>(c->F32, c->lo_kidx, c->lo_val, c->lo_S, c->U32, c->Y, c->sc32, N,
+    k_slice_f32<RPT, NBT, KB, NCG><<<grid, 256 * NCG, smem, s>>>(c->F32, c->lo_kidx, c->lo_val, c->lo_S, c->U32, c->Y, c->sc32, N,
                                                       c->L, l0, nsl);
     return cudaGetLastError();
 }
 
-// Largest staged block (32, 16 or 8 rows of F) that fits the shared-memory budget.
+// Largest staged block (32, 16 or 8 rows of F) that fits the shared-memory budget. With one
+// column group (256 threads, about half the registers and shared memory of two groups) a CTA
+// leaves room on its SM for a CTA of the FP64 stabilisation kernels of another sub-batch.
+template <int RPT, int NBT, int NCG>
+cudaError_t launch_slice_f32_g(const slmc_ctx* c, int nf, int l0, int nsl, cudaStream_t s) {
+    const size_t budget = NCG == 1 ? kSmemBudget / 2 : kSmemBudget;
+    const size_t panel = (size_t)2 * c->N * (NCG * NBT + 4) * sizeof(float);
+    const size_t per_row = (size_t)2 * c->N * sizeof(float);
+    if (panel + 32 * per_row <= budget) return launch_slice_f32_kb<RPT, NBT, 32, NCG>(c, nf, l0, nsl, s);
+    if (panel + 16 * per_row <= budget) return launch_slice_f32_kb<RPT, NBT, 16, NCG>(c, nf, l0, nsl, s);
+    return launch_slice_f32_kb<RPT, NBT, 8, NCG>(c, nf, l0, nsl, s);
+}
+
 template <int RPT, int NBT>
 cudaError_t launch_slice_f32(const slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s) {
     (void)x;
-    const size_t panel = (size_t)2 * c->N * (2 * NBT + 4) * sizeof(float);
-    const size_t per_row = (size_t)2 * c->N * sizeof(float);
-    if (panel + 32 * per_row <= kSmemBudget) return launch_slice_f32_kb<RPT, NBT, 32>(c, nf, l0, nsl, s);
-    if (panel + 16 * per_row <= kSmemBudget) return launch_slice_f32_kb<RPT, NBT, 16>(c, nf, l0, nsl, s);
-    return launch_slice_f32_kb<RPT, NBT, 8>(c, nf, l0, nsl, s);
+    if (c->tune_slice_groups == 2) return launch_slice_f32_g<RPT, NBT, 2>(c, nf, l0, nsl, s);
+    return launch_slice_f32_g<RPT, NBT, 1>(c, nf, l0, nsl, s);
 }
 
 // exp(-dtau lambda x[f][i][l]) in FP64, rounded once to FP32, stored [f][l][i]: the slice

@@ -139,6 +139,68 @@ __device__ __forceinline__ void wy_update(const T* __restrict__ Vp, const T* __r
     }
 }
 
+// Householder reflector of panel column c (logical row k = p + c) by one warp: beta, tau and
+// v = x / (alpha - beta) below the diagonal, written back into the panel.
+template <int BP>
+__device__ __forceinline__ void panel_reflector(double* __restrict__ Vp, int k, int c, int N, int lane,
+                                                double* s_tau, double* s_beta, double* __restrict__ tau_f,
+                                                int* s_ntriv) {
+    constexpr int BPS = BP + 1;
+    const double alpha = Vp[k * BPS + c];
+    double sig = 0.0;
+    for (int r = k + 1 + lane; r < N; r += 32) {
+        const double v = Vp[r * BPS + c];
+        sig = fma(v, v, sig);
+    }
+    sig = slmc::warp_allsum(sig);
+    double tau = 0.0, beta = alpha, scal = 0.0;
+    if (sig != 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, sig));
+        beta = (alpha >= 0.0) ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+    }
+    for (int r = k + 1 + lane; r < N; r += 32) Vp[r * BPS + c] *= scal;
+    if (lane == 0) {
+        s_tau[c] = tau;
+        s_beta[c] = beta;
+        tau_f[k] = tau;
+        if (tau != 0.0) *s_ntriv += 1;
+    }
+}
+
+// Applies reflector c (rows k.., v_k = 1) to the NC panel columns c0, c0 + cs, ... by one warp:
+// a -= tau (v . a) v, with the NC dot products and reductions interleaved.
+template <int BP, int NC>
+__device__ __forceinline__ void panel_apply(double* __restrict__ Vp, int k, int c, double tau, int c0, int cs, int N,
+                                            int lane) {
+    constexpr int BPS = BP + 1;
+    int cols[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) cols[j] = c0 + j * cs;
+    double d[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) d[j] = (lane == 0) ? Vp[k * BPS + cols[j]] : 0.0;
+    for (int r = k + 1 + lane; r < N; r += 32) {
+        const double v = Vp[r * BPS + c];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) d[j] = fma(v, Vp[r * BPS + cols[j]], d[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NC; ++j) d[j] = slmc::warp_allsum(d[j]) * tau;
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) Vp[k * BPS + cols[j]] -= d[j];
+    }
+    for (int r = k + 1 + lane; r < N; r += 32) {
+        const double v = Vp[r * BPS + c];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) Vp[r * BPS + cols[j]] = fma(-d[j], v, Vp[r * BPS + cols[j]]);
+    }
+}
+
+__device__ __forceinline__ int k_of(int p, int c) { return p + c; }
+
 template <int BP>
 __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, double* __restrict__ lnD_all,
                                                   double* __restrict__ QRall, double* __restrict__ tau_all,
@@ -214,41 +276,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
             Vp[(p + rr) * BPS + c] = Y[(size_t)s_perm[p + c] * N + p + rr];
         }
         __syncthreads();
-        // unblocked Householder on the panel (shared memory)
+        // Householder on the panel (shared memory), one block barrier per column: warp 0 applies
+        // reflector c to column c+1 and forms reflector c+1 from it, while warps 1.. apply
+        // reflector c to columns c+2.. (their dot products and reductions interleaved).
+        if (warp == 0) panel_reflector<BP>(Vp, k_of(p, 0), 0, N, lane, s_tau, s_beta, tau_all + (size_t)f * N, &s_ntriv);
+        __syncthreads();
         for (int c = 0; c < nb; ++c) {
             const int k = p + c;
-            if (warp == 0) {
-                const double alpha = Vp[k * BPS + c];
-                double sig = 0.0;
-                for (int r = k + 1 + lane; r < N; r += 32) {
-                    const double v = Vp[r * BPS + c];
-                    sig = fma(v, v, sig);
-                }
-                sig = slmc::warp_allsum(sig);
-                double tau = 0.0, beta = alpha, scal = 0.0;
-                if (sig != 0.0) {
-                    const double nrm = sqrt(fma(alpha, alpha, sig));
-                    beta = (alpha >= 0.0) ? -nrm : nrm;
-                    tau = (beta - alpha) / beta;
-                    scal = 1.0 / (alpha - beta);
-                }
-                for (int r = k + 1 + lane; r < N; r += 32) Vp[r * BPS + c] *= scal;
-                if (lane == 0) {
-                    s_tau[c] = tau;
-                    s_beta[c] = beta;
-                    tau_all[(size_t)f * N + k] = tau;
-                    if (tau != 0.0) s_ntriv += 1;
-                }
-            }
-            __syncthreads();
             const double tau = s_tau[c];
-            if (tau != 0.0) {
-                for (int c2 = c + 1 + warp; c2 < nb; c2 += kWarps) {
-                    double d = (lane == 0) ? Vp[k * BPS + c2] : 0.0;  // v_k[k] = 1
-                    for (int r = k + 1 + lane; r < N; r += 32) d = fma(Vp[r * BPS + c], Vp[r * BPS + c2], d);
-                    d = slmc::warp_allsum(d) * tau;
-                    if (lane == 0) Vp[k * BPS + c2] -= d;
-                    for (int r = k + 1 + lane; r < N; r += 32) Vp[r * BPS + c2] = fma(-d, Vp[r * BPS + c], Vp[r * BPS + c2]);
+            if (warp == 0) {
+                if (c + 1 < nb) {
+                    if (tau != 0.0) panel_apply<BP, 1>(Vp, k, c, tau, c + 1, 1, N, lane);
+                    __syncwarp();
+                    panel_reflector<BP>(Vp, k + 1, c + 1, N, lane, s_tau, s_beta, tau_all + (size_t)f * N, &s_ntriv);
+                }
+            } else if (tau != 0.0) {
+                // columns c0, c0 + 7, ... below nb (warp-uniform count nv <= 5)
+                const int c0 = c + 2 + (warp - 1), cs = kWarps - 1;
+                const int nv = (c0 < nb) ? (nb - 1 - c0) / cs + 1 : 0;
+                switch (nv) {
+                    case 0: break;
+                    case 1: panel_apply<BP, 1>(Vp, k, c, tau, c0, cs, N, lane); break;
+                    case 2: panel_apply<BP, 2>(Vp, k, c, tau, c0, cs, N, lane); break;
+                    case 3: panel_apply<BP, 3>(Vp, k, c, tau, c0, cs, N, lane); break;
+                    case 4: panel_apply<BP, 4>(Vp, k, c, tau, c0, cs, N, lane); break;
+                    default: panel_apply<BP, 5>(Vp, k, c, tau, c0, cs, N, lane); break;
                 }
             }
             __syncthreads();
@@ -291,13 +343,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
         }
         __syncthreads();
         double* G = Wsm;  // [BP][BP]
-        for (int pr = warp; pr < nb * nb; pr += kWarps) {
-            const int a = pr / nb, c = pr - a * nb;
-            if (a >= c) continue;
-            double d = 0.0;
-            for (int r = p + c + lane; r < N; r += 32) d = fma(Vp[r * BPS + a], Vp[r * BPS + c], d);
-            d = slmc::warp_allsum(d);
-            if (lane == 0) G[a * BP + c] = d;
+        {   // G[a][c] = v_a . v_c for a < c; each warp interleaves four pairs (independent chains)
+            const int npairs = nb * (nb - 1) / 2;
+            for (int q0 = warp * 4; q0 < npairs; q0 += kWarps * 4) {
+                int pa[4], pc[4];
+                double d[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    int q = q0 + j, cc = 1;
+                    while (q >= cc) {  // pair index -> (a, c): pairs ordered by c, then a
+                        q -= cc;
+                        ++cc;
+                    }
+                    pa[j] = q;
+                    pc[j] = (q0 + j < npairs) ? cc : N;  // N: empty range
+                    d[j] = 0.0;
+                }
+                const int rmax = N - p - pc[0];
+                for (int t = 0; t * 32 < rmax; ++t) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int r = p + pc[j] + lane + 32 * t;
+                        if (r < N) d[j] = fma(Vp[r * BPS + pa[j]], Vp[r * BPS + pc[j]], d[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) d[j] = slmc::warp_allsum(d[j]);
+                if (lane == 0) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (q0 + j < npairs) G[pa[j] * BP + pc[j]] = d[j];
+                }
+            }
         }
         __syncthreads();
         // S: S_cc = tau_c, S[0:c, c] = -tau_c S[0:c, 0:c] G[0:c, c]  (one warp, lane = row)
@@ -305,9 +382,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
             for (int c = 0; c < nb; ++c) {
                 const double tc = s_tau[c];
                 double v = 0.0;
-                if (lane < c) {
-                    for (int q = lane; q < c; ++q) v = fma(Ssm[lane * BP + q], G[q * BP + c], v);
-                    v = -tc * v;
+                if (lane < c) {  // four independent partial sums (short dependency chains)
+                    double v4[4] = {0.0, 0.0, 0.0, 0.0};
+                    int q = lane;
+                    for (; q + 4 <= c; q += 4) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * BP + c], v4[j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        if (q + j < c) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * BP + c], v4[j]);
+                    v = -tc * ((v4[0] + v4[1]) + (v4[2] + v4[3]));
                 } else if (lane == c) {
                     v = tc;
                 }

@@ -38,7 +38,7 @@ EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", 
            "slmc_get_update_counter", "slmc_set_tuning", "slmc_batch_create", "slmc_batch_destroy",
            "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune",
            "slmc_fit_eff_state", "slmc_fit_eff_merge", "slmc_profile_read_detail",
-           "slmc_set_sub_batches")
+           "slmc_set_sub_batches", "slmc_set_slice_groups")
 
 UPDATE_CONTINUE = (1 << 64) - 1
 FIT_STATE_DOUBLES = 64
@@ -97,6 +97,7 @@ def load_library(path=LIB_PATH):
         "slmc_fit_eff_merge": ([P, P, I, P, P, V], I),
         "slmc_profile_read_detail": ([P, P, P, P, P, V], I),
         "slmc_set_sub_batches": ([P, I], I),
+        "slmc_set_slice_groups": ([P, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -300,6 +301,10 @@ class Context:
 
     def set_tuning(self, qr_panel=0, slice_cols=0):
         self._check("slmc_set_tuning", self.lib.slmc_set_tuning(self._ctx, qr_panel, slice_cols))
+
+    def set_slice_groups(self, groups):
+        """Column groups per CTA of the FP32 slice kernel (0 = default 1, or 2)."""
+        self._check("slmc_set_slice_groups", self.lib.slmc_set_slice_groups(self._ctx, groups))
 
     def set_sub_batches(self, n):
         """Sub-batches (forked streams) a large determinant batch is split into (1..4)."""

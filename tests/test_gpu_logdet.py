@@ -226,3 +226,15 @@ def test_sub_batch_split_is_bit_identical_and_profiled(precision):
     for f in (0, 64, 129):
         ref = fermion_logdet(p, x[f], E=E, want_G=False)[0]
         assert abs(out[0][1][f] - ref) <= tol
+
+
+def test_slice_column_groups_bit_identical():
+    """One or two column groups per CTA of the FP32 slice kernel run the same arithmetic per
+    output element: bit-identical results."""
+    Lx, L, n_s, nf = 12, 40, 10, 20
+    x = inputs.mixed_fields(nf, Lx, Lx, L, seed=91)
+    ctx = make_ctx(Lx, L, n_s, precision="fp32", max_fields=nf)
+    G2, ld2, _ = ctx.greens(cuda(x))
+    ctx.set_slice_groups(2)
+    G1, ld1, _ = ctx.greens(cuda(x))
+    assert torch.equal(G1, G2) and torch.equal(ld1, ld2)
