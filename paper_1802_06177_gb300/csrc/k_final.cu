@@ -3,7 +3,8 @@
 //   I + U D T = U D_b M,   M = D_b^-1 U^T + D_s T,
 //   ln|det(I + B_L ... B_1)| = sum ln D_b + ln|det M|,  sign = det(U) sign(det M),
 //   G = (I + B_L ... B_1)^-1 = M^-1 D_b^-1 U^T.
-// M is factored by a right-looking LU with partial pivoting (one CTA per field); G is
+// M is factored by a blocked right-looking LU with partial pivoting (one CTA per field; the
+// unblocked kernel covers N > 842, whose panel does not fit in shared memory); G is
 // solved by blocked triangular solves, 32 right-hand sides per CTA (for N > 842, whose
 // right-hand sides do not fit in shared memory, one warp per column).
 #include <cfloat>
@@ -204,6 +205,156 @@ __global__ void __launch_bounds__(256) k_greens(const double* __restrict__ LUall
     for (int i = lane; i < N; i += 32) Gout[f * NN + (size_t)i * N + j] = b[i];
 }
 
+// Right-looking blocked LU with partial pivoting of M (column-major, in global memory), one CTA
+// per field, panels of 32 columns. The panel is factored in shared memory one column at a time
+// (pivot search by warp 0, ties to the lowest row); its row interchanges are then applied to the
+// other columns, the panel's 32 rows of U to its right are solved against its unit lower
+// triangle (one thread per column, values in registers), and the trailing matrix receives the
+// rank-32 update (one thread per row and 8 columns, plain FMAs). Same factors (LAPACK
+// convention: piv[k] = row interchanged with row k at step k) as the unblocked kernel, up to
+// rounding; ln|det M| and the sign are accumulated from the pivots.
+constexpr int kLB = 32;  // panel width
+constexpr int kLS = 33;  // padded row stride of the panel in shared memory
+
+__global__ void __launch_bounds__(256) k_lu_blk(double* __restrict__ Mall, int* __restrict__ piv_all,
+                                                const double* __restrict__ lnD_all, const int* __restrict__ sgnU,
+                                                double* __restrict__ lndet, int* __restrict__ sign,
+                                                unsigned int* __restrict__ err, int N) {
+    const int f = blockIdx.x;
+    const size_t NN = (size_t)N * N;
+    double* __restrict__ M = Mall + f * NN;
+    int* __restrict__ piv = piv_all + (size_t)f * N;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* P = reinterpret_cast<double*>(smraw);  // panel rows p0..N-1: P[(r - p0) * kLS + c]
+    __shared__ int s_piv[kLB];
+    __shared__ double s_logabs;
+    __shared__ int s_neg, s_sing;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_logabs = 0.0;
+        s_neg = 0;
+        s_sing = 0;
+    }
+    for (int p0 = 0; p0 < N; p0 += kLB) {
+        const int nb = min(kLB, N - p0), R = N - p0;
+        __syncthreads();
+        for (int idx = tid; idx < R * nb; idx += 256) {
+            const int c = idx / R, rr = idx - c * R;
+            P[rr * kLS + c] = M[(size_t)(p0 + c) * N + p0 + rr];
+        }
+        __syncthreads();
+        // ---- panel ----
+        for (int c = 0; c < nb; ++c) {
+            if (warp == 0) {
+                double bv = -1.0;
+                int bi = R;
+                for (int rr = c + lane; rr < R; rr += 32) {
+                    const double a = fabs(P[rr * kLS + c]);
+                    if (a > bv) {  // rows ascend per lane: ties keep the lower row
+                        bv = a;
+                        bi = rr;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ov > bv || (ov == bv && oi < bi)) {
+                        bv = ov;
+                        bi = oi;
+                    }
+                }
+                if (bi >= R) bi = c;  // no comparable entry (NaN column): no interchange
+                if (lane == 0) {
+                    const double pval = P[bi * kLS + c];
+                    s_piv[c] = bi;
+                    piv[p0 + c] = p0 + bi;
+                    if (pval == 0.0) s_sing = 1;
+                    s_logabs += log(fabs(pval));
+                    s_neg ^= (pval < 0.0) ^ (bi != c);
+                }
+            }
+            __syncthreads();
+            const int bi = s_piv[c];
+            if (bi != c && tid < nb) {
+                const double a = P[c * kLS + tid];
+                P[c * kLS + tid] = P[bi * kLS + tid];
+                P[bi * kLS + tid] = a;
+            }
+            __syncthreads();
+            const double pv = P[c * kLS + c];
+            const double rinv = (pv != 0.0) ? 1.0 / pv : 0.0;
+            for (int rr = c + 1 + tid; rr < R; rr += 256) {  // multiplier and rank-1 update of the row
+                const double l = P[rr * kLS + c] * rinv;
+                P[rr * kLS + c] = l;
+                for (int j = c + 1; j < nb; ++j) P[rr * kLS + j] = fma(-l, P[c * kLS + j], P[rr * kLS + j]);
+            }
+            __syncthreads();
+        }
+        for (int idx = tid; idx < R * nb; idx += 256) {
+            const int c = idx / R, rr = idx - c * R;
+            M[(size_t)(p0 + c) * N + p0 + rr] = P[rr * kLS + c];
+        }
+        // ---- interchanges on the other columns; rows of U to the right of the panel ----
+        for (int j = tid; j < N; j += 256) {
+            if (j >= p0 && j < p0 + nb) continue;
+            double* __restrict__ Mj = M + (size_t)j * N;
+            for (int c = 0; c < nb; ++c) {
+                const int bi = s_piv[c];
+                if (bi != c) {
+                    const double a = Mj[p0 + c];
+                    Mj[p0 + c] = Mj[p0 + bi];
+                    Mj[p0 + bi] = a;
+                }
+            }
+            if (j >= p0 + nb) {  // U12[:, j] = L11^-1 A12[:, j]
+                double x[kLB];
+#pragma unroll
+                for (int i = 0; i < kLB; ++i) x[i] = (i < nb) ? Mj[p0 + i] : 0.0;
+#pragma unroll
+                for (int c = 0; c < kLB - 1; ++c) {
+#pragma unroll
+                    for (int i = c + 1; i < kLB; ++i)
+                        if (i < nb) x[i] = fma(-P[i * kLS + c], x[c], x[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < kLB; ++i)
+                    if (i < nb) Mj[p0 + i] = x[i];
+            }
+        }
+        __syncthreads();
+        // ---- trailing update A22 -= L21 U12 ----
+        const int nr = N - p0 - nb;
+        const int ncg = (nr + 7) / 8;
+        for (int item = tid; item < nr * ncg; item += 256) {
+            const int rr = item % nr, g = item / nr;
+            const int i = p0 + nb + rr, j0 = p0 + nb + 8 * g;
+            double acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = (j0 + q < N) ? M[(size_t)(j0 + q) * N + i] : 0.0;
+            for (int c = 0; c < nb; ++c) {
+                const double l = P[(nb + rr) * kLS + c];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (j0 + q < N) acc[q] = fma(-l, M[(size_t)(j0 + q) * N + p0 + c], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < N) M[(size_t)(j0 + q) * N + i] = acc[q];
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double ld = s_logabs;
+        for (int i = 0; i < N; ++i) ld += fmax(lnD_all[(size_t)f * N + i], 0.0);
+        const bool ok = !s_sing && isfinite(ld);
+        lndet[f] = ok ? ld : __longlong_as_double(0x7ff8000000000000ll);
+        sign[f] = ok ? (sgnU[f] * (s_neg ? -1 : 1)) : 0;
+        if (s_sing) atomicOr(err, SLMC_EBIT_SINGULAR);
+        else if (!ok) atomicOr(err, SLMC_EBIT_NONFINITE);
+    }
+}
+
 // G[:, j0..j0+31] = M^-1 (D_b^-1 U^T)[:, j0..j0+31] with the LU factors of M (P M = L U'),
 // blocked over rows in blocks of 32. One CTA owns 32 right-hand-side columns of one field,
 // held in shared memory row-major with a padded row stride (X[i][c] at i * 33 + c):
@@ -342,6 +493,13 @@ template <int MAXR>
 cudaError_t launch_final(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s) {
     const int N = c->N;
     k_assemble_M<<<nf, kThreads, 2 * N * sizeof(double), s>>>(c->U, c->Ta, c->lnD, c->Y, N);
+    const size_t smem = (size_t)N * kLS * sizeof(double);
+    if (smem <= 227 * 1024) {  // blocked LU (the panel fits in shared memory)
+        cudaError_t e = cudaFuncSetAttribute(k_lu_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_lu_blk<<<nf, 256, smem, s>>>(c->Y, c->piv, c->lnD, c->sgnU, lndet, sign, c->err, N);
+        return cudaGetLastError();
+    }
     k_lu<MAXR><<<nf, kThreads, N * sizeof(double), s>>>(c->Y, c->piv, c->lnD, c->sgnU, lndet, sign, c->err, N);
     return cudaGetLastError();
 }
