@@ -294,6 +294,8 @@ def run_gpu(args):
             c.set_sub_batches(args.sub_batches)
         if args.slice_groups:
             c.set_slice_groups(args.slice_groups)
+        if args.sub_priorities >= 0:
+            c.set_sub_batch_priorities(args.sub_priorities)
         return c
 
     def setup(ctx):
@@ -548,6 +550,7 @@ def main():
     ap.add_argument("--batch-rounds", type=int, default=20)
     ap.add_argument("--sub-batches", type=int, default=0, help="forked streams per batch (0 = library default)")
     ap.add_argument("--slice-groups", type=int, default=0, help="FP32 slice kernel column groups (0 = default)")
+    ap.add_argument("--sub-priorities", type=int, default=-1, help="descending sub-batch stream priorities (1/0)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "slmc":
         args.warmup = 3

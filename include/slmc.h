@@ -203,6 +203,11 @@ SLMC_API int slmc_set_tuning(slmc_ctx* ctx, int qr_panel, int slice_cols);
  * created with max_fields < 64 have no forked streams (SLMC_ERR_UNSUPPORTED for n > 1). */
 SLMC_API int slmc_set_sub_batches(slmc_ctx* ctx, int n);
 
+/* on = 1: sub-batch k runs on a stream of scheduling priority (highest - k), so the first
+ * sub-batch runs ahead and the others fill the SMs it leaves idle; on = 0: equal priorities.
+ * Results do not depend on it. SLMC_ERR_UNSUPPORTED for contexts without forked streams. */
+SLMC_API int slmc_set_sub_batch_priorities(slmc_ctx* ctx, int on);
+
 /* Column groups per CTA of the FP32 slice kernel: 1 (default, 0 selects it) or 2. One group
  * (256 threads, about 104 KB of shared memory at N = 256) leaves room on the SM for a CTA of
  * another sub-batch's FP64 stabilisation, so the FP32 and FP64 pipes work at the same time;

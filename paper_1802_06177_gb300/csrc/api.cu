@@ -204,11 +204,11 @@ int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign,
     SLMC_CK(cudaEventRecord(c->sub_fork, s));
     for (int k = 0; k < nsub; ++k) {
         const int f0 = (int)((long long)k * nf / nsub), f1 = (int)((long long)(k + 1) * nf / nsub);
-        SLMC_CK(cudaStreamWaitEvent(c->sub_stream[k], c->sub_fork, 0));
+        cudaStream_t sk = c->sub_prio ? c->sub_stream_prio[k] : c->sub_stream[k];
+        SLMC_CK(cudaStreamWaitEvent(sk, c->sub_fork, 0));
         slmc_ctx v = make_view(c, f0);
-        SLMC_TRY(logdet_run(c, &v, x + f0 * NL, f1 - f0, lndet + f0, sign + f0, G ? G + f0 * NN : nullptr,
-                            c->sub_stream[k]));
-        SLMC_CK(cudaEventRecord(c->sub_join[k], c->sub_stream[k]));
+        SLMC_TRY(logdet_run(c, &v, x + f0 * NL, f1 - f0, lndet + f0, sign + f0, G ? G + f0 * NN : nullptr, sk));
+        SLMC_CK(cudaEventRecord(c->sub_join[k], sk));
         SLMC_CK(cudaStreamWaitEvent(s, c->sub_join[k], 0));
     }
     return SLMC_OK;
@@ -227,6 +227,7 @@ int for_batches(slmc_ctx* c, int n, F&& fn) {
 void free_ctx(slmc_ctx* c) {
     for (int k = 0; k < slmc_ctx::kMaxSub; ++k) {
         if (c->sub_stream[k]) cudaStreamDestroy(c->sub_stream[k]);
+        if (c->sub_stream_prio[k]) cudaStreamDestroy(c->sub_stream_prio[k]);
         if (c->sub_join[k]) cudaEventDestroy(c->sub_join[k]);
     }
     if (c->sub_fork) cudaEventDestroy(c->sub_fork);
@@ -340,9 +341,17 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     c->nsub = 0;
     if (max_fields >= 2 * kMinSubFields) {
         bool sok = cudaEventCreateWithFlags(&c->sub_fork, cudaEventDisableTiming) == cudaSuccess;
-        for (int k = 0; k < slmc_ctx::kMaxSub && sok; ++k)
+        int prio_least = 0, prio_greatest = 0;
+        sok = sok && cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) == cudaSuccess;
+        for (int k = 0; k < slmc_ctx::kMaxSub && sok; ++k) {
+            // sub-batch k on priority greatest + k: the first sub-batch runs ahead and the others fill
+            // the SMs it leaves idle, so the sub-batches drift out of phase (FP32 slice products of one
+            // beside FP64 stabilisation of another)
+            const int prio = std::min(prio_greatest + k, prio_least);
             sok = cudaStreamCreateWithFlags(&c->sub_stream[k], cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithPriority(&c->sub_stream_prio[k], cudaStreamNonBlocking, prio) == cudaSuccess &&
                   cudaEventCreateWithFlags(&c->sub_join[k], cudaEventDisableTiming) == cudaSuccess;
+        }
         if (sok) {
             c->nsub_avail = slmc_ctx::kMaxSub;
             c->nsub = 3;
@@ -517,6 +526,13 @@ int slmc_set_tuning(slmc_ctx* c, int qr_panel, int slice_cols) {
 int slmc_set_slice_groups(slmc_ctx* c, int groups) {
     if (!c || groups < 0 || groups > 2) return SLMC_ERR_ARG;
     c->tune_slice_groups = groups;
+    return SLMC_OK;
+}
+
+int slmc_set_sub_batch_priorities(slmc_ctx* c, int on) {
+    if (!c || on < 0 || on > 1) return SLMC_ERR_ARG;
+    if (on && c->nsub_avail == 0) return SLMC_ERR_UNSUPPORTED;
+    c->sub_prio = on;
     return SLMC_OK;
 }
 

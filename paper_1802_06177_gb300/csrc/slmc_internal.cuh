@@ -69,6 +69,8 @@ struct slmc_ctx {
     int nsub;       // sub-batches used for large batches (1 = no split)
     int nsub_avail; // forked streams created at init (0 or kMaxSub)
     cudaStream_t sub_stream[kMaxSub];
+    cudaStream_t sub_stream_prio[kMaxSub];  // same, with descending scheduling priorities
+    int sub_prio;                           // 1: sub-batches use the prioritised streams
     cudaEvent_t sub_fork, sub_join[kMaxSub];
     slmc_ctx* parent;
     // Launch accounting and optional per-class event timing (host side).

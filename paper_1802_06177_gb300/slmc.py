@@ -38,7 +38,8 @@ EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", 
            "slmc_get_update_counter", "slmc_set_tuning", "slmc_batch_create", "slmc_batch_destroy",
            "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune",
            "slmc_fit_eff_state", "slmc_fit_eff_merge", "slmc_profile_read_detail",
-           "slmc_set_sub_batches", "slmc_set_slice_groups")
+           "slmc_set_sub_batches", "slmc_set_slice_groups",
+           "slmc_set_sub_batch_priorities")
 
 UPDATE_CONTINUE = (1 << 64) - 1
 FIT_STATE_DOUBLES = 64
@@ -98,6 +99,7 @@ def load_library(path=LIB_PATH):
         "slmc_profile_read_detail": ([P, P, P, P, P, V], I),
         "slmc_set_sub_batches": ([P, I], I),
         "slmc_set_slice_groups": ([P, I], I),
+        "slmc_set_sub_batch_priorities": ([P, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -305,6 +307,10 @@ class Context:
     def set_slice_groups(self, groups):
         """Column groups per CTA of the FP32 slice kernel (0 = default 1, or 2)."""
         self._check("slmc_set_slice_groups", self.lib.slmc_set_slice_groups(self._ctx, groups))
+
+    def set_sub_batch_priorities(self, on):
+        """Descending stream priorities for the sub-batches (1) or equal priorities (0)."""
+        self._check("slmc_set_sub_batch_priorities", self.lib.slmc_set_sub_batch_priorities(self._ctx, 1 if on else 0))
 
     def set_sub_batches(self, n):
         """Sub-batches (forked streams) a large determinant batch is split into (1..4)."""

@@ -218,6 +218,10 @@ def test_sub_batch_split_is_bit_identical_and_profiled(precision):
         assert units == nf * groups and calls == groups * nsub
         assert 0.0 < busy <= ms * (1 + 1e-6) + 1e-3
         assert prof["greens"][3] == nf
+    ctx.set_sub_batches(3)
+    ctx.set_sub_batch_priorities(1)
+    G, ld, sg = ctx.greens(cuda(x))
+    out.append((G.cpu().numpy(), ld.cpu().numpy(), sg.cpu().numpy()))
     for G, ld, sg in out[1:]:
         assert np.array_equal(G, out[0][0]) and np.array_equal(ld, out[0][1]) and np.array_equal(sg, out[0][2])
     p = HolsteinParams(Lx, Lx, L, n_s=n_s)
