@@ -208,6 +208,13 @@ SLMC_API int slmc_set_sub_batches(slmc_ctx* ctx, int n);
  * Results do not depend on it. SLMC_ERR_UNSUPPORTED for contexts without forked streams. */
 SLMC_API int slmc_set_sub_batch_priorities(slmc_ctx* ctx, int on);
 
+/* CTAs per field for the stabilising QR and the formation of Q: 1, 2 or 4 (0 = automatic:
+ * 4 when there are at most a quarter as many fields as SMs, 2 up to half, else 1). With more
+ * than one, the QR of a field runs on a thread-block cluster (panels round-robin over the
+ * CTAs, the panel's reflectors shared through distributed shared memory) and Q's columns are
+ * split over the CTAs. Results are bit-identical for every value. */
+SLMC_API int slmc_set_qr_cluster(slmc_ctx* ctx, int ctas);
+
 /* Column groups per CTA of the FP32 slice kernel: 1 (default, 0 selects it) or 2. One group
  * (256 threads, about 104 KB of shared memory at N = 256) leaves room on the SM for a CTA of
  * another sub-batch's FP64 stabilisation, so the FP32 and FP64 pipes work at the same time;

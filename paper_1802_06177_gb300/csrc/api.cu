@@ -191,6 +191,8 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
     v.tune_qr_panel = c->tune_qr_panel;
     v.tune_slice_cols = c->tune_slice_cols;
     v.tune_slice_groups = c->tune_slice_groups;
+    v.tune_qr_cluster = c->tune_qr_cluster;
+    v.num_sms = c->num_sms;
     v.nsub = 0;
     v.parent = c;
     return v;
@@ -280,7 +282,8 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     c->N = p->Lx * p->Ly;
     c->L = p->L;
     c->max_fields = max_fields;
-    if (cudaGetDevice(&c->device) != cudaSuccess) {
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
         delete c;
         return SLMC_ERR_CUDA;
     }
@@ -526,6 +529,12 @@ int slmc_set_tuning(slmc_ctx* c, int qr_panel, int slice_cols) {
 int slmc_set_slice_groups(slmc_ctx* c, int groups) {
     if (!c || groups < 0 || groups > 2) return SLMC_ERR_ARG;
     c->tune_slice_groups = groups;
+    return SLMC_OK;
+}
+
+int slmc_set_qr_cluster(slmc_ctx* c, int ctas) {
+    if (!c || (ctas != 0 && ctas != 1 && ctas != 2 && ctas != 4)) return SLMC_ERR_ARG;
+    c->tune_qr_cluster = ctas;
     return SLMC_OK;
 }
 

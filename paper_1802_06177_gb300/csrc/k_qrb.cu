@@ -16,9 +16,21 @@
 // (pivot keys ||y_j||^2 exp(2 (lnD_j - max lnD)), new scales ln D'_k = ln|R_kk| + lnD_{p_k}).
 // Outputs match the unblocked kernel (logical column order): QR = Rt on/above the diagonal and
 // v_k below it, tau, perm, lnD', sgnU, plus the panels' WY triangles S for the formation of Q.
+//
+// Few large fields (fewer fields than SMs) are factored by a thread-block cluster of C CTAs per
+// field: panel t belongs to CTA t mod C, which also owns (and alone updates) the columns of
+// every panel t' = t mod C. The owner factors the panel in its shared memory; after a cluster
+// barrier the other CTAs copy V, S and the new scales from the owner's shared memory
+// (distributed shared memory) and update their own trailing columns. One cluster barrier per
+// panel suffices: a CTA overwrites its panel buffer only C panels later, after every CTA has
+// passed the barriers in between (and so finished its copies). C = 1 is the one-CTA kernel.
 #include <cfloat>
 
+#include <cooperative_groups.h>
+
 #include "slmc_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -70,22 +82,21 @@ __device__ __forceinline__ void wy_rows(const T* __restrict__ Vp, const T* __res
     }
 }
 
-// Rank-BP update of columns [j_begin, N) rows [p, N) of the column-major matrix A (column j
-// stored at col(j)): A <- (I - V op(S) V^T) A, op(S) = S^T for the QR trailing update
-// (Q_p^T A) and S for the backward formation of Q (Q_p A). V is the clean panel in shared
-// memory (rows p..N-1, unit diagonal, zeros above), row stride BP+1.
+// Rank-BP update of ncols columns, rows [p, N), of a column-major matrix A (column jj stored at
+// col(jj)): A <- (I - V op(S) V^T) A, op(S) = S^T for the QR trailing update (Q_p^T A) and S
+// for the backward formation of Q (Q_p A). V is the clean panel in shared memory (rows
+// p..N-1, unit diagonal, zeros above), row stride BP+1.
 template <int BP, bool TRANS, typename T, typename ColFn>
 __device__ __forceinline__ void wy_update(const T* __restrict__ Vp, const T* __restrict__ Ssm, T* __restrict__ Wsm,
-                                          int N, int p, int nb, int j_begin, ColFn col) {
+                                          int N, int p, int nb, int ncols, ColFn col) {
     constexpr int BPS = BP + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T* W = Wsm + warp * BP * kCT;
     using CT = decltype(col(0));  // column pointer: same precision as T (no conversions in the loops)
-    const int ncols = N - j_begin;
     for (int g = warp * kCT; g < ncols; g += kWarps * kCT) {
         CT cptr[kCT];
 #pragma unroll
-        for (int c = 0; c < kCT; ++c) cptr[c] = (j_begin + g + c < N) ? col(j_begin + g + c) : nullptr;
+        for (int c = 0; c < kCT; ++c) cptr[c] = (g + c < ncols) ? col(g + c) : nullptr;
         // W[m][c] = sum_r V[r][m] A[r][c]: lane (m, h) owns reflector m = lane % BP and the
         // CPL columns of half h = lane / BP (A rows are broadcast to the warp)
         constexpr int CPL = kCT * BP / 32;
@@ -207,7 +218,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
                                                   int* __restrict__ perm_all, int* __restrict__ sgnU,
                                                   double* __restrict__ Sall, unsigned int* __restrict__ err, int N) {
     constexpr int BPS = BP + 1;
-    const int f = blockIdx.x;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+    const int f = blockIdx.x / C;
     const size_t NN = (size_t)N * N;
     double* __restrict__ Y = Yall + f * NN;
     double* __restrict__ QR = QRall + f * NN;
@@ -268,165 +281,207 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
         if (fabs(s_lnd[k]) > 600.0) s_wide = 1;
 
     // ---- panels ----
-    for (int p = 0; p < N; p += BP) {
-        const int nb = min(BP, N - p);
+    const int npanels = (N + BP - 1) / BP;
+    for (int t = 0; t < npanels; ++t) {
+        const int p = t * BP, nb = min(BP, N - p), owner = t % C;
         __syncthreads();
-        for (int idx = tid; idx < nb * (N - p); idx += kThreads) {
-            const int c = idx / (N - p), rr = idx - c * (N - p);
-            Vp[(p + rr) * BPS + c] = Y[(size_t)s_perm[p + c] * N + p + rr];
-        }
-        __syncthreads();
-        // Householder on the panel (shared memory), one block barrier per column: warp 0 applies
-        // reflector c to column c+1 and forms reflector c+1 from it, while warps 1.. apply
-        // reflector c to columns c+2.. (their dot products and reductions interleaved).
-        if (warp == 0) panel_reflector<BP>(Vp, k_of(p, 0), 0, N, lane, s_tau, s_beta, tau_all + (size_t)f * N, &s_ntriv);
-        __syncthreads();
-        for (int c = 0; c < nb; ++c) {
-            const int k = p + c;
-            const double tau = s_tau[c];
-            if (warp == 0) {
-                if (c + 1 < nb) {
-                    if (tau != 0.0) panel_apply<BP, 1>(Vp, k, c, tau, c + 1, 1, N, lane);
-                    __syncwarp();
-                    panel_reflector<BP>(Vp, k + 1, c + 1, N, lane, s_tau, s_beta, tau_all + (size_t)f * N, &s_ntriv);
+        if (rank == owner) {
+            for (int idx = tid; idx < nb * (N - p); idx += kThreads) {
+                const int c = idx / (N - p), rr = idx - c * (N - p);
+                Vp[(p + rr) * BPS + c] = Y[(size_t)s_perm[p + c] * N + p + rr];
+            }
+            __syncthreads();
+            // Householder on the panel (shared memory), one block barrier per column: warp 0 applies
+            // reflector c to column c+1 and forms reflector c+1 from it, while warps 1.. apply
+            // reflector c to columns c+2.. (their dot products and reductions interleaved).
+            if (warp == 0) panel_reflector<BP>(Vp, k_of(p, 0), 0, N, lane, s_tau, s_beta, tau_all + (size_t)f * N, &s_ntriv);
+            __syncthreads();
+            for (int c = 0; c < nb; ++c) {
+                const int k = p + c;
+                const double tau = s_tau[c];
+                if (warp == 0) {
+                    if (c + 1 < nb) {
+                        if (tau != 0.0) panel_apply<BP, 1>(Vp, k, c, tau, c + 1, 1, N, lane);
+                        __syncwarp();
+                        panel_reflector<BP>(Vp, k + 1, c + 1, N, lane, s_tau, s_beta, tau_all + (size_t)f * N, &s_ntriv);
+                    }
+                } else if (tau != 0.0) {
+                    // columns c0, c0 + 7, ... below nb (warp-uniform count nv <= 5)
+                    const int c0 = c + 2 + (warp - 1), cs = kWarps - 1;
+                    const int nv = (c0 < nb) ? (nb - 1 - c0) / cs + 1 : 0;
+                    switch (nv) {
+                        case 0: break;
+                        case 1: panel_apply<BP, 1>(Vp, k, c, tau, c0, cs, N, lane); break;
+                        case 2: panel_apply<BP, 2>(Vp, k, c, tau, c0, cs, N, lane); break;
+                        case 3: panel_apply<BP, 3>(Vp, k, c, tau, c0, cs, N, lane); break;
+                        case 4: panel_apply<BP, 4>(Vp, k, c, tau, c0, cs, N, lane); break;
+                        default: panel_apply<BP, 5>(Vp, k, c, tau, c0, cs, N, lane); break;
+                    }
                 }
-            } else if (tau != 0.0) {
-                // columns c0, c0 + 7, ... below nb (warp-uniform count nv <= 5)
-                const int c0 = c + 2 + (warp - 1), cs = kWarps - 1;
-                const int nv = (c0 < nb) ? (nb - 1 - c0) / cs + 1 : 0;
-                switch (nv) {
-                    case 0: break;
-                    case 1: panel_apply<BP, 1>(Vp, k, c, tau, c0, cs, N, lane); break;
-                    case 2: panel_apply<BP, 2>(Vp, k, c, tau, c0, cs, N, lane); break;
-                    case 3: panel_apply<BP, 3>(Vp, k, c, tau, c0, cs, N, lane); break;
-                    case 4: panel_apply<BP, 4>(Vp, k, c, tau, c0, cs, N, lane); break;
-                    default: panel_apply<BP, 5>(Vp, k, c, tau, c0, cs, N, lane); break;
+                __syncthreads();
+            }
+            // new scales of this panel's rows
+            if (tid < nb) {
+                const int k = p + tid;
+                const double l = log(fabs(s_beta[tid])) + s_lnd[s_perm[k]];
+                s_lnDn[k] = l;
+                s_g[k] = exp(-l);
+                if (fabs(l) > 600.0) s_wide = 1;
+            }
+            __syncthreads();
+            // write logical columns p..p+nb-1 of the packed output (Rt above, v below)
+            const bool wide = s_wide != 0;
+            for (int c = warp; c < nb; c += kWarps) {
+                const int k = p + c;
+                const int pc = s_perm[k];
+                const double lk = s_lnd[pc];
+                const double ek = wide ? 0.0 : exp(lk);
+                for (int i = lane; i < N; i += 32) {
+                    double o;
+                    if (i < k) {
+                        const double rv = (i < p) ? Y[(size_t)pc * N + i] : Vp[i * BPS + c];
+                        o = wide ? rv * exp(lk - s_lnDn[i]) : rv * ek * s_g[i];
+                    } else if (i == k) {
+                        o = (s_beta[c] >= 0.0) ? 1.0 : -1.0;
+                    } else {
+                        o = Vp[i * BPS + c];
+                    }
+                    QR[(size_t)k * N + i] = o;
                 }
             }
             __syncthreads();
-        }
-        // new scales of this panel's rows
-        if (tid < nb) {
-            const int k = p + tid;
-            const double l = log(fabs(s_beta[tid])) + s_lnd[s_perm[k]];
-            s_lnDn[k] = l;
-            s_g[k] = exp(-l);
-            if (fabs(l) > 600.0) s_wide = 1;
-        }
-        __syncthreads();
-        // write logical columns p..p+nb-1 of the packed output (Rt above, v below)
-        const bool wide = s_wide != 0;
-        for (int c = warp; c < nb; c += kWarps) {
-            const int k = p + c;
-            const int pc = s_perm[k];
-            const double lk = s_lnd[pc];
-            const double ek = wide ? 0.0 : exp(lk);
-            for (int i = lane; i < N; i += 32) {
-                double o;
-                if (i < k) {
-                    const double rv = (i < p) ? Y[(size_t)pc * N + i] : Vp[i * BPS + c];
-                    o = wide ? rv * exp(lk - s_lnDn[i]) : rv * ek * s_g[i];
-                } else if (i == k) {
-                    o = (s_beta[c] >= 0.0) ? 1.0 : -1.0;
-                } else {
-                    o = Vp[i * BPS + c];
-                }
-                QR[(size_t)k * N + i] = o;
+            // clean V (unit diagonal, zeros above) and the Gram matrix G = V^T V in Wsm
+            for (int idx = tid; idx < nb * nb; idx += kThreads) {
+                const int a = idx / nb, c = idx - a * nb;  // Vp row p+a, column c
+                if (a < c) Vp[(p + a) * BPS + c] = 0.0;
+                else if (a == c) Vp[(p + a) * BPS + c] = 1.0;
             }
-        }
-        __syncthreads();
-        // clean V (unit diagonal, zeros above) and the Gram matrix G = V^T V in Wsm
-        for (int idx = tid; idx < nb * nb; idx += kThreads) {
-            const int a = idx / nb, c = idx - a * nb;  // Vp row p+a, column c
-            if (a < c) Vp[(p + a) * BPS + c] = 0.0;
-            else if (a == c) Vp[(p + a) * BPS + c] = 1.0;
-        }
-        __syncthreads();
-        double* G = Wsm;  // [BP][BP]
-        {   // G[a][c] = v_a . v_c for a < c; each warp interleaves four pairs (independent chains)
-            const int npairs = nb * (nb - 1) / 2;
-            for (int q0 = warp * 4; q0 < npairs; q0 += kWarps * 4) {
-                int pa[4], pc[4];
-                double d[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    int q = q0 + j, cc = 1;
-                    while (q >= cc) {  // pair index -> (a, c): pairs ordered by c, then a
-                        q -= cc;
-                        ++cc;
-                    }
-                    pa[j] = q;
-                    pc[j] = (q0 + j < npairs) ? cc : N;  // N: empty range
-                    d[j] = 0.0;
-                }
-                const int rmax = N - p - pc[0];
-                for (int t = 0; t * 32 < rmax; ++t) {
-#pragma unroll
+            __syncthreads();
+            double* G = Wsm;  // [BP][BP]
+            {   // G[a][c] = v_a . v_c for a < c; each warp interleaves four pairs (independent chains)
+                const int npairs = nb * (nb - 1) / 2;
+                for (int q0 = warp * 4; q0 < npairs; q0 += kWarps * 4) {
+                    int pa[4], pc[4];
+                    double d[4];
+    #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const int r = p + pc[j] + lane + 32 * t;
-                        if (r < N) d[j] = fma(Vp[r * BPS + pa[j]], Vp[r * BPS + pc[j]], d[j]);
+                        int q = q0 + j, cc = 1;
+                        while (q >= cc) {  // pair index -> (a, c): pairs ordered by c, then a
+                            q -= cc;
+                            ++cc;
+                        }
+                        pa[j] = q;
+                        pc[j] = (q0 + j < npairs) ? cc : N;  // N: empty range
+                        d[j] = 0.0;
+                    }
+                    const int rmax = N - p - pc[0];
+                    for (int t = 0; t * 32 < rmax; ++t) {
+    #pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int r = p + pc[j] + lane + 32 * t;
+                            if (r < N) d[j] = fma(Vp[r * BPS + pa[j]], Vp[r * BPS + pc[j]], d[j]);
+                        }
+                    }
+    #pragma unroll
+                    for (int j = 0; j < 4; ++j) d[j] = slmc::warp_allsum(d[j]);
+                    if (lane == 0) {
+    #pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (q0 + j < npairs) G[pa[j] * BP + pc[j]] = d[j];
                     }
                 }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) d[j] = slmc::warp_allsum(d[j]);
-                if (lane == 0) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (q0 + j < npairs) G[pa[j] * BP + pc[j]] = d[j];
+            }
+            __syncthreads();
+            // S: S_cc = tau_c, S[0:c, c] = -tau_c S[0:c, 0:c] G[0:c, c]  (one warp, lane = row)
+            if (warp == 0) {
+                for (int c = 0; c < nb; ++c) {
+                    const double tc = s_tau[c];
+                    double v = 0.0;
+                    if (lane < c) {  // four independent partial sums (short dependency chains)
+                        double v4[4] = {0.0, 0.0, 0.0, 0.0};
+                        int q = lane;
+                        for (; q + 4 <= c; q += 4) {
+    #pragma unroll
+                            for (int j = 0; j < 4; ++j) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * BP + c], v4[j]);
+                        }
+    #pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            if (q + j < c) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * BP + c], v4[j]);
+                        v = -tc * ((v4[0] + v4[1]) + (v4[2] + v4[3]));
+                    } else if (lane == c) {
+                        v = tc;
+                    }
+                    if (lane < BP) Ssm[lane * BP + c] = (lane <= c) ? v : 0.0;
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            for (int idx = tid; idx < nb * BP; idx += kThreads) {
+                const int a = idx / BP, b = idx - a * BP;
+                Sall[(size_t)f * N * BP + (size_t)(p + a) * BP + b] = (b < nb) ? Ssm[a * BP + b] : 0.0;
+            }
+        }  // owner
+        if (C > 1) {
+            cluster.sync();  // panel t: V, S and the new scales are in the owner's shared memory
+            if (rank != owner) {
+                const double* oV = cluster.map_shared_rank(Vp, owner);
+                const double* oS = cluster.map_shared_rank(Ssm, owner);
+                const double* oL = cluster.map_shared_rank(s_lnDn, owner);
+                const double* oG = cluster.map_shared_rank(s_g, owner);
+                for (int idx = tid; idx < (N - p) * nb; idx += kThreads) {
+                    const int rr = idx / nb, c = idx - rr * nb;
+                    Vp[(p + rr) * BPS + c] = oV[(p + rr) * BPS + c];
+                }
+                for (int idx = tid; idx < BP * BP; idx += kThreads) Ssm[idx] = oS[idx];
+                if (tid < nb) {
+                    const double l = oL[p + tid];
+                    s_lnDn[p + tid] = l;
+                    s_g[p + tid] = oG[p + tid];
+                    if (fabs(l) > 600.0) s_wide = 1;
                 }
             }
         }
         __syncthreads();
-        // S: S_cc = tau_c, S[0:c, c] = -tau_c S[0:c, 0:c] G[0:c, c]  (one warp, lane = row)
-        if (warp == 0) {
-            for (int c = 0; c < nb; ++c) {
-                const double tc = s_tau[c];
-                double v = 0.0;
-                if (lane < c) {  // four independent partial sums (short dependency chains)
-                    double v4[4] = {0.0, 0.0, 0.0, 0.0};
-                    int q = lane;
-                    for (; q + 4 <= c; q += 4) {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * BP + c], v4[j]);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-                        if (q + j < c) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * BP + c], v4[j]);
-                    v = -tc * ((v4[0] + v4[1]) + (v4[2] + v4[3]));
-                } else if (lane == c) {
-                    v = tc;
-                }
-                if (lane < BP) Ssm[lane * BP + c] = (lane <= c) ? v : 0.0;
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        for (int idx = tid; idx < nb * BP; idx += kThreads) {
-            const int a = idx / BP, b = idx - a * BP;
-            Sall[(size_t)f * N * BP + (size_t)(p + a) * BP + b] = (b < nb) ? Ssm[a * BP + b] : 0.0;
-        }
-        // trailing update C <- Q_p^T C on logical columns p+nb..N-1
-        wy_update<BP, true>(Vp, Ssm, Wsm, N, p, nb, p + nb, [&](int j) { return Y + (size_t)s_perm[j] * N; });
+        // trailing update C <- Q_p^T C on this CTA's logical columns beyond the panel: the columns
+        // of panels t1, t1 + C, ... (t1 the first panel after t that this CTA owns)
+        const int t1 = t + 1 + ((rank - (t + 1)) % C + C) % C;
+        int ncols = 0;
+        for (int u = t1; u < npanels; u += C) ncols += min(BP, N - u * BP);
+        wy_update<BP, true>(Vp, Ssm, Wsm, N, p, nb, ncols, [&](int jj) {
+            const int j = (t1 + (jj / BP) * C) * BP + jj % BP;
+            return Y + (size_t)s_perm[j] * N;
+        });
     }
+    if (C > 1) cluster.sync();  // every CTA holds all scales; the ranks' reflector counts are final
     __syncthreads();
-    bool bad = false;
-    for (int k = tid; k < N; k += kThreads) {
-        lnD_all[(size_t)f * N + k] = s_lnDn[k];
-        perm_all[(size_t)f * N + k] = s_perm[k];
-        bad |= !isfinite(s_lnDn[k]);
+    if (rank == 0) {
+        bool bad = false;
+        for (int k = tid; k < N; k += kThreads) {
+            lnD_all[(size_t)f * N + k] = s_lnDn[k];
+            perm_all[(size_t)f * N + k] = s_perm[k];
+            bad |= !isfinite(s_lnDn[k]);
+        }
+        if (tid == 0) {
+            int ntriv = s_ntriv;
+            for (int r = 1; r < C; ++r) ntriv += *cluster.map_shared_rank(&s_ntriv, r);
+            sgnU[f] = (ntriv & 1) ? -1 : 1;
+        }
+        if (bad) atomicOr(err, SLMC_EBIT_NONFINITE);
     }
-    if (tid == 0) sgnU[f] = (s_ntriv & 1) ? -1 : 1;
-    if (bad) atomicOr(err, SLMC_EBIT_NONFINITE);
+    if (C > 1) cluster.sync();  // shared memory stays alive until rank 0 has read the counts
 }
 
 // Q = Q_0 Q_1 ... (Q_p = I - V_p S_p V_p^T), accumulated backwards into U (column-major),
 // computed in T: FP64, or FP32 when Q only feeds reduced-precision slice products (which round
 // it to FP32 on entry anyway).
+// Columns of Q are independent: CTA (field, blockIdx.y) forms columns [j0, j1) of gridDim.y
+// blocks (several CTAs per field when there are few fields).
 template <int BP, typename T>
 __global__ void __launch_bounds__(kThreads, 2) k_formq_b(const double* __restrict__ QRall, const double* __restrict__ Sall,
                                                       T* __restrict__ Uall, int N) {
     constexpr int BPS = BP + 1;
     const int f = blockIdx.x;
+    const int j0 = (int)((long long)blockIdx.y * N / gridDim.y), j1 = (int)((long long)(blockIdx.y + 1) * N / gridDim.y);
     const size_t NN = (size_t)N * N;
     const double* __restrict__ QR = QRall + f * NN;
     T* __restrict__ U = Uall + f * NN;
@@ -435,7 +490,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_formq_b(const double* __restric
     T* Ssm = Vp + (size_t)N * BPS;
     T* Wsm = Ssm + BP * BP;
     const int tid = threadIdx.x;
-    for (size_t idx = tid; idx < NN; idx += kThreads) U[idx] = (idx % (N + 1) == 0) ? T(1) : T(0);
+    for (size_t idx = (size_t)j0 * N + tid; idx < (size_t)j1 * N; idx += kThreads)
+        U[idx] = (idx % (N + 1) == 0) ? T(1) : T(0);
     for (int p = ((N - 1) / BP) * BP; p >= 0; p -= BP) {
         const int nb = min(BP, N - p);
         __syncthreads();
@@ -449,7 +505,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_formq_b(const double* __restric
             Ssm[a * BP + b] = (T)Sall[(size_t)f * N * BP + (size_t)(p + a) * BP + b];
         }
         __syncthreads();
-        wy_update<BP, false>(Vp, Ssm, Wsm, N, p, nb, p, [&](int j) { return U + (size_t)j * N; });
+        const int jb = max(p, j0);  // columns left of the panel are still unit vectors
+        if (jb < j1) wy_update<BP, false>(Vp, Ssm, Wsm, N, p, nb, j1 - jb, [&](int jj) { return U + (size_t)(jb + jj) * N; });
     }
 }
 
@@ -508,13 +565,38 @@ __global__ void __launch_bounds__(256) k_tupd(const double* __restrict__ QRall, 
     }
 }
 
+// CTAs per field for the QR and the formation of Q: 1, 2 or 4, so that few fields still
+// occupy most SMs (tuned value if set).
+int qr_cluster_size(const slmc_ctx* c, int nf) {
+    if (c->tune_qr_cluster) return c->tune_qr_cluster;
+    if (c->N < 128 || c->num_sms <= 0 || nf <= 0) return 1;
+    const int r = c->num_sms / nf;
+    return r >= 4 ? 4 : (r >= 2 ? 2 : 1);
+}
+
 template <int BP>
 cudaError_t launch_qrb(slmc_ctx* c, int nf, cudaStream_t s) {
     const size_t smem = QrSmem<BP>::bytes(c->N);
     cudaError_t e = cudaFuncSetAttribute(k_qrb<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_qrb<BP><<<nf, kThreads, smem, s>>>(c->Y, c->lnD, c->QR, c->tau, c->perm, c->sgnU, c->Sws, c->err, c->N);
-    return cudaGetLastError();
+    const int C = qr_cluster_size(c, nf);
+    if (C == 1) {
+        k_qrb<BP><<<nf, kThreads, smem, s>>>(c->Y, c->lnD, c->QR, c->tau, c->perm, c->sgnU, c->Sws, c->err, c->N);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nf * C));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_qrb<BP>, c->Y, c->lnD, c->QR, c->tau, c->perm, c->sgnU, c->Sws, c->err, c->N);
 }
 
 template <int BP, typename T>
@@ -525,7 +607,8 @@ cudaError_t launch_formq_b(slmc_ctx* c, int nf, cudaStream_t s) {
     T* U;
     if constexpr (sizeof(T) == 4) U = c->U32;
     else U = c->U;
-    k_formq_b<BP, T><<<nf, kThreads, smem, s>>>(c->QR, c->Sws, U, c->N);
+    dim3 grid(nf, qr_cluster_size(c, nf));  // column blocks per field
+    k_formq_b<BP, T><<<grid, kThreads, smem, s>>>(c->QR, c->Sws, U, c->N);
     return cudaGetLastError();
 }
 

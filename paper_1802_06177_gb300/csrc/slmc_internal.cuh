@@ -53,7 +53,9 @@ struct slmc_ctx {
     unsigned long long* dctr;  // device-side cumulative-update counter (Philox stream position)
     int tune_qr_panel;          // 0: by N; else 16 or 32 (blocked QR panel width)
     int tune_slice_cols;
-    int tune_slice_groups;  // FP32 slice kernel column groups per CTA (0 = default 1, or 2)        // 0: by N; else 8 or 16 (FP32 slice columns per thread)
+    int tune_slice_groups;
+    int tune_qr_cluster;    // CTAs per field of the QR / formation of Q (0 = by field count)
+    int num_sms;            // multiprocessors of the device  // FP32 slice kernel column groups per CTA (0 = default 1, or 2)        // 0: by N; else 8 or 16 (FP32 slice columns per thread)
     // Tensor-core slice path (SLMC_PREC_TF32X3 / BF16X9): operand pieces of F and of the
     // running slice product (ping/pong), FP32 copies of it, and their TMA descriptors.
     int tc_npad, tc_nt;

@@ -39,7 +39,7 @@ EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", 
            "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune",
            "slmc_fit_eff_state", "slmc_fit_eff_merge", "slmc_profile_read_detail",
            "slmc_set_sub_batches", "slmc_set_slice_groups",
-           "slmc_set_sub_batch_priorities")
+           "slmc_set_sub_batch_priorities", "slmc_set_qr_cluster")
 
 UPDATE_CONTINUE = (1 << 64) - 1
 FIT_STATE_DOUBLES = 64
@@ -100,6 +100,7 @@ def load_library(path=LIB_PATH):
         "slmc_set_sub_batches": ([P, I], I),
         "slmc_set_slice_groups": ([P, I], I),
         "slmc_set_sub_batch_priorities": ([P, I], I),
+        "slmc_set_qr_cluster": ([P, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -307,6 +308,10 @@ class Context:
     def set_slice_groups(self, groups):
         """Column groups per CTA of the FP32 slice kernel (0 = default 1, or 2)."""
         self._check("slmc_set_slice_groups", self.lib.slmc_set_slice_groups(self._ctx, groups))
+
+    def set_qr_cluster(self, ctas):
+        """CTAs per field of the QR and the formation of Q (0 = automatic, 1, 2 or 4)."""
+        self._check("slmc_set_qr_cluster", self.lib.slmc_set_qr_cluster(self._ctx, ctas))
 
     def set_sub_batch_priorities(self, on):
         """Descending stream priorities for the sub-batches (1) or equal priorities (0)."""
