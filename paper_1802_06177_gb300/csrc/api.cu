@@ -472,27 +472,51 @@ int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int n
     const size_t NL = (size_t)c->N * c->L;
     cudaStream_t s = as_stream(stream);
     if (update0 != SLMC_UPDATE_CONTINUE) SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::counter_op(c, update0, false, s));
+    // Chains are independent: a batch is split into sub-batches (as for slmc_logdet), each running all
+    // its updates (sweeps, E_eff, ln w with G, Eq. (6), S) on its own forked stream, so the sweeps of one
+    // sub-batch overlap the determinants of another.
     SLMC_TRY(for_batches(c, n, [&](int f0, int nf) {
-        double* xc = x + f0 * NL;
-        for (int u = 0; u < nupdates; ++u) {
-            SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::update_draws(c, nf, f0, (uint64_t)u, iscal(c, 1), scal(c, 4), s));
-            SLMC_CK(cudaMemcpyAsync(c->x_old, xc, nf * NL * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, xc, nf, J, nullptr, 0, scal(c, 1), s));
-            for (int sw = 0; sw < nsweeps; ++sw)
-                for (int h = 0; h < 2; ++h)
-                    SLMC_LAUNCH(SLMC_PROF_SWEEP, 1, s,
-                                slmc::eff_half_sweep(c, xc, nf, f0, J, (uint64_t)u * nsweeps + sw, 0, iscal(c, 1), h,
-                                                     n_sweep_acc ? n_sweep_acc + f0 : nullptr, s, c->dctr, nsweeps));
-            SLMC_LAUNCH(SLMC_PROF_EFF, 1, s, slmc::eff_features(c, xc, nf, J, nullptr, 0, scal(c, 2), s));
-            SLMC_TRY(logdet_batch(c, xc, nf, scal(c, 0), iscal(c, 0), s_cdw ? c->QR : nullptr, s));
-            SLMC_LAUNCH(SLMC_PROF_BOSE, 1, s, slmc::bose_log_weight(c, xc, nf, scal(c, 0), scal(c, 3), s));
-            SLMC_LAUNCH(SLMC_PROF_ACCEPT, 2, s,
-                        slmc::accept_update(c, nf, xc, c->x_old, scal(c, 3), scal(c, 1), scal(c, 2), scal(c, 4),
-                                            lnw + f0, iscal(c, 2), n_acc ? n_acc + f0 : nullptr, s));
-            if (s_cdw)
-                SLMC_LAUNCH(SLMC_PROF_CDW, 1, s,
-                            slmc::cdw_measure(c, c->QR, nf, s_cdw + f0, iscal(c, 2),
-                                              obs ? obs + (size_t)u * n + f0 : nullptr, s));
+        const bool tc = c->p.precision == SLMC_PREC_TF32X3 || c->p.precision == SLMC_PREC_BF16X9;
+        int nsub = std::min(c->nsub, nf / kMinSubFields);
+        if (nsub < 2 || tc) nsub = 1;
+        if (nsub > 1) SLMC_CK(cudaEventRecord(c->sub_fork, s));
+        for (int k = 0; k < nsub; ++k) {
+            const int a = (int)((long long)k * nf / nsub), b = (int)((long long)(k + 1) * nf / nsub), m = b - a;
+            cudaStream_t sk = nsub == 1 ? s : (c->sub_prio ? c->sub_stream_prio[k] : c->sub_stream[k]);
+            if (nsub > 1) SLMC_CK(cudaStreamWaitEvent(sk, c->sub_fork, 0));
+            slmc_ctx view = make_view(c, a);
+            slmc_ctx* v = nsub == 1 ? c : &view;
+            const int g0 = f0 + a;  // first chain of the sub-batch
+            double* xc = x + (size_t)g0 * NL;
+            double* xo = c->x_old + (size_t)a * NL;
+            auto sc = [&](int col) { return scal(c, col) + a; };
+            auto isc = [&](int col) { return iscal(c, col) + a; };
+            for (int u = 0; u < nupdates; ++u) {
+                c->cur_units = m;
+                SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, sk, slmc::update_draws(c, m, g0, (uint64_t)u, isc(1), sc(4), sk));
+                SLMC_CK(cudaMemcpyAsync(xo, xc, m * NL * sizeof(double), cudaMemcpyDeviceToDevice, sk));
+                SLMC_LAUNCH(SLMC_PROF_EFF, 1, sk, slmc::eff_features(c, xc, m, J, nullptr, 0, sc(1), sk));
+                for (int sw = 0; sw < nsweeps; ++sw)
+                    for (int h = 0; h < 2; ++h)
+                        SLMC_LAUNCH(SLMC_PROF_SWEEP, 1, sk,
+                                    slmc::eff_half_sweep(c, xc, m, g0, J, (uint64_t)u * nsweeps + sw, 0, isc(1), h,
+                                                         n_sweep_acc ? n_sweep_acc + g0 : nullptr, sk, c->dctr, nsweeps));
+                SLMC_LAUNCH(SLMC_PROF_EFF, 1, sk, slmc::eff_features(c, xc, m, J, nullptr, 0, sc(2), sk));
+                SLMC_TRY(logdet_run(c, v, xc, m, sc(0), isc(0), s_cdw ? v->QR : nullptr, sk));
+                c->cur_units = m;
+                SLMC_LAUNCH(SLMC_PROF_BOSE, 1, sk, slmc::bose_log_weight(c, xc, m, sc(0), sc(3), sk));
+                SLMC_LAUNCH(SLMC_PROF_ACCEPT, 2, sk,
+                            slmc::accept_update(c, m, xc, xo, sc(3), sc(1), sc(2), sc(4), lnw + g0, isc(2),
+                                                n_acc ? n_acc + g0 : nullptr, sk));
+                if (s_cdw)
+                    SLMC_LAUNCH(SLMC_PROF_CDW, 1, sk,
+                                slmc::cdw_measure(c, v->QR, m, s_cdw + g0, isc(2),
+                                                  obs ? obs + (size_t)u * n + g0 : nullptr, sk));
+            }
+            if (nsub > 1) {
+                SLMC_CK(cudaEventRecord(c->sub_join[k], sk));
+                SLMC_CK(cudaStreamWaitEvent(s, c->sub_join[k], 0));
+            }
         }
         return SLMC_OK;
     }));

@@ -267,19 +267,24 @@ __device__ __forceinline__ void givens_absorb(double (&Rrow)[7], double a, int l
     }
 }
 
+// Warps take consecutive chunks of the configurations (the first warp starts from the current
+// triangle), reduce them to partial triangles, and the partial triangles are merged pairwise
+// in shared memory (all rows are taken relative to the same reference, so no shift is needed).
 __global__ void k_fit_accumulate(double* __restrict__ R, const double* __restrict__ feat, int ldF,
                                  const double* __restrict__ lnw, int nconf, double sc) {
-    // one warp: lane m < 7 holds column m of the current row and of R's rows
-    const int lane = threadIdx.x;
-    if (lane == 0 && R[55] == 0.0) {
+    __shared__ double sR[32][49];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0 && R[55] == 0.0) {
         for (int q = 0; q < 5; ++q) R[49 + q] = feat[q];
         R[54] = lnw[0];
         R[55] = 1.0;
     }
-    __syncwarp();
-    double Rrow[7];
-    for (int k = 0; k < 7; ++k) Rrow[k] = (lane < 7) ? R[k * 7 + lane] : 0.0;
-    for (int c = 0; c < nconf; ++c) {
+    __syncthreads();
+    double Rrow[7];  // lane m < 7 holds column m of every row
+    for (int k = 0; k < 7; ++k) Rrow[k] = (warp == 0 && lane < 7) ? R[k * 7 + lane] : 0.0;
+    const int per = (nconf + nw - 1) / nw;
+    const int c0 = warp * per, c1 = min(nconf, c0 + per);
+    for (int c = c0; c < c1; ++c) {
         double a;
         if (lane == 0) a = 1.0;
         else if (lane < 6) a = (feat[(size_t)c * ldF + lane - 1] - R[49 + lane - 1]) / sc;
@@ -287,9 +292,20 @@ __global__ void k_fit_accumulate(double* __restrict__ R, const double* __restric
         else a = 0.0;
         givens_absorb(Rrow, a, lane);
     }
-    for (int k = 0; k < 7; ++k)
-        if (lane < 7) R[k * 7 + lane] = Rrow[k];
-    if (lane == 0) R[56] += nconf;
+    for (int st = 1; st < nw; st <<= 1) {
+        if (warp % (2 * st) == st)
+            for (int k = 0; k < 7; ++k)
+                if (lane < 7) sR[warp][k * 7 + lane] = Rrow[k];
+        __syncthreads();
+        if (warp % (2 * st) == 0 && warp + st < nw)
+            for (int k = 0; k < 7; ++k) givens_absorb(Rrow, (lane < 7) ? sR[warp + st][k * 7 + lane] : 0.0, lane);
+        __syncthreads();
+    }
+    if (warp == 0) {
+        for (int k = 0; k < 7; ++k)
+            if (lane < 7) R[k * 7 + lane] = Rrow[k];
+        if (lane == 0) R[56] += nconf;
+    }
 }
 
 // Merges partial states (same layout as R) into R. Each state's factor is first moved to the
@@ -419,7 +435,8 @@ cudaError_t fit_begin(slmc_ctx* c, double* R, cudaStream_t s) {
 }
 
 cudaError_t fit_accumulate(slmc_ctx* c, double* R, const double* feat, const double* lnw, int nconf, cudaStream_t s) {
-    k_fit_accumulate<<<1, 32, 0, s>>>(R, feat, 8, lnw, nconf, (double)c->N * c->L);
+    const int warps = nconf >= 32 * 16 ? 32 : (nconf + 15) / 16;  // about 16 configurations per warp
+    k_fit_accumulate<<<1, 32 * (warps < 1 ? 1 : warps), 0, s>>>(R, feat, 8, lnw, nconf, (double)c->N * c->L);
     return cudaGetLastError();
 }
 
