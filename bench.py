@@ -257,7 +257,7 @@ def config_of(wl, args, precision):
     return {"workload": wl.name, "model": "holstein_2d", "N": wl.N, "Lx": wl.Lx, "L": wl.L, "beta": wl.beta,
             "n_s": wl.n_s, "chains_per_gpu": args.fields or wl.nfields, "nsweeps": args.nsweeps,
             "sub_batches": getattr(args, "sub_batches", 0) or 3,
-            "slice_groups": getattr(args, "slice_groups", 0) or 1,
+            "slice_groups": getattr(args, "slice_groups", 0) or (4 if wl.N <= 256 else 1),
             "precision": precision, "global_batch": (args.fields or wl.nfields) * args.gpus,
             "parallelism": "replicas x%d" % args.gpus,
             "l2": "inputs larger than L2 (fields %.0f MB + workspace), no flush" % (

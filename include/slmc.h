@@ -215,10 +215,11 @@ SLMC_API int slmc_set_sub_batch_priorities(slmc_ctx* ctx, int on);
  * split over the CTAs. Results are bit-identical for every value. */
 SLMC_API int slmc_set_qr_cluster(slmc_ctx* ctx, int ctas);
 
-/* Column groups per CTA of the FP32 slice kernel: 1 (default, 0 selects it) or 2. One group
- * (256 threads, about 104 KB of shared memory at N = 256) leaves room on the SM for a CTA of
- * another sub-batch's FP64 stabilisation, so the FP32 and FP64 pipes work at the same time;
- * two groups (512 threads) fill the SM alone. Results do not depend on it. */
+/* Thread layout of the FP32 slice kernel: 1: one column group of 256 row threads; 2: two such
+ * groups (512 threads); 4 (N <= 256): four column groups of 64 row threads, each thread up to
+ * 4 rows x 8 columns. 0 (default) selects 4 for N <= 256 and 1 above. The 256-thread layouts (about 104 KB of shared memory
+ * at N = 256) leave room on the SM for a CTA of another sub-batch's FP64 stabilisation, so the
+ * FP32 and FP64 pipes work at the same time. Results do not depend on it. */
 SLMC_API int slmc_set_slice_groups(slmc_ctx* ctx, int groups);
 
 /* Multi-linear regression of the effective model [Eq. (5)]: least squares of

@@ -551,7 +551,7 @@ int slmc_set_tuning(slmc_ctx* c, int qr_panel, int slice_cols) {
 }
 
 int slmc_set_slice_groups(slmc_ctx* c, int groups) {
-    if (!c || groups < 0 || groups > 2) return SLMC_ERR_ARG;
+    if (!c || groups < 0 || groups > 4 || groups == 3) return SLMC_ERR_ARG;
     c->tune_slice_groups = groups;
     return SLMC_OK;
 }

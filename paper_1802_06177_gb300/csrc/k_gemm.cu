@@ -18,6 +18,7 @@
 namespace {
 
 constexpr int kWarps = 8;
+constexpr int kTS = 32;  // products accumulated in FP32 between two TwoSum steps of the FP32 slice kernel
 
 template <typename T>
 __device__ __forceinline__ T slice_scale(double xv, double dtlam);
@@ -166,8 +167,8 @@ __device__ __forceinline__ void stage_F(float* Fs, const float* __restrict__ Fhi
     }
 }
 
-template <int RPT, int NBT, int KB, int NCG>
-__global__ void __launch_bounds__(256 * NCG) k_slice_f32(const float* __restrict__ Fhi, const int* __restrict__ lo_kidx,
+template <int RPT, int NBT, int KB, int NCG, int TR>
+__global__ void __launch_bounds__(TR * NCG, (TR * NCG == 256 ? 2 : 1)) k_slice_f32(const float* __restrict__ Fhi, const int* __restrict__ lo_kidx,
                                                    const float* __restrict__ lo_val, int S,
                                                    const float* __restrict__ U, double* __restrict__ out,
                                                    const float* __restrict__ sc32, int N, int L, int l0, int nsl) {
@@ -178,10 +179,10 @@ __global__ void __launch_bounds__(256 * NCG) k_slice_f32(const float* __restrict
     float* P1 = P0 + (size_t)N * NBP;
     float* Fs0 = P1 + (size_t)N * NBP;  // two stages of [KB][N]
     float* Fs1 = Fs0 + (size_t)KB * N;
-    const int f = blockIdx.y, j0 = blockIdx.x * NB, tid = threadIdx.x & 255, cg = (threadIdx.x >> 8) * NBT;
+    const int f = blockIdx.y, j0 = blockIdx.x * NB, tid = threadIdx.x % TR, cg = (threadIdx.x / TR) * NBT;
     const size_t NN = (size_t)N * N;
     const int nblk = (N + KB - 1) / KB;
-    for (int idx = threadIdx.x; idx < NB * N; idx += 256 * NCG) {
+    for (int idx = threadIdx.x; idx < NB * N; idx += TR * NCG) {
         const int jj = idx / N, k = idx - jj * N, j = j0 + jj;
         P0[k * NBP + jj] = (j < N) ? U[(size_t)f * NN + (size_t)j * N + k] : 0.f;
     }
@@ -217,23 +218,25 @@ __global__ void __launch_bounds__(256 * NCG) k_slice_f32(const float* __restrict
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    const int i = tid + 256 * r;
+                    const int i = tid + TR * r;
                     const float ah = (i < N) ? Fh[kk * N + i] : 0.f;
 #pragma unroll
                     for (int c = 0; c < NBT; ++c) blk[r][c] = fmaf(ah, pv[c], blk[r][c]);
                 }
             }
+            if (((b + 1) * KB) % kTS == 0 || b + 1 == nblk) {  // blocks of kTS products per TwoSum
 #pragma unroll
-            for (int r = 0; r < RPT; ++r)
+                for (int r = 0; r < RPT; ++r)
 #pragma unroll
-                for (int c = 0; c < NBT; ++c) {  // TwoSum(hi, blk) -> hi + error into cp
-                    const float t = __fadd_rn(hi[r][c], blk[r][c]);
-                    const float bp = __fsub_rn(t, hi[r][c]);
-                    const float e = __fadd_rn(__fsub_rn(hi[r][c], __fsub_rn(t, bp)), __fsub_rn(blk[r][c], bp));
-                    cp[r][c] = __fadd_rn(cp[r][c], e);
-                    hi[r][c] = t;
-                    blk[r][c] = 0.f;
-                }
+                    for (int c = 0; c < NBT; ++c) {  // TwoSum(hi, blk) -> hi + error into cp
+                        const float t = __fadd_rn(hi[r][c], blk[r][c]);
+                        const float bp = __fsub_rn(t, hi[r][c]);
+                        const float e = __fadd_rn(__fsub_rn(hi[r][c], __fsub_rn(t, bp)), __fsub_rn(blk[r][c], bp));
+                        cp[r][c] = __fadd_rn(cp[r][c], e);
+                        hi[r][c] = t;
+                        blk[r][c] = 0.f;
+                    }
+            }
             __syncthreads();  // the stage just read is refilled two blocks later
         }
         // F_lo on its stencil (rows of the panel already in shared memory)
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(256 * NCG) k_slice_f32(const float* __restrict
             const float v = __ldg(lo_val + q);
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
-                const int i = tid + 256 * r;
+                const int i = tid + TR * r;
                 if (i < N) {
                     const int k = __ldg(lo_kidx + (size_t)q * N + i);
 #pragma unroll
@@ -259,7 +262,7 @@ __global__ void __launch_bounds__(256 * NCG) k_slice_f32(const float* __restrict
         const float* scl = sc32 + ((size_t)f * L + l0 + s) * N;
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-            const int i = tid + 256 * r;
+            const int i = tid + TR * r;
             if (i >= N) continue;
             const float sc = scl[i];
 #pragma unroll
@@ -288,17 +291,17 @@ __global__ void __launch_bounds__(256 * NCG) k_slice_f32(const float* __restrict
 
 constexpr size_t kSmemBudget = 220 * 1024;
 
-template <int RPT, int NBT, int KB, int NCG>
+template <int RPT, int NBT, int KB, int NCG, int TR>
 cudaError_t launch_slice_f32_kb(const slmc_ctx* c, int nf, int l0, int nsl, cudaStream_t s) {
     const int N = c->N;
     constexpr int NBP = NCG * NBT + 4;
     const size_t smem = ((size_t)2 * N * NBP + (size_t)2 * KB * N) * sizeof(float);
-    cudaError_t e =
-        cudaFuncSetAttribute(k_slice_f32<RPT, NBT, KB, NCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_slice_f32<RPT, NBT, KB, NCG, TR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     constexpr int NB = NCG * NBT;
     dim3 grid((N + NB - 1) / NB, nf);
-    k_slice_f32<RPT, NBT, KB, NCG><<<grid, 256 * NCG, smem, s>>>(c->F32, c->lo_kidx, c->lo_val, c->lo_S, c->U32, c->Y, c->sc32, N,
+    k_slice_f32<RPT, NBT, KB, NCG, TR><<<grid, TR * NCG, smem, s>>>(c->F32, c->lo_kidx, c->lo_val, c->lo_S, c->U32, c->Y, c->sc32, N,
                                                       c->L, l0, nsl);
     return cudaGetLastError();
 }
@@ -306,20 +309,29 @@ cudaError_t launch_slice_f32_kb(const slmc_ctx* c, int nf, int l0, int nsl, cuda
 // Largest staged block (32, 16 or 8 rows of F) that fits the shared-memory budget. With one
 // column group (256 threads, about half the registers and shared memory of two groups) a CTA
 // leaves room on its SM for a CTA of the FP64 stabilisation kernels of another sub-batch.
-template <int RPT, int NBT, int NCG>
+template <int RPT, int NBT, int NCG, int TR = 256>
 cudaError_t launch_slice_f32_g(const slmc_ctx* c, int nf, int l0, int nsl, cudaStream_t s) {
-    const size_t budget = NCG == 1 ? kSmemBudget / 2 : kSmemBudget;
+    const size_t budget = TR * NCG == 256 ? kSmemBudget / 2 : kSmemBudget;
     const size_t panel = (size_t)2 * c->N * (NCG * NBT + 4) * sizeof(float);
     const size_t per_row = (size_t)2 * c->N * sizeof(float);
-    if (panel + 32 * per_row <= budget) return launch_slice_f32_kb<RPT, NBT, 32, NCG>(c, nf, l0, nsl, s);
-    if (panel + 16 * per_row <= budget) return launch_slice_f32_kb<RPT, NBT, 16, NCG>(c, nf, l0, nsl, s);
-    return launch_slice_f32_kb<RPT, NBT, 8, NCG>(c, nf, l0, nsl, s);
+    if (panel + 32 * per_row <= budget) return launch_slice_f32_kb<RPT, NBT, 32, NCG, TR>(c, nf, l0, nsl, s);
+    if (panel + 16 * per_row <= budget) return launch_slice_f32_kb<RPT, NBT, 16, NCG, TR>(c, nf, l0, nsl, s);
+    return launch_slice_f32_kb<RPT, NBT, 8, NCG, TR>(c, nf, l0, nsl, s);
 }
 
 template <int RPT, int NBT>
 cudaError_t launch_slice_f32(const slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s) {
     (void)x;
     if (c->tune_slice_groups == 2) return launch_slice_f32_g<RPT, NBT, 2>(c, nf, l0, nsl, s);
+    if ((c->tune_slice_groups == 4 || c->tune_slice_groups == 0) && c->N <= 256) {
+        // default for N <= 256: 64 row threads x 4 column groups of 8, up to 4 rows each
+        switch ((c->N + 63) / 64) {
+            case 1: return launch_slice_f32_g<1, 8, 4, 64>(c, nf, l0, nsl, s);
+            case 2: return launch_slice_f32_g<2, 8, 4, 64>(c, nf, l0, nsl, s);
+            case 3: return launch_slice_f32_g<3, 8, 4, 64>(c, nf, l0, nsl, s);
+            default: return launch_slice_f32_g<4, 8, 4, 64>(c, nf, l0, nsl, s);
+        }
+    }
     return launch_slice_f32_g<RPT, NBT, 1>(c, nf, l0, nsl, s);
 }
 

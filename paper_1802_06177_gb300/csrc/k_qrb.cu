@@ -150,6 +150,32 @@ __device__ __forceinline__ void wy_update(const T* __restrict__ Vp, const T* __r
     }
 }
 
+// Warp sums of K values per lane (K a power of two <= 32) with K - 1 + log2(32 / K) additions per
+// lane instead of 5 K: at each butterfly level a lane keeps half of its values and adds the
+// partner's copy of that half. Returns the sum of value index j in lane j * (32 / K).
+template <int K>
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[K], int lane) {
+#pragma unroll
+    for (int size = K, o = 16; size > 1; size >>= 1, o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < size / 2; ++i) {
+            const double keep = upper ? v[i + size / 2] : v[i];
+            const double other = upper ? v[i] : v[i + size / 2];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, other, o);
+        }
+    }
+    double sum = v[0];
+#pragma unroll
+    for (int o = 16 / K; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    return sum;
+}
+
+template <int N>
+struct Pow2Ceil {
+    static constexpr int value = N <= 1 ? 1 : (N <= 2 ? 2 : (N <= 4 ? 4 : (N <= 8 ? 8 : (N <= 16 ? 16 : 32))));
+};
+
 // Householder reflector of panel column c (logical row k = p + c) by one warp: beta, tau and
 // v = x / (alpha - beta) below the diagonal, written back into the panel.
 template <int BP>
@@ -197,8 +223,15 @@ __device__ __forceinline__ void panel_apply(double* __restrict__ Vp, int k, int 
 #pragma unroll
         for (int j = 0; j < NC; ++j) d[j] = fma(v, Vp[r * BPS + cols[j]], d[j]);
     }
+    {  // all NC dot products reduced together, then broadcast
+        constexpr int K = Pow2Ceil<NC>::value;
+        double t[K];
 #pragma unroll
-    for (int j = 0; j < NC; ++j) d[j] = slmc::warp_allsum(d[j]) * tau;
+        for (int j = 0; j < K; ++j) t[j] = (j < NC) ? d[j] : 0.0;
+        const double sum = warp_transpose_sum<K>(t, lane);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) d[j] = __shfl_sync(0xffffffffu, sum, j * (32 / K)) * tau;
+    }
     if (lane == 0) {
 #pragma unroll
         for (int j = 0; j < NC; ++j) Vp[k * BPS + cols[j]] -= d[j];
@@ -363,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
                 for (int q0 = warp * 4; q0 < npairs; q0 += kWarps * 4) {
                     int pa[4], pc[4];
                     double d[4];
-    #pragma unroll
+#pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         int q = q0 + j, cc = 1;
                         while (q >= cc) {  // pair index -> (a, c): pairs ordered by c, then a
@@ -376,19 +409,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
                     }
                     const int rmax = N - p - pc[0];
                     for (int t = 0; t * 32 < rmax; ++t) {
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const int r = p + pc[j] + lane + 32 * t;
                             if (r < N) d[j] = fma(Vp[r * BPS + pa[j]], Vp[r * BPS + pc[j]], d[j]);
                         }
                     }
-    #pragma unroll
-                    for (int j = 0; j < 4; ++j) d[j] = slmc::warp_allsum(d[j]);
-                    if (lane == 0) {
-    #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (q0 + j < npairs) G[pa[j] * BP + pc[j]] = d[j];
-                    }
+                    const double sum = warp_transpose_sum<4>(d, lane);  // pair j's sum in lane 8 j
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (lane == 8 * j && q0 + j < npairs) G[pa[j] * BP + pc[j]] = sum;
                 }
             }
             __syncthreads();
@@ -401,10 +431,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
                         double v4[4] = {0.0, 0.0, 0.0, 0.0};
                         int q = lane;
                         for (; q + 4 <= c; q += 4) {
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < 4; ++j) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * BP + c], v4[j]);
                         }
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < 3; ++j)
                             if (q + j < c) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * BP + c], v4[j]);
                         v = -tc * ((v4[0] + v4[1]) + (v4[2] + v4[3]));

@@ -306,7 +306,7 @@ class Context:
         self._check("slmc_set_tuning", self.lib.slmc_set_tuning(self._ctx, qr_panel, slice_cols))
 
     def set_slice_groups(self, groups):
-        """Column groups per CTA of the FP32 slice kernel (0 = default 1, or 2)."""
+        """Thread layout of the FP32 slice kernel (0 = default, 1, 2 or 4)."""
         self._check("slmc_set_slice_groups", self.lib.slmc_set_slice_groups(self._ctx, groups))
 
     def set_qr_cluster(self, ctas):

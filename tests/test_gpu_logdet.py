@@ -233,15 +233,17 @@ def test_sub_batch_split_is_bit_identical_and_profiled(precision):
 
 
 def test_slice_column_groups_bit_identical():
-    """One or two column groups per CTA of the FP32 slice kernel run the same arithmetic per
-    output element: bit-identical results."""
+    """The thread layouts of the FP32 slice kernel (one or two column groups of 256 row threads,
+    four groups of 64 row threads) run the same arithmetic per output element: bit-identical
+    results."""
     Lx, L, n_s, nf = 12, 40, 10, 20
     x = inputs.mixed_fields(nf, Lx, Lx, L, seed=91)
     ctx = make_ctx(Lx, L, n_s, precision="fp32", max_fields=nf)
     G2, ld2, _ = ctx.greens(cuda(x))
-    ctx.set_slice_groups(2)
-    G1, ld1, _ = ctx.greens(cuda(x))
-    assert torch.equal(G1, G2) and torch.equal(ld1, ld2)
+    for groups in (2, 4):
+        ctx.set_slice_groups(groups)
+        G1, ld1, _ = ctx.greens(cuda(x))
+        assert torch.equal(G1, G2) and torch.equal(ld1, ld2), groups
 
 
 @pytest.mark.parametrize("Lx,Ly,L,n_s,nf,precision", [(16, 16, 40, 8, 6, "fp64"), (10, 10, 30, 10, 5, "fp32"),
