@@ -40,7 +40,7 @@ UNIT = "evals/s"
 # 1.25 TFLOP/s), with the throughput probe of profiles/hw_probe_gb300.md reported beside
 # them (FP64 DFMA 1.01, FP32 FFMA 73.3, cuBLAS TF32 1062 TFLOP/s).
 NOMINAL = {"fp64_tflops": 1.25, "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "hbm_gbs": 6800.0}
-PROBED = {"fp64_tflops": 1.01, "fp32_tflops": 73.3, "tf32_tflops": 1062.0}
+PROBED = {"fp64_tflops": 1.01, "fp32_tflops": 73.3, "tf32_tflops": 1062.0, "bf16_tflops": 2056.0}
 
 
 def load_peaks():
@@ -296,6 +296,8 @@ def run_gpu(args):
             c.set_slice_groups(args.slice_groups)
         if args.sub_priorities >= 0:
             c.set_sub_batch_priorities(args.sub_priorities)
+        if args.qr_cluster:
+            c.set_qr_cluster(args.qr_cluster)
         return c
 
     def setup(ctx):
@@ -380,14 +382,24 @@ def run_gpu(args):
     lndets[args.precision] = ctx.logdet(xs)[0].cpu().numpy()
     ctx.close()
     fp64_value = None
+    tensor_modes = {}
     for extra in ([] if args.no_fp64 else ["tf32x3", "bf16x9"]):
         if extra == args.precision:
             continue
         ce = make(extra)
-        ms_e, _, _, _ = timed(ce, {"x": x0.clone()}, 1, 1, 0)
+        ms_e, _, prof_e, _ = timed(ce, {"x": x0.clone()}, 1, 1, 0, profile=True)
         rates[extra] = nf * world / (ms_e / 1e3)
         lndets[extra] = ce.logdet(xs)[0].cpu().numpy()
         ce.close()
+        # tensor-core slice products: dense work 2 N^3 per slice and field; the split products
+        # issue 3 (TF32) or 9 (BF16) MMAs per product, against that pipe's probed peak
+        busy = prof_e["slice"][2] / 1e3
+        dense = 2.0 * float(wl.N) ** 3 * wl.L * nf / max(busy, 1e-12) / 1e12
+        pieces, peak = (3, PROBED["tf32_tflops"]) if extra == "tf32x3" else (9, PROBED["bf16_tflops"])
+        tensor_modes[extra] = {"slice_busy_ms": prof_e["slice"][2], "dense_tflops": dense,
+                               "issued_tflops": dense * pieces, "tensor_peak_tflops": peak,
+                               "frac_of_tensor_peak": dense * pieces / peak,
+                               "peak_source": "probed tcgen05 rate of this pipe (profiles/hw_probe_gb300.md)"}
     if not args.no_fp64 and args.precision != "fp64":
         c64 = make("fp64")
         ms64, _, _, _ = timed(c64, {"x": x0.clone()}, 1, 1, 0)
@@ -442,6 +454,13 @@ def run_gpu(args):
             achieved = work * dom_units / busy_s / 1e9
             roof = dict(common, bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
                         frac=achieved / peaks["hbm_gbs"], traffic=traffic, peak_source=peaks["source"])
+    # E_eff sweeps: algorithmic bytes per half-sweep and chain = read the field, write the updated half
+    sweep_roof = None
+    if prof.get("sweep") and prof["sweep"][2] > 0:
+        sb = 12.0 * wl.N * wl.L * prof["sweep"][3] / (prof["sweep"][2] / 1e3) / 1e9
+        sweep_roof = {"bound": "hbm", "achieved": sb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                      "frac": sb / peaks["hbm_gbs"], "algorithmic_bytes_per_half_sweep_and_chain": 12 * wl.N * wl.L,
+                      "peak_source": peaks["source"]}
     total_prof = sum(v[2] for v in prof.values())
     shares = {k: round(v[2] / total_prof, 4) for k, v in prof.items() if v[2] > 0}
 
@@ -479,7 +498,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
             "fp64_value": fp64_value, "logdet_only_evals_per_s": rates, "accuracy_max_abs_dlndet": acc,
-            "fp64_step": fp64_step, "time_shares": shares, "mode": args.mode, "batched_uneven": batched}
+            "fp64_step": fp64_step, "sweep_roofline": sweep_roof, "tensor_modes": tensor_modes,
+            "time_shares": shares, "mode": args.mode, "batched_uneven": batched}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -551,6 +571,7 @@ def main():
     ap.add_argument("--sub-batches", type=int, default=0, help="forked streams per batch (0 = library default)")
     ap.add_argument("--slice-groups", type=int, default=0, help="FP32 slice kernel column groups (0 = default)")
     ap.add_argument("--sub-priorities", type=int, default=-1, help="descending sub-batch stream priorities (1/0)")
+    ap.add_argument("--qr-cluster", type=int, default=0, help="CTAs per field of the QR (0 = automatic, 1, 2, 4)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "slmc":
         args.warmup = 3
