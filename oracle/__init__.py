@@ -15,8 +15,9 @@ layout) the docstring states the reading taken.
 Parity pins (tests/test_oracle_*.py, run with ``-m "not gpu"``): closed forms at
 lambda=0, uniform and static staggered fields and t=0, brute-force LU of the NL x NL
 fermion matrix, particle-hole / translation / time-reversal invariances, the Z2 mirror
-of E_eff, exact Boltzmann sampling on tiny systems, exact regression recovery and the
-J_k = 1/(2 dtau^2) entry of Table S1. Parity is unpinned only for the physics values of
+of E_eff, exact Boltzmann sampling on tiny systems, exact regression recovery, the
+J_k = 1/(2 dtau^2) entry of Table S1, and exact detailed balance of the modified Wolff
+cluster move (enumeration of all bond-activation patterns on small lattices). Parity is unpinned only for the physics values of
 S(pi,pi) at the benchmark parameters (the paper prints none there).
 """
 from .params import HolsteinParams  # noqa: F401
