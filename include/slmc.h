@@ -143,6 +143,24 @@ SLMC_API int slmc_eff_features(slmc_ctx* ctx, const double* x, int n, double* F,
 SLMC_API int slmc_eff_log_weight(slmc_ctx* ctx, const double* x, int n, const double* J, double* lnw_eff,
                         void* stream);
 
+/* Modified Wolff cluster updates of the effective model [Sec. "Wolff update of the effective
+ * Hamiltonian", Eq. (S9)], inserted by slmc_eff_sweep and slmc_cumulative_update between the
+ * two colours of every sweep (nwolff per sweep, 0..64; default 0 = local sweeps only). Each
+ * update builds a cluster in the spatial plane out of whole temporal columns: bond term
+ * (i, j) of J_nn F_nn (each site's +x and +y bonds) is activated with probability
+ * max(0, 1 - exp(2 dtau J_nn sum_l x_il x_jl)) (uniform of Philox counter (b, ctr, chain, 2),
+ * b = 2 i for +x, 2 i + 1 for +y, ctr = (sweep counter) * nwolff + k), the seed site is drawn
+ * uniformly (counter (2N, ctr, chain, 2)), and the columns of the seed's connected component
+ * are reflected, x -> -x. The other terms of E_eff are invariant under reflecting whole columns,
+ * so the move needs no acceptance step. Placed between the colours, the Wolff updates keep the
+ * composite proposal of a cumulative update reversible (its reverse is the sequence with the
+ * other starting colour), so Eq. (6) stays exact. */
+SLMC_API int slmc_set_wolff(slmc_ctx* ctx, int nwolff);
+
+/* Total number of columns reflected by Wolff updates since the context was created or last
+ * reset (synchronises `stream`; reset != 0 clears the total). */
+SLMC_API int slmc_get_wolff_sites(slmc_ctx* ctx, long long* total, int reset, void* stream);
+
 /* Metropolis sweeps of the effective model on n independent chains, in place
  * [Sec. "SLMC": local updates are O(1) on the bosonic model]. One sweep visits the
  * checkerboard colours (ix + iy + l) mod 2 in the order first_colour, 1 - first_colour;
@@ -152,7 +170,9 @@ SLMC_API int slmc_eff_log_weight(slmc_ctx* ctx, const double* x, int n, const do
  * (else SLMC_ERR_UNSUPPORTED).
  *   x       [n][N][L] in/out
  *   J       [6] device couplings
- *   n_acc   [n] int64 in/out: accepted local moves are added (may be NULL) */
+ *   n_acc   [n] int64 in/out: accepted local moves are added (may be NULL)
+ * With slmc_set_wolff(ctx, k > 0), k Wolff cluster updates run between the two colours
+ * of every sweep. */
 SLMC_API int slmc_eff_sweep(slmc_ctx* ctx, double* x, int n, const double* J, int nsweeps, uint64_t sweep0,
                    int first_colour, long long* n_acc, void* stream);
 
@@ -272,7 +292,8 @@ SLMC_API int slmc_measure_cdw(slmc_ctx* ctx, const double* G, int n, double* S, 
 #define SLMC_PROF_ACCEPT 9    /* acceptance draws, accept/restore */
 #define SLMC_PROF_FIT 10      /* regression */
 #define SLMC_PROF_CDW 11      /* S(pi,pi) */
-#define SLMC_PROF_NCLASS 12
+#define SLMC_PROF_WOLFF 12    /* Wolff cluster updates of the effective model */
+#define SLMC_PROF_NCLASS 13
 
 /* Total number of CUDA kernels this context has enqueued since slmc_init (host counter,
  * no synchronisation). */

@@ -188,6 +188,8 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
     v.Sws = c->Sws + F0 * N * 32;
     v.err = c->err;
     v.dctr = c->dctr;
+    v.nwolff = c->nwolff;
+    v.wolff_sites = c->wolff_sites;
     v.tune_qr_panel = c->tune_qr_panel;
     v.tune_slice_cols = c->tune_slice_cols;
     v.tune_slice_groups = c->tune_slice_groups;
@@ -238,6 +240,7 @@ void free_ctx(slmc_ctx* c) {
     if (c->prof_base) cudaEventDestroy(c->prof_base);
     void* bufs[] = {c->E64, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
                     c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err, c->dctr,
+                    c->wolff_sites,
                     c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -323,6 +326,8 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     alloc(&c->err, sizeof(unsigned int));
     alloc(&c->dctr, sizeof(unsigned long long));
     if (ok && cudaMemset(c->dctr, 0, sizeof(unsigned long long)) != cudaSuccess) ok = false;
+    alloc(&c->wolff_sites, sizeof(unsigned long long));
+    if (ok && cudaMemset(c->wolff_sites, 0, sizeof(unsigned long long)) != cudaSuccess) ok = false;
     const bool tc = p->precision == SLMC_PREC_TF32X3 || p->precision == SLMC_PREC_BF16X9;
     if (tc) {
         size_t es = 0;
@@ -444,10 +449,15 @@ int slmc_eff_sweep(slmc_ctx* c, double* x, int n, const double* J, int nsweeps, 
         return SLMC_ERR_ARG;
     if (!checkerboard_ok(c)) return SLMC_ERR_UNSUPPORTED;
     cudaStream_t s = as_stream(stream);
+    c->cur_units = n;
     for (int sw = 0; sw < nsweeps && n > 0; ++sw)
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1)  // Wolff cluster updates between the two colours of the sweep
+                for (int k = 0; k < c->nwolff; ++k)
+                    SLMC_LAUNCH(SLMC_PROF_WOLFF, 1, s, slmc::eff_wolff(c, x, n, 0, J, sweep0 + sw, k, s));
             SLMC_LAUNCH(SLMC_PROF_SWEEP, 1, s,
                         slmc::eff_half_sweep(c, x, n, 0, J, sweep0 + sw, first_colour ^ h, nullptr, 0, n_acc, s));
+        }
     return SLMC_OK;
 }
 
@@ -497,10 +507,16 @@ int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int n
                 SLMC_CK(cudaMemcpyAsync(xo, xc, m * NL * sizeof(double), cudaMemcpyDeviceToDevice, sk));
                 SLMC_LAUNCH(SLMC_PROF_EFF, 1, sk, slmc::eff_features(c, xc, m, J, nullptr, 0, sc(1), sk));
                 for (int sw = 0; sw < nsweeps; ++sw)
-                    for (int h = 0; h < 2; ++h)
+                    for (int h = 0; h < 2; ++h) {
+                        if (h == 1)  // Wolff cluster updates between the two colours of the sweep
+                            for (int k = 0; k < c->nwolff; ++k)
+                                SLMC_LAUNCH(SLMC_PROF_WOLFF, 1, sk,
+                                            slmc::eff_wolff(c, xc, m, g0, J, (uint64_t)u * nsweeps + sw, k, sk,
+                                                            c->dctr, nsweeps));
                         SLMC_LAUNCH(SLMC_PROF_SWEEP, 1, sk,
                                     slmc::eff_half_sweep(c, xc, m, g0, J, (uint64_t)u * nsweeps + sw, 0, isc(1), h,
                                                          n_sweep_acc ? n_sweep_acc + g0 : nullptr, sk, c->dctr, nsweeps));
+                    }
                 SLMC_LAUNCH(SLMC_PROF_EFF, 1, sk, slmc::eff_features(c, xc, m, J, nullptr, 0, sc(2), sk));
                 SLMC_TRY(logdet_run(c, v, xc, m, sc(0), isc(0), s_cdw ? v->QR : nullptr, sk));
                 c->cur_units = m;
@@ -553,6 +569,23 @@ int slmc_set_tuning(slmc_ctx* c, int qr_panel, int slice_cols) {
 int slmc_set_slice_groups(slmc_ctx* c, int groups) {
     if (!c || groups < 0 || groups > 4 || groups == 3) return SLMC_ERR_ARG;
     c->tune_slice_groups = groups;
+    return SLMC_OK;
+}
+
+int slmc_set_wolff(slmc_ctx* c, int nwolff) {
+    if (!c || nwolff < 0 || nwolff > 64) return SLMC_ERR_ARG;
+    c->nwolff = nwolff;
+    return SLMC_OK;
+}
+
+int slmc_get_wolff_sites(slmc_ctx* c, long long* total, int reset, void* stream) {
+    if (!c || !total) return SLMC_ERR_ARG;
+    unsigned long long v = 0;
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess ||
+        cudaMemcpy(&v, c->wolff_sites, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SLMC_ERR_CUDA;
+    if (reset && cudaMemset(c->wolff_sites, 0, sizeof(v)) != cudaSuccess) return SLMC_ERR_CUDA;
+    *total = (long long)v;
     return SLMC_OK;
 }
 

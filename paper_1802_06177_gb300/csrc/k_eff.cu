@@ -182,6 +182,81 @@ __global__ void __launch_bounds__(kThreads) k_half_sweep(double* __restrict__ x,
     if (threadIdx.x == 0 && n_acc && s_cnt) atomicAdd(n_acc + f, (unsigned long long)s_cnt);
 }
 
+// Modified Wolff cluster update of E_eff [Sec. "Wolff update of the effective Hamiltonian",
+// Eq. (S9)], one CTA per chain. Bond term b = 2i, (i, i + x^), or 2i + 1, (i, i + y^), of J_nn F_nn
+// is activated with probability max(0, 1 - exp(t_b)), t_b = 2 dtau J_nn sum_l x_il x_jl: reflecting
+// the whole column of one endpoint multiplies the term's weight by exp(t_b). The sum runs over l
+// in order with products and sums rounded separately (as in the oracle, so both take the same
+// decisions); the uniform is that of Philox counter (b, ctr, chain, 2), the seed site that of
+// (2N, ctr, chain, 2), ctr = (sweep counter) * nwolff + k. The seed's connected component over
+// the activated bonds is found by label propagation in shared memory (marks only go from 0 to 1,
+// so at most N + 1 rounds) and its columns are reflected, x -> -x. Every other term of E_eff is
+// invariant under reflecting whole columns: the move is always accepted.
+__global__ void __launch_bounds__(256) k_wolff(double* __restrict__ x, int Lx, int Ly, int L,
+                                               const double* __restrict__ Jg, double dtau, uint32_t key0,
+                                               uint32_t key1, uint32_t sweep_arg,
+                                               const unsigned long long* __restrict__ dctr, int nsweeps, int nwolff,
+                                               int k, int chain0, unsigned long long* __restrict__ n_sites) {
+    extern __shared__ unsigned char wsm[];
+    const int N = Lx * Ly;
+    unsigned char* act = wsm;        // [2N] activated bond terms
+    unsigned char* in_c = wsm + 2 * N;  // [N] cluster marks
+    __shared__ int s_seed, s_cnt;
+    const int f = blockIdx.x, tid = threadIdx.x;
+    double* __restrict__ xf = x + (size_t)f * N * L;
+    const uint32_t sweep = dctr ? (uint32_t)((*dctr) * (unsigned long long)nsweeps + sweep_arg) : sweep_arg;
+    const uint32_t ctr = sweep * (uint32_t)nwolff + (uint32_t)k;
+    const uint32_t chain = (uint32_t)(chain0 + f);
+    const double cfac = __dmul_rn(__dmul_rn(2.0, dtau), Jg[4]);
+    for (int b = tid; b < 2 * N; b += blockDim.x) {
+        const int i = b >> 1, ix = i % Lx, iy = i / Lx;
+        const int j = (b & 1) ? ix + Lx * (iy + 1 == Ly ? 0 : iy + 1) : (ix + 1 == Lx ? 0 : ix + 1) + Lx * iy;
+        const double* xi = xf + (size_t)i * L;
+        const double* xj = xf + (size_t)j * L;
+        double sb = 0.0;
+        for (int l = 0; l < L; ++l) sb = __dadd_rn(sb, __dmul_rn(xi[l], xj[l]));
+        const double t = __dmul_rn(cfac, sb);
+        unsigned char a = 0;
+        if (t < 0.0) {
+            const slmc::u32x4 w = slmc::philox4x32_10(slmc::u32x4{(uint32_t)b, ctr, chain, 2u}, key0, key1);
+            a = slmc::uniform53(w.x, w.y) < __dadd_rn(1.0, -exp(t));
+        }
+        act[b] = a;
+    }
+    if (tid == 0) {
+        const slmc::u32x4 w = slmc::philox4x32_10(slmc::u32x4{(uint32_t)(2 * N), ctr, chain, 2u}, key0, key1);
+        const int s0 = (int)(slmc::uniform53(w.x, w.y) * (double)N);
+        s_seed = s0 < N - 1 ? s0 : N - 1;
+        s_cnt = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += blockDim.x) in_c[i] = (i == s_seed);
+    __syncthreads();
+    for (int round = 0; round <= N; ++round) {
+        int changed = 0;
+        for (int b = tid; b < 2 * N; b += blockDim.x) {
+            if (!act[b]) continue;
+            const int i = b >> 1, ix = i % Lx, iy = i / Lx;
+            const int j = (b & 1) ? ix + Lx * (iy + 1 == Ly ? 0 : iy + 1) : (ix + 1 == Lx ? 0 : ix + 1) + Lx * iy;
+            if (in_c[i] != in_c[j]) {
+                in_c[i] = 1;
+                in_c[j] = 1;
+                changed = 1;
+            }
+        }
+        if (!__syncthreads_or(changed)) break;
+    }
+    int cnt = 0;
+    for (int i = tid; i < N; i += blockDim.x) cnt += in_c[i];
+    for (size_t idx = tid; idx < (size_t)N * L; idx += blockDim.x)
+        if (in_c[idx / L]) xf[idx] = -xf[idx];
+    if (n_sites) {
+        atomicAdd(&s_cnt, cnt);
+        __syncthreads();
+        if (tid == 0) atomicAdd(n_sites, (unsigned long long)s_cnt);
+    }
+}
+
 __global__ void k_update_draws(int nf, int chain0, uint32_t u_off, const unsigned long long* __restrict__ dctr,
                                uint32_t key0, uint32_t key1, int* __restrict__ first, double* __restrict__ u) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -410,6 +485,14 @@ cudaError_t accept_update(slmc_ctx* c, int nf, double* x, const double* x_old, c
     const int NL = c->N * c->L;
     dim3 grid((NL + 255) / 256 < 64 ? (NL + 255) / 256 : 64, nf);
     k_restore<<<grid, 256, 0, s>>>(x, x_old, accepted, NL);
+    return cudaGetLastError();
+}
+
+cudaError_t eff_wolff(slmc_ctx* c, double* x, int nf, int chain0, const double* J, uint64_t sweep, int k,
+                      cudaStream_t s, const unsigned long long* dctr, int nsweeps) {
+    k_wolff<<<nf, 256, 3 * c->N, s>>>(x, c->p.Lx, c->p.Ly, c->L, J, c->p.dtau, (uint32_t)(c->p.seed & 0xffffffffu),
+                                      (uint32_t)(c->p.seed >> 32), (uint32_t)sweep, dctr, nsweeps, c->nwolff, k,
+                                      chain0, c->wolff_sites);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,8 @@ struct slmc_ctx {
     double* fitR;    // [64] Givens-QR state of the regression
     unsigned int* err;
     unsigned long long* dctr;  // device-side cumulative-update counter (Philox stream position)
+    int nwolff;                        // Wolff cluster updates between the half-sweeps of a sweep
+    unsigned long long* wolff_sites;   // device total of reflected columns
     int tune_qr_panel;          // 0: by N; else 16 or 32 (blocked QR panel width)
     int tune_slice_cols;
     int tune_slice_groups;
@@ -162,6 +164,8 @@ cudaError_t eff_features(slmc_ctx* c, const double* x, int nf, const double* J, 
 cudaError_t eff_half_sweep(slmc_ctx* c, double* x, int nf, int chain0, const double* J, uint64_t sweep,
                            int colour, const int* colour_per_chain, int colour_xor, long long* n_acc,
                            cudaStream_t s, const unsigned long long* dctr = nullptr, int nsweeps = 0);
+cudaError_t eff_wolff(slmc_ctx* c, double* x, int nf, int chain0, const double* J, uint64_t sweep, int k,
+                      cudaStream_t s, const unsigned long long* dctr = nullptr, int nsweeps = 0);
 cudaError_t update_draws(slmc_ctx* c, int nf, int chain0, uint64_t u_off, int* first_colour, double* u_acc,
                          cudaStream_t s);
 cudaError_t counter_op(slmc_ctx* c, uint64_t v, bool add, cudaStream_t s);

@@ -31,6 +31,24 @@ from .dist import fit_eff_distributed, sum_over_processes
 from .slmc import UPDATE_CONTINUE, Context
 
 
+def integrated_autocorrelation(series_per_chain, window=5.0):
+    """Integrated autocorrelation time of a [T][chains] time series: the normalised
+    autocorrelation is averaged over chains and summed up to the first lag M >= window * tau
+    (Sokal's self-consistent window)."""
+    a = np.asarray(series_per_chain, dtype=np.float64)
+    a = a - a.mean(axis=0, keepdims=True)
+    T = a.shape[0]
+    var = (a * a).mean()
+    if T < 4 or var == 0.0:
+        return float("nan")
+    tau = 0.5
+    for m in range(1, T // 2):
+        tau += float((a[:-m] * a[m:]).mean() / var)
+        if m >= window * tau:
+            break
+    return tau
+
+
 def binned_error(series, nbins=10):
     series = np.asarray(series, dtype=np.float64)
     nb = min(nbins, len(series))
@@ -41,11 +59,12 @@ def binned_error(series, nbins=10):
 
 
 def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision="fp32", dtau=0.1, lam=1.0,
-        omega0=1.0, sweep_delta=0.3, seed=0x1802061774, rounds=2, device="cuda", rank=0, world=1):
+        omega0=1.0, sweep_delta=0.3, seed=0x1802061774, rounds=2, device="cuda", rank=0, world=1, wolff=0):
     dev = torch.device(device)
     seed = seed + rank
     ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
                   sweep_delta=sweep_delta, seed=seed, max_fields=chains, device=dev)
+    ctx.set_wolff(wolff)  # Wolff cluster updates between the colours of every sweep
     N = Lx * Lx
     x = torch.from_numpy(inputs.gaussian_fields(chains, Lx, Lx, L, sigma=1.0, seed=seed)).to(dev)
     J = torch.tensor([0.0, omega0 ** 2 / 4 + 1.0 / (2 * dtau ** 2), 0.1, 0.0, 0.0, omega0 ** 2 / 2],
@@ -84,6 +103,7 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     # ---- production ----
+    ctx.wolff_sites(reset=True)
     n_acc = torch.zeros(chains, dtype=torch.int64, device=dev)
     n_sw = torch.zeros(chains, dtype=torch.int64, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -93,6 +113,8 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
     torch.cuda.synchronize()
     ctx.get_error()
     ms = e0.elapsed_time(e1)
+    tau = integrated_autocorrelation(obs.cpu().numpy()[updates // 5:])  # this process's chains
+    wsites = ctx.wolff_sites()
     S_sum = sum_over_processes(obs.sum(dim=1))  # [updates], summed over every process's chains
     acc = sum_over_processes(torch.stack([n_acc.sum(), n_sw.sum()]))
     therm = updates // 5
@@ -103,6 +125,8 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
         "training_rounds": history,
         "updates": updates, "sweeps_per_update": sweeps,
         "S_pipi_mean": float(series.mean()), "S_pipi_err": binned_error(series),
+        "S_pipi_tau_int_updates": tau, "wolff_per_sweep": wolff,
+        "wolff_mean_cluster": (wsites / (chains * updates * sweeps * wolff)) if wolff else None,
         "acceptance": float(acc[0].item()) / (chains * world * updates),
         "sweep_acceptance": float(acc[1].item()) / (chains * world * updates * sweeps * N * L),
         "production_seconds": ms / 1e3, "training_seconds": t_train,
@@ -123,6 +147,7 @@ def main():
     ap.add_argument("--sweeps", type=int, default=100)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--rounds", type=int, default=2)
+    ap.add_argument("--wolff", type=int, default=0, help="Wolff cluster updates per sweep")
     a = ap.parse_args()
     import os
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -133,7 +158,7 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     res = run(a.Lx, a.L, a.n_s, a.chains, a.train, a.updates, a.sweeps, a.precision, rounds=a.rounds,
-              device="cuda:%d" % local, rank=rank, world=world)
+              device="cuda:%d" % local, rank=rank, world=world, wolff=a.wolff)
     if rank == 0:
         print(json.dumps(res))
     if world > 1:

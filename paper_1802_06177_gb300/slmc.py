@@ -39,7 +39,7 @@ EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", 
            "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune",
            "slmc_fit_eff_state", "slmc_fit_eff_merge", "slmc_profile_read_detail",
            "slmc_set_sub_batches", "slmc_set_slice_groups",
-           "slmc_set_sub_batch_priorities", "slmc_set_qr_cluster")
+           "slmc_set_sub_batch_priorities", "slmc_set_qr_cluster", "slmc_set_wolff", "slmc_get_wolff_sites")
 
 UPDATE_CONTINUE = (1 << 64) - 1
 FIT_STATE_DOUBLES = 64
@@ -49,7 +49,8 @@ class TuneResult(ctypes.Structure):
     _fields_ = [("n_s", ctypes.c_int), ("qr_panel", ctypes.c_int), ("slice_cols", ctypes.c_int),
                 ("sec_per_eval", ctypes.c_double), ("max_abs_dlndet", ctypes.c_double), ("candidates", ctypes.c_int)]
 
-PROF_CLASSES = ("slice", "qr", "formq", "tupdate", "final", "greens", "sweep", "eff", "bose", "accept", "fit", "cdw")
+PROF_CLASSES = ("slice", "qr", "formq", "tupdate", "final", "greens", "sweep", "eff", "bose", "accept", "fit", "cdw",
+                "wolff")
 
 _lib = None
 
@@ -101,6 +102,8 @@ def load_library(path=LIB_PATH):
         "slmc_set_slice_groups": ([P, I], I),
         "slmc_set_sub_batch_priorities": ([P, I], I),
         "slmc_set_qr_cluster": ([P, I], I),
+        "slmc_set_wolff": ([P, I], I),
+        "slmc_get_wolff_sites": ([P, ctypes.POINTER(ctypes.c_longlong), I, V], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -308,6 +311,17 @@ class Context:
     def set_slice_groups(self, groups):
         """Thread layout of the FP32 slice kernel (0 = default, 1, 2 or 4)."""
         self._check("slmc_set_slice_groups", self.lib.slmc_set_slice_groups(self._ctx, groups))
+
+    def set_wolff(self, nwolff):
+        """Wolff cluster updates between the two colours of every sweep (0 = local sweeps only)."""
+        self._check("slmc_set_wolff", self.lib.slmc_set_wolff(self._ctx, nwolff))
+
+    def wolff_sites(self, reset=False):
+        """Columns reflected by Wolff updates so far (synchronises the current stream)."""
+        v = ctypes.c_longlong()
+        self._check("slmc_get_wolff_sites", self.lib.slmc_get_wolff_sites(self._ctx, ctypes.byref(v), 1 if reset else 0,
+                                                                          _stream(self.device)))
+        return v.value
 
     def set_qr_cluster(self, ctas):
         """CTAs per field of the QR and the formation of Q (0 = automatic, 1, 2 or 4)."""

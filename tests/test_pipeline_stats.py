@@ -1,0 +1,26 @@
+"""Host-side statistics of the SLMC pipeline: the integrated autocorrelation time estimator
+against the closed form of an AR(1) process, tau_int = (1 + rho) / (2 (1 - rho)), and the
+binned error of uncorrelated data against sigma / sqrt(T)."""
+import math
+
+import numpy as np
+
+from paper_1802_06177_gb300.pipeline import binned_error, integrated_autocorrelation
+
+
+def test_tau_int_of_ar1_process():
+    rng = np.random.default_rng(0)
+    for rho in (0.0, 0.5, 0.8):
+        T, C = 20000, 8
+        a = np.zeros((T, C))
+        e = rng.normal(size=(T, C))
+        for t in range(1, T):
+            a[t] = rho * a[t - 1] + e[t]
+        exact = (1 + rho) / (2 * (1 - rho))
+        assert abs(integrated_autocorrelation(a) - exact) < 0.08 * exact + 0.03
+
+
+def test_binned_error_of_white_noise():
+    rng = np.random.default_rng(1)
+    x = rng.normal(scale=2.0, size=40000)
+    assert abs(binned_error(x, nbins=20) / (2.0 / math.sqrt(len(x))) - 1.0) < 0.5
