@@ -126,6 +126,7 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
         "updates": updates, "sweeps_per_update": sweeps,
         "S_pipi_mean": float(series.mean()), "S_pipi_err": binned_error(series),
         "S_pipi_tau_int_updates": tau, "wolff_per_sweep": wolff,
+        "S_pipi_halves": [float(h.mean()) for h in np.array_split(series, 2)],  # drift check
         "wolff_mean_cluster": (wsites / (chains * updates * sweeps * wolff)) if wolff else None,
         "acceptance": float(acc[0].item()) / (chains * world * updates),
         "sweep_acceptance": float(acc[1].item()) / (chains * world * updates * sweeps * N * L),
@@ -148,6 +149,9 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--rounds", type=int, default=2)
     ap.add_argument("--wolff", type=int, default=0, help="Wolff cluster updates per sweep")
+    ap.add_argument("--lam", type=float, default=1.0, help="electron-phonon coupling g")
+    ap.add_argument("--omega0", type=float, default=1.0, help="phonon frequency")
+    ap.add_argument("--seed", type=int, default=0x1802061774)
     a = ap.parse_args()
     import os
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -158,7 +162,8 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     res = run(a.Lx, a.L, a.n_s, a.chains, a.train, a.updates, a.sweeps, a.precision, rounds=a.rounds,
-              device="cuda:%d" % local, rank=rank, world=world, wolff=a.wolff)
+              device="cuda:%d" % local, rank=rank, world=world, wolff=a.wolff, lam=a.lam, omega0=a.omega0,
+              seed=a.seed)
     if rank == 0:
         print(json.dumps(res))
     if world > 1:
