@@ -24,6 +24,7 @@
 // (distributed shared memory) and update their own trailing columns. One cluster barrier per
 // panel suffices: a CTA overwrites its panel buffer only C panels later, after every CTA has
 // passed the barriers in between (and so finished its copies). C = 1 is the one-CTA kernel.
+#include <algorithm>
 #include <cfloat>
 
 #include <cooperative_groups.h>
@@ -637,7 +638,10 @@ cudaError_t launch_formq_b(slmc_ctx* c, int nf, cudaStream_t s) {
     T* U;
     if constexpr (sizeof(T) == 4) U = c->U32;
     else U = c->U;
-    dim3 grid(nf, qr_cluster_size(c, nf));  // column blocks per field
+    // column blocks per field: at least the QR's cluster size, and enough for about two CTAs per SM
+    int cb = qr_cluster_size(c, nf);
+    if (c->num_sms > 0 && nf > 0) cb = std::max(cb, std::min(4, (2 * c->num_sms + nf - 1) / nf));
+    dim3 grid(nf, cb);
     k_formq_b<BP, T><<<grid, kThreads, smem, s>>>(c->QR, c->Sws, U, c->N);
     return cudaGetLastError();
 }
