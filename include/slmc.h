@@ -176,6 +176,26 @@ SLMC_API int slmc_get_wolff_sites(slmc_ctx* ctx, long long* total, int reset, vo
 SLMC_API int slmc_eff_sweep(slmc_ctx* ctx, double* x, int n, const double* J, int nsweeps, uint64_t sweep0,
                    int first_colour, long long* n_acc, void* stream);
 
+/* Conventional DQMC updates of n independent chains, in place [Supplemental Material,
+ * Eqs. (S3)-(S6), and the block update described after them]: the baseline the self-learning
+ * method is compared with. Each of nsweeps sweeps visits the slices l = 1..L and, at each, the
+ * sites i = 0..N-1: the field of B_l at site i proposes x + U[-sweep_delta, sweep_delta]
+ * (Philox counter (i L + l - 1, sweep, chain, 3), words 0-1; acceptance uniform words 2-3),
+ * accepted with probability min(1, R^2 exp(d ln w_bose)), R = 1 + (1 - G_ii(l)) Delta_ii,
+ * Delta_ii = exp(-dtau lambda d) - 1 (fast ratio of Eq. (S5); both spin species); accepted
+ * moves update G(l) by Sherman-Morrison (Eq. (S6)); G is carried to the next slice by
+ * G(l) = B_l G(l-1) B_l^-1 and recomputed from scratch (stabilised determinant path on the
+ * time-rotated field) at the start of every group of n_s slices. Then nblock block updates
+ * reflect the whole column of one site (x -> -x, the paper's X -> -X - 2g/Omega^2), site and
+ * acceptance uniform from Philox counter (k, sweep, chain, 4), accepted with the ratio of the
+ * full weights. Sweep s uses counter sweep0 + s.
+ *   x            [n][N][L] in/out
+ *   n_acc_local  [n] int64 in/out: accepted local moves are added (may be NULL)
+ *   n_acc_block  [n] int64 in/out: accepted block updates are added (may be NULL)
+ * Requires L >= 2 (else SLMC_ERR_UNSUPPORTED). */
+SLMC_API int slmc_dqmc_sweep(slmc_ctx* ctx, double* x, int n, int nsweeps, uint64_t sweep0, int nblock,
+                             long long* n_acc_local, long long* n_acc_block, void* stream);
+
 /* Prepares chain state for slmc_cumulative_update: lnw[n] = ln w(x) and, if s_cdw is not
  * NULL, s_cdw[n] = S(pi,pi) of each configuration. */
 SLMC_API int slmc_chain_init(slmc_ctx* ctx, const double* x, int n, double* lnw, double* s_cdw, void* stream);
@@ -293,7 +313,8 @@ SLMC_API int slmc_measure_cdw(slmc_ctx* ctx, const double* G, int n, double* S, 
 #define SLMC_PROF_FIT 10      /* regression */
 #define SLMC_PROF_CDW 11      /* S(pi,pi) */
 #define SLMC_PROF_WOLFF 12    /* Wolff cluster updates of the effective model */
-#define SLMC_PROF_NCLASS 13
+#define SLMC_PROF_DQMC 13     /* DQMC local updates (fast ratio, Sherman-Morrison, wrapping) */
+#define SLMC_PROF_NCLASS 14
 
 /* Total number of CUDA kernels this context has enqueued since slmc_init (host counter,
  * no synchronisation). */

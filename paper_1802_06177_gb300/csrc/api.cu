@@ -169,6 +169,7 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
     v.device = c->device;
     const size_t N = c->N, NN = N * N, F0 = (size_t)f0;
     v.E64 = c->E64;
+    v.Einv64 = c->Einv64;
     v.F32 = c->F32;
     v.lo_kidx = c->lo_kidx;
     v.lo_val = c->lo_val;
@@ -238,7 +239,7 @@ void free_ctx(slmc_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
     if (c->prof_base) cudaEventDestroy(c->prof_base);
-    void* bufs[] = {c->E64, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
+    void* bufs[] = {c->E64, c->Einv64, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
                     c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err, c->dctr,
                     c->wolff_sites,
                     c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
@@ -297,6 +298,7 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
         if (cudaMalloc(reinterpret_cast<void**>(ptr), bytes) != cudaSuccess) ok = false;
     };
     alloc(&c->E64, NN * sizeof(double));
+    alloc(&c->Einv64, NN * sizeof(double));
     alloc(&c->F32, NN * sizeof(float));
     if (p->precision == SLMC_PREC_FP32) {
         c->lo_S = std::min(slmc::kLoStencil, (int)N);
@@ -538,6 +540,48 @@ int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int n
     }));
     if (nupdates > 0) SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::counter_op(c, (uint64_t)nupdates, true, s));
     return SLMC_OK;
+}
+
+int slmc_dqmc_sweep(slmc_ctx* c, double* x, int n, int nsweeps, uint64_t sweep0, int nblock, long long* n_acc_local,
+                    long long* n_acc_block, void* stream) {
+    if (!c || n < 0 || nsweeps < 0 || nblock < 0 || (n > 0 && !x)) return SLMC_ERR_ARG;
+    if (c->L < 2) return SLMC_ERR_UNSUPPORTED;
+    const size_t NL = (size_t)c->N * c->L;
+    cudaStream_t s = as_stream(stream);
+    return for_batches(c, n, [&](int f0, int nf) {
+        double* xc = x + (size_t)f0 * NL;
+        for (int sw = 0; sw < nsweeps; ++sw) {
+            const uint64_t sweep = sweep0 + (uint64_t)sw;
+            // local updates: G recomputed at the start of every group of n_s slices, then carried
+            for (int g0 = 0; g0 < c->L; g0 += c->p.n_s) {
+                const int nsl = std::min(c->p.n_s, c->L - g0);
+                c->cur_units = nf;
+                SLMC_LAUNCH(SLMC_PROF_DQMC, 1, s, slmc::dqmc_rotate(c, xc, c->x_old, nf, g0, s));
+                SLMC_TRY(logdet_batch(c, c->x_old, nf, scal(c, 0), iscal(c, 0), c->QR, s));  // G(g0) -> QR
+                c->cur_units = nf;
+                SLMC_LAUNCH(SLMC_PROF_DQMC, 1, s,
+                            slmc::dqmc_slices(c, xc, c->QR, c->Y, nf, f0, g0, nsl, sweep,
+                                              n_acc_local ? n_acc_local + f0 : nullptr, s));
+            }
+            if (nblock == 0) continue;
+            // block updates: reflect one column, accept with the ratio of the full weights
+            SLMC_TRY(logdet_batch(c, xc, nf, scal(c, 0), iscal(c, 0), nullptr, s));
+            SLMC_LAUNCH(SLMC_PROF_BOSE, 1, s, slmc::bose_log_weight(c, xc, nf, scal(c, 0), scal(c, 5), s));
+            SLMC_CK(cudaMemsetAsync(scal(c, 1), 0, nf * sizeof(double), s));  // no effective-model terms
+            SLMC_CK(cudaMemsetAsync(scal(c, 2), 0, nf * sizeof(double), s));
+            for (int k = 0; k < nblock; ++k) {
+                SLMC_CK(cudaMemcpyAsync(c->x_old, xc, nf * NL * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                c->cur_units = nf;
+                SLMC_LAUNCH(SLMC_PROF_DQMC, 1, s, slmc::dqmc_block_propose(c, xc, nf, f0, sweep, k, scal(c, 4), s));
+                SLMC_TRY(logdet_batch(c, xc, nf, scal(c, 0), iscal(c, 0), nullptr, s));
+                SLMC_LAUNCH(SLMC_PROF_BOSE, 1, s, slmc::bose_log_weight(c, xc, nf, scal(c, 0), scal(c, 3), s));
+                SLMC_LAUNCH(SLMC_PROF_ACCEPT, 2, s,
+                            slmc::accept_update(c, nf, xc, c->x_old, scal(c, 3), scal(c, 1), scal(c, 2), scal(c, 4),
+                                                scal(c, 5), iscal(c, 2), n_acc_block ? n_acc_block + f0 : nullptr, s));
+            }
+        }
+        return SLMC_OK;
+    });
 }
 
 int slmc_set_update_counter(slmc_ctx* c, uint64_t value, void* stream) {

@@ -101,6 +101,8 @@ cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s) {
     const int N = c->N;
     const int NN = N * N;
     k_hopping_exp<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->p.Lx, c->p.Ly, c->p.dtau, c->p.t, c->p.mu);
+    if (c->Einv64)  // exp(+dtau K): the same plane-wave sum with -dtau
+        k_hopping_exp<<<(NN + 255) / 256, 256, 0, s>>>(c->Einv64, c->p.Lx, c->p.Ly, -c->p.dtau, c->p.t, c->p.mu);
     k_split_F<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->F32, c->Ftf, c->Fbf, N);
     if (c->lo_kidx) {
         int* sel = c->lo_kidx + (size_t)c->lo_S * N;

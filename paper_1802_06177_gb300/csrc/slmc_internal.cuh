@@ -21,6 +21,7 @@ struct slmc_ctx {
     int N, L, max_fields, device;
     // exp(-dtau K), built on the device from the plane-wave eigenbasis of K.
     double* E64;
+    double* Einv64;  // exp(+dtau K), for carrying G between slices in the DQMC updates
     float* F32;      // F = E - I rounded to FP32 (reduced-precision slices use Y + F Y)
     int* lo_kidx;    // FP32 modes: [S][N] column of the S-th stencil entry of row i, then sel[S]
     float* lo_val;   // [S] FP32 rounding residual of F on the S largest-|F| displacements
@@ -166,6 +167,11 @@ cudaError_t eff_half_sweep(slmc_ctx* c, double* x, int nf, int chain0, const dou
                            cudaStream_t s, const unsigned long long* dctr = nullptr, int nsweeps = 0);
 cudaError_t eff_wolff(slmc_ctx* c, double* x, int nf, int chain0, const double* J, uint64_t sweep, int k,
                       cudaStream_t s, const unsigned long long* dctr = nullptr, int nsweeps = 0);
+cudaError_t dqmc_rotate(slmc_ctx* c, const double* x, double* xr, int nf, int g0, cudaStream_t s);
+cudaError_t dqmc_slices(slmc_ctx* c, double* x, double* G, double* W, int nf, int chain0, int l0, int nsl,
+                        uint64_t sweep, long long* n_acc, cudaStream_t s);
+cudaError_t dqmc_block_propose(slmc_ctx* c, double* x, int nf, int chain0, uint64_t sweep, int k, double* u,
+                               cudaStream_t s);
 cudaError_t update_draws(slmc_ctx* c, int nf, int chain0, uint64_t u_off, int* first_colour, double* u_acc,
                          cudaStream_t s);
 cudaError_t counter_op(slmc_ctx* c, uint64_t v, bool add, cudaStream_t s);

@@ -39,7 +39,8 @@ EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", 
            "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune",
            "slmc_fit_eff_state", "slmc_fit_eff_merge", "slmc_profile_read_detail",
            "slmc_set_sub_batches", "slmc_set_slice_groups",
-           "slmc_set_sub_batch_priorities", "slmc_set_qr_cluster", "slmc_set_wolff", "slmc_get_wolff_sites")
+           "slmc_set_sub_batch_priorities", "slmc_set_qr_cluster", "slmc_set_wolff", "slmc_get_wolff_sites",
+           "slmc_dqmc_sweep")
 
 UPDATE_CONTINUE = (1 << 64) - 1
 FIT_STATE_DOUBLES = 64
@@ -50,7 +51,7 @@ class TuneResult(ctypes.Structure):
                 ("sec_per_eval", ctypes.c_double), ("max_abs_dlndet", ctypes.c_double), ("candidates", ctypes.c_int)]
 
 PROF_CLASSES = ("slice", "qr", "formq", "tupdate", "final", "greens", "sweep", "eff", "bose", "accept", "fit", "cdw",
-                "wolff")
+                "wolff", "dqmc")
 
 _lib = None
 
@@ -104,6 +105,7 @@ def load_library(path=LIB_PATH):
         "slmc_set_qr_cluster": ([P, I], I),
         "slmc_set_wolff": ([P, I], I),
         "slmc_get_wolff_sites": ([P, ctypes.POINTER(ctypes.c_longlong), I, V], I),
+        "slmc_dqmc_sweep": ([P, P, I, I, U64, I, P, P, V], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -224,6 +226,14 @@ class Context:
         self._check("slmc_eff_sweep", self.lib.slmc_eff_sweep(
             self._ctx, px, n, _ptr(J, torch.float64, "J", (6,)), nsweeps, sweep0, first_colour,
             _ptr(n_acc, torch.int64, "n_acc", (n,)), _stream(self.device)))
+        return x
+
+    def dqmc_sweep(self, x, nsweeps, sweep0=0, nblock=0, n_acc_local=None, n_acc_block=None):
+        """Conventional DQMC sweeps (local updates with fast ratios, then nblock block updates)."""
+        px, n = self._fields(x)
+        self._check("slmc_dqmc_sweep", self.lib.slmc_dqmc_sweep(
+            self._ctx, px, n, nsweeps, sweep0, nblock, _ptr(n_acc_local, torch.int64, "n_acc_local", (n,)),
+            _ptr(n_acc_block, torch.int64, "n_acc_block", (n,)), _stream(self.device)))
         return x
 
     def chain_init(self, x, want_cdw=True):
