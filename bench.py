@@ -485,8 +485,8 @@ def run_gpu(args):
     N3 = float(wl.N) ** 3
     w64 = ngroups * (4.0 / 3.0 + 1.0) * N3 + (4.0 / 3.0) * N3 * (ngroups if args.precision == "fp64" else 1) \
         + (2.0 / 3.0 + (2.0 if args.mode == "step" else 0.0)) * N3
-    if args.precision == "fp64":
-        w64 += 2.0 * N3 * wl.L
+    if args.precision == "fp64":  # slices through the separable exp(-dtau K): N^2 (Lx + Ly) FMAs each
+        w64 += 2.0 * float(wl.N) ** 2 * (2 * wl.Lx) * wl.L
     ach64 = w64 * nf * world / (ms_step / 1e3) / 1e12 / world
     fp64_step = {"flop_per_eval": w64, "achieved_per_gpu": ach64, "unit": "TFLOP/s",
                  "frac_of_nominal": ach64 / NOMINAL["fp64_tflops"], "frac_of_probed": ach64 / PROBED["fp64_tflops"]}

@@ -192,7 +192,7 @@ SLMC_API int slmc_eff_sweep(slmc_ctx* ctx, double* x, int n, const double* J, in
  *   x            [n][N][L] in/out
  *   n_acc_local  [n] int64 in/out: accepted local moves are added (may be NULL)
  *   n_acc_block  [n] int64 in/out: accepted block updates are added (may be NULL)
- * Requires L >= 2 (else SLMC_ERR_UNSUPPORTED). */
+ * Requires L >= 2 and Lx, Ly <= 32 (else SLMC_ERR_UNSUPPORTED). */
 SLMC_API int slmc_dqmc_sweep(slmc_ctx* ctx, double* x, int n, int nsweeps, uint64_t sweep0, int nblock,
                              long long* n_acc_local, long long* n_acc_block, void* stream);
 

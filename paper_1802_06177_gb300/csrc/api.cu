@@ -170,6 +170,8 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
     const size_t N = c->N, NN = N * N, F0 = (size_t)f0;
     v.E64 = c->E64;
     v.Einv64 = c->Einv64;
+    v.kron = c->kron;
+    v.dense_slices = c->dense_slices;
     v.F32 = c->F32;
     v.lo_kidx = c->lo_kidx;
     v.lo_val = c->lo_val;
@@ -239,7 +241,7 @@ void free_ctx(slmc_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
     if (c->prof_base) cudaEventDestroy(c->prof_base);
-    void* bufs[] = {c->E64, c->Einv64, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
+    void* bufs[] = {c->E64, c->Einv64, c->kron, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
                     c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err, c->dctr,
                     c->wolff_sites,
                     c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
@@ -299,6 +301,7 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     };
     alloc(&c->E64, NN * sizeof(double));
     alloc(&c->Einv64, NN * sizeof(double));
+    if (c->p.Lx <= slmc::kKronMaxLine && c->p.Ly <= slmc::kKronMaxLine) alloc(&c->kron, 4 * slmc::kKronTab * sizeof(double));
     alloc(&c->F32, NN * sizeof(float));
     if (p->precision == SLMC_PREC_FP32) {
         c->lo_S = std::min(slmc::kLoStencil, (int)N);
@@ -545,7 +548,7 @@ int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int n
 int slmc_dqmc_sweep(slmc_ctx* c, double* x, int n, int nsweeps, uint64_t sweep0, int nblock, long long* n_acc_local,
                     long long* n_acc_block, void* stream) {
     if (!c || n < 0 || nsweeps < 0 || nblock < 0 || (n > 0 && !x)) return SLMC_ERR_ARG;
-    if (c->L < 2) return SLMC_ERR_UNSUPPORTED;
+    if (!slmc::dqmc_ok(c)) return SLMC_ERR_UNSUPPORTED;
     const size_t NL = (size_t)c->N * c->L;
     cudaStream_t s = as_stream(stream);
     return for_batches(c, n, [&](int f0, int nf) {
@@ -560,7 +563,7 @@ int slmc_dqmc_sweep(slmc_ctx* c, double* x, int n, int nsweeps, uint64_t sweep0,
                 SLMC_TRY(logdet_batch(c, c->x_old, nf, scal(c, 0), iscal(c, 0), c->QR, s));  // G(g0) -> QR
                 c->cur_units = nf;
                 SLMC_LAUNCH(SLMC_PROF_DQMC, 1, s,
-                            slmc::dqmc_slices(c, xc, c->QR, c->Y, nf, f0, g0, nsl, sweep,
+                            slmc::dqmc_slices(c, xc, c->QR, nf, f0, g0, nsl, sweep,
                                               n_acc_local ? n_acc_local + f0 : nullptr, s));
             }
             if (nblock == 0) continue;

@@ -30,6 +30,21 @@ __global__ void k_hopping_exp(double* __restrict__ E, int Lx, int Ly, double dta
     E[idx] = acc / N;
 }
 
+// The one-dimensional factors of the plane-wave sum above: for a side of Ld sites,
+// e[d] = (1/Ld) sum_n cos(2 pi n d / Ld) exp(+-2 dtau t cos(2 pi n / Ld)); the sums over
+// x and y separate because the hopping along x and along y commute. Block q of tab holds
+// [E_x | E_x^-1 | E_y | E_y^-1][q], each written twice over.
+__global__ void k_kron_tables(double* __restrict__ tab, int Lx, int Ly, double dtau_t2) {
+    const int q = blockIdx.x, d = threadIdx.x;
+    const int Ld = q < 2 ? Lx : Ly;
+    const double a = (q & 1) ? -dtau_t2 : dtau_t2;
+    if (d >= Ld) return;
+    double acc = 0.0;
+    for (int n = 0; n < Ld; ++n) acc += cospi(2.0 * ((n * d) % Ld) / Ld) * exp(a * cospi(2.0 * n / Ld));
+    tab[q * slmc::kKronTab + d] = acc / Ld;
+    tab[q * slmc::kKronTab + d + Ld] = acc / Ld;
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float v) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
@@ -103,6 +118,7 @@ cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s) {
     k_hopping_exp<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->p.Lx, c->p.Ly, c->p.dtau, c->p.t, c->p.mu);
     if (c->Einv64)  // exp(+dtau K): the same plane-wave sum with -dtau
         k_hopping_exp<<<(NN + 255) / 256, 256, 0, s>>>(c->Einv64, c->p.Lx, c->p.Ly, -c->p.dtau, c->p.t, c->p.mu);
+    if (c->kron) k_kron_tables<<<4, kKronMaxLine, 0, s>>>(c->kron, c->p.Lx, c->p.Ly, 2.0 * c->p.dtau * c->p.t);
     k_split_F<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->F32, c->Ftf, c->Fbf, N);
     if (c->lo_kidx) {
         int* sel = c->lo_kidx + (size_t)c->lo_S * N;

@@ -3,14 +3,26 @@
 // with.
 //
 // Local updates: at time slice l the equal-time Green's function G(l) (row-major, one chain
-// per CTA, in global memory: one N x N matrix per chain stays L2-resident) decides the move
-// of x_{i,l-1} through the fast ratio R = 1 + (1 - G_ii) Delta_ii, Delta_ii =
-// exp(-dtau lam d) - 1 (Eq. (S5)); with both spin species the weight ratio is
+// per CTA) decides the move of x_{i,l-1} through the fast ratio R = 1 + (1 - G_ii) Delta_ii,
+// Delta_ii = exp(-dtau lam d) - 1 (Eq. (S5)); with both spin species the weight ratio is
 // R^2 exp(d ln w_bose). An accepted move updates G by Sherman-Morrison,
-// G -= (Delta_ii / R) G[:, i] (e_i - G[i, :]) (Eq. (S6)), a rank-1 update spread over the CTA.
-// Between slices G(l) = B_l G(l-1) B_l^-1 with B_l = diag(s) E (two N^3 products through a
-// per-chain scratch matrix); at the start of every group of n_s slices G is recomputed from
-// scratch by the stabilised determinant path on the time-rotated field.
+// G -= (Delta_ii / R) G[:, i] (e_i - G[i, :]) (Eq. (S6)). Between slices G(l) = B_l G(l-1) B_l^-1
+// with B_l = diag(s) exp(-dtau K); at the start of every group of n_s slices G is recomputed
+// from scratch by the stabilised determinant path on the time-rotated field.
+//
+// FP64 issue is the scarce resource on this GPU (about two FMAs per clock per SM), so the
+// kernel spends it only on the arithmetic the method needs:
+//  * exp(-dtau K) of the periodic square lattice factorises exactly into
+//    e^{dtau mu} (E_x kron E_y), E_x and E_y symmetric circulant (the hopping along x and
+//    along y commute); the mu factors of B_l and B_l^-1 cancel, and the wrap becomes four
+//    in-place circulant transforms along the lines of G: 2 N^2 (Lx + Ly) FMAs instead of
+//    the 2 N^3 of two dense products;
+//  * G stays in shared memory when it fits (N <= 160), else in global memory (L2-resident);
+//  * the proposal, Delta_ii, exp(d ln w_bose) and both uniforms of every site of a slice are
+//    computed in parallel before the slice's sites are visited; each thread then takes the
+//    site's decision itself (u < R^2 exp(d ln w_bose), the same test as
+//    ln(R^2) + d ln w_bose compared with ln u up to rounding), so a rejected move costs no
+//    barrier and an accepted one costs the N^2 FMAs of the rank-1 update and two barriers.
 // Sites of a slice are visited in order; the proposal x' = x + U[-Delta, Delta] and the
 // acceptance uniform come from Philox counter (i L + l - 1, sweep, chain, 3). The new field is
 // rounded step by step as in the oracle, so accepted moves leave identical fields.
@@ -19,6 +31,8 @@
 // full weights (computed by the determinant path); the site and the uniform come from Philox
 // counter (k, sweep, chain, 4).
 #include "slmc_internal.cuh"
+
+#include <algorithm>
 
 namespace {
 
@@ -35,84 +49,103 @@ __global__ void k_rotate(const double* __restrict__ x, double* __restrict__ xr, 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_dqmc_slices(double* __restrict__ x, double* __restrict__ Gall,
-                                                          double* __restrict__ Wall, const double* __restrict__ E,
-                                                          const double* __restrict__ Einv, int N, int L, int l0, int nsl,
-                                                          double dtau, double lam, double w02, double delta,
-                                                          uint32_t key0, uint32_t key1, uint32_t sweep, int chain0,
+template <int LMAX>
+__global__ void __launch_bounds__(kThreads) k_dqmc_slices(double* __restrict__ x, double* __restrict__ Gall, int Lx,
+                                                          int Ly, int L, int l0, int nsl, double dtau,
+                                                          const double* __restrict__ kron,
+                                                          double lam, double w02, double delta, uint32_t key0,
+                                                          uint32_t key1, uint32_t sweep, int chain0, int g_in_smem,
                                                           unsigned long long* __restrict__ n_acc) {
     extern __shared__ double dsm[];
-    double* s = dsm;          // [N] slice scales
-    double* col = dsm + N;    // [N] G[:, i]
-    double* row = dsm + 2 * N;  // [N] e_i - G[i, :]
-    __shared__ double s_coef;
-    __shared__ int s_acc[2];  // decision of site i in s_acc[i & 1]: thread 0 writes the next one while
-                              // others may still be reading this one
+    const int N = Lx * Ly;
     const int f = blockIdx.x, tid = threadIdx.x;
     const size_t NN = (size_t)N * N;
-    double* __restrict__ G = Gall + f * NN;
-    double* __restrict__ W = Wall + f * NN;
-    double* __restrict__ xf = x + (size_t)f * N * L;
+    double* G = g_in_smem ? dsm : Gall + f * NN;
+    double* p = g_in_smem ? dsm + NN : dsm;
+    double* s = p;                 // [N] slice scales exp(-dtau lam x_{i,l-1})
+    double* sinv = p + N;          // [N] 1 / s
+    double* xn = p + 2 * N;        // [N] proposed field
+    double* dl = p + 3 * N;        // [N] Delta_ii
+    double* eb = p + 4 * N;        // [N] exp(d ln w_bose)
+    double* ua = p + 5 * N;        // [N] acceptance uniform
+    double* ac = p + 6 * N;        // [N] -(Delta_ii / R) G[:, i]
+    double* rw = p + 7 * N;        // [N] e_i - G[i, :]
+    double* ex = p + 8 * N;        // [2 Lx] E_x
+    double* exi = ex + slmc::kKronTab;   // [2 Lx] E_x^-1
+    double* ey = exi + slmc::kKronTab;   // [2 Ly] E_y
+    double* eyi = ey + slmc::kKronTab;   // [2 Ly] E_y^-1
+    double* xf = x + (size_t)f * N * L;
     const uint32_t chain = (uint32_t)(chain0 + f);
+
+    for (int k = tid; k < 4 * slmc::kKronTab; k += kThreads) ex[k] = kron[k];  // ex, exi, ey, eyi are contiguous
+    if (g_in_smem) {
+        const double2* src = reinterpret_cast<const double2*>(Gall + f * NN);
+        double2* dst = reinterpret_cast<double2*>(G);
+        for (size_t k = tid; k < NN / 2; k += kThreads) dst[k] = src[k];
+        if ((NN & 1) && tid == 0) G[NN - 1] = Gall[f * NN + NN - 1];
+    }
     int accepted = 0;
     for (int l = l0 + 1; l <= l0 + nsl; ++l) {
         const int c = l - 1;
-        for (int i = tid; i < N; i += kThreads) s[i] = exp(-dtau * lam * xf[(size_t)i * L + c]);
-        // wrap: W = G Einv, G = diag(s) E W diag(1/s)
-        for (size_t idx = tid; idx < NN; idx += kThreads) {
-            const int i = (int)(idx / N), j = (int)(idx - (size_t)i * N);
-            const double* gi = G + (size_t)i * N;
-            double acc = 0.0;
-            for (int m = 0; m < N; ++m) acc = fma(gi[m], Einv[(size_t)m * N + j], acc);
-            W[idx] = acc;
+        const int cu = c + 1 == L ? 0 : c + 1, cd = c == 0 ? L - 1 : c - 1;
+        for (int i = tid; i < N; i += kThreads) {
+            const double v = xf[(size_t)i * L + c];
+            const slmc::u32x4 w = slmc::philox4x32_10(slmc::u32x4{(uint32_t)(i * L + c), sweep, chain, 3u}, key0, key1);
+            const double u1 = slmc::uniform53(w.x, w.y);
+            const double xp = __dadd_rn(v, __dmul_rn(delta, __dadd_rn(__dmul_rn(2.0, u1), -1.0)));
+            const double up = xf[(size_t)i * L + cu], dn = xf[(size_t)i * L + cd];
+            const double kin = ((up - xp) * (up - xp) + (xp - dn) * (xp - dn) - (up - v) * (up - v) -
+                                (v - dn) * (v - dn)) / (2.0 * dtau * dtau);
+            const double dlb = dtau * lam * (xp - v) - dtau * (0.5 * w02 * (xp * xp - v * v) + kin);
+            s[i] = exp(-dtau * lam * v);
+            sinv[i] = exp(dtau * lam * v);
+            xn[i] = xp;
+            dl[i] = exp(-dtau * lam * (xp - v)) - 1.0;
+            eb[i] = exp(dlb);
+            ua[i] = slmc::uniform53(w.z, w.w);
         }
         __syncthreads();
-        for (size_t idx = tid; idx < NN; idx += kThreads) {
-            const int i = (int)(idx / N), j = (int)(idx - (size_t)i * N);
-            const double* ei = E + (size_t)i * N;
-            double acc = 0.0;
-            for (int k = 0; k < N; ++k) acc = fma(ei[k], W[(size_t)k * N + j], acc);
-            G[idx] = s[i] * acc / s[j];
+        // wrap: G <- diag(s) (E_x kron E_y) G (E_x kron E_y)^-1 diag(1/s), site i = ix + Lx iy
+        for (int q = tid; q < N * Lx; q += kThreads)  // right factor along y: lines (i, jx)
+            slmc::circ_line<LMAX, false>(G, (q / Lx) * N + q % Lx, Lx, Ly, eyi, nullptr, 0, nullptr, 0, 1.0);
+        __syncthreads();
+        for (int q = tid; q < N * Ly; q += kThreads)  // right factor along x: lines (i, jy)
+            slmc::circ_line<LMAX, false>(G, (q / Ly) * N + (q % Ly) * Lx, 1, Lx, exi, nullptr, 0, nullptr, 0, 1.0);
+        __syncthreads();
+        for (int q = tid; q < Ly * N; q += kThreads)  // left factor along x: lines (iy, j)
+            slmc::circ_line<LMAX, true>(G, (q / N) * Lx * N + q % N, N, Lx, ex, nullptr, 0, nullptr, 0, 1.0);
+        __syncthreads();
+        for (int q = tid; q < Lx * N; q += kThreads) {  // left factor along y, then the scales
+            const int ix = q / N, j = q % N;
+            slmc::circ_line<LMAX, true>(G, ix * N + j, Lx * N, Ly, ey, nullptr, 0, s + ix, Lx, sinv[j]);  // row ix + Lx d
         }
         __syncthreads();
         for (int i = 0; i < N; ++i) {
+            // every thread takes the same decision from the same G_ii
+            const double R = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -G[(size_t)i * N + i]), dl[i]));
+            if (!(ua[i] < R * R * eb[i])) continue;
+            const double a = dl[i] * __drcp_rn(R);
+            for (int j = tid; j < N; j += kThreads) {
+                ac[j] = -a * G[(size_t)j * N + i];
+                rw[j] = (j == i ? 1.0 : 0.0) - G[(size_t)i * N + j];
+            }
             if (tid == 0) {
-                const slmc::u32x4 w =
-                    slmc::philox4x32_10(slmc::u32x4{(uint32_t)(i * L + c), sweep, chain, 3u}, key0, key1);
-                const double u1 = slmc::uniform53(w.x, w.y), u2 = slmc::uniform53(w.z, w.w);
-                const double v = xf[(size_t)i * L + c];
-                const double xn = __dadd_rn(v, __dmul_rn(delta, __dadd_rn(__dmul_rn(2.0, u1), -1.0)));
-                const double dl = exp(-dtau * lam * (xn - v)) - 1.0;
-                const double R = 1.0 + (1.0 - G[(size_t)i * N + i]) * dl;
-                const double up = xf[(size_t)i * L + (c + 1 == L ? 0 : c + 1)];
-                const double dn = xf[(size_t)i * L + (c == 0 ? L - 1 : c - 1)];
-                const double kin = ((up - xn) * (up - xn) + (xn - dn) * (xn - dn) - (up - v) * (up - v) -
-                                    (v - dn) * (v - dn)) / (2.0 * dtau * dtau);
-                const double dlb = dtau * lam * (xn - v) - dtau * (0.5 * w02 * (xn * xn - v * v) + kin);
-                const double lnr = log(R * R) + dlb;
-                const int acc = (lnr >= 0.0 || u2 < exp(lnr)) ? 1 : 0;
-                if (acc) {
-                    xf[(size_t)i * L + c] = xn;
-                    s_coef = dl / R;
-                    ++accepted;
-                }
-                s_acc[i & 1] = acc;
+                xf[(size_t)i * L + c] = xn[i];
+                ++accepted;
             }
             __syncthreads();
-            if (s_acc[i & 1]) {  // Sherman-Morrison (block-uniform branch)
-                for (int j = tid; j < N; j += kThreads) {
-                    col[j] = G[(size_t)j * N + i];
-                    row[j] = (j == i ? 1.0 : 0.0) - G[(size_t)i * N + j];
+            int j = tid / N, k = tid - (tid / N) * N;
+            for (size_t idx = tid; idx < NN; idx += kThreads) {
+                G[idx] = fma(ac[j], rw[k], G[idx]);
+                k += kThreads;
+                while (k >= N) {
+                    k -= N;
+                    ++j;
                 }
-                __syncthreads();
-                const double a = s_coef;
-                for (size_t idx = tid; idx < NN; idx += kThreads) {
-                    const int j = (int)(idx / N), k = (int)(idx - (size_t)j * N);
-                    G[idx] = fma(-a * col[j], row[k], G[idx]);
-                }
-                __syncthreads();
             }
+            __syncthreads();
         }
+        __syncthreads();  // rejected sites take no barrier: the next slice's tables wait for all threads here
     }
     if (tid == 0 && n_acc) n_acc[f] += (unsigned long long)accepted;
 }
@@ -130,6 +163,30 @@ __global__ void k_block_propose(double* __restrict__ x, int N, int L, uint32_t k
     if (threadIdx.x == 0) u[f] = slmc::uniform53(w.z, w.w);
 }
 
+size_t dqmc_smem_bytes(int N, bool g_in_smem) {
+    return ((g_in_smem ? (size_t)N * N : 0) + 8 * (size_t)N + 4 * slmc::kKronTab) * sizeof(double);
+}
+
+bool dqmc_supported(const slmc_ctx* c) { return c->L >= 2 && c->kron != nullptr; }
+
+template <int LMAX>
+cudaError_t launch_slices(slmc_ctx* c, double* x, double* G, int nf, int chain0, int l0, int nsl, uint64_t sweep,
+                          long long* n_acc, cudaStream_t s) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const bool in_smem = dqmc_smem_bytes(c->N, true) <= (size_t)optin;
+    const size_t bytes = dqmc_smem_bytes(c->N, in_smem);
+    e = cudaFuncSetAttribute(k_dqmc_slices<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_dqmc_slices<LMAX><<<nf, kThreads, bytes, s>>>(
+        x, G, c->p.Lx, c->p.Ly, c->L, l0, nsl, c->p.dtau, c->kron, c->p.lambda, c->p.omega0 * c->p.omega0,
+        c->p.sweep_delta, (uint32_t)(c->p.seed & 0xffffffffu), (uint32_t)(c->p.seed >> 32), (uint32_t)sweep, chain0,
+        in_smem ? 1 : 0, reinterpret_cast<unsigned long long*>(n_acc));
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 namespace slmc {
@@ -141,13 +198,14 @@ cudaError_t dqmc_rotate(slmc_ctx* c, const double* x, double* xr, int nf, int g0
     return cudaGetLastError();
 }
 
-cudaError_t dqmc_slices(slmc_ctx* c, double* x, double* G, double* W, int nf, int chain0, int l0, int nsl,
-                        uint64_t sweep, long long* n_acc, cudaStream_t s) {
-    k_dqmc_slices<<<nf, kThreads, 3 * c->N * sizeof(double), s>>>(
-        x, G, W, c->E64, c->Einv64, c->N, c->L, l0, nsl, c->p.dtau, c->p.lambda, c->p.omega0 * c->p.omega0,
-        c->p.sweep_delta, (uint32_t)(c->p.seed & 0xffffffffu), (uint32_t)(c->p.seed >> 32), (uint32_t)sweep, chain0,
-        reinterpret_cast<unsigned long long*>(n_acc));
-    return cudaGetLastError();
+bool dqmc_ok(const slmc_ctx* c) { return dqmc_supported(c); }
+
+cudaError_t dqmc_slices(slmc_ctx* c, double* x, double* G, int nf, int chain0, int l0, int nsl, uint64_t sweep,
+                        long long* n_acc, cudaStream_t s) {
+    const int lm = std::max(c->p.Lx, c->p.Ly);
+    if (lm <= 8) return launch_slices<8>(c, x, G, nf, chain0, l0, nsl, sweep, n_acc, s);
+    if (lm <= 16) return launch_slices<16>(c, x, G, nf, chain0, l0, nsl, sweep, n_acc, s);
+    return launch_slices<32>(c, x, G, nf, chain0, l0, nsl, sweep, n_acc, s);
 }
 
 cudaError_t dqmc_block_propose(slmc_ctx* c, double* x, int nf, int chain0, uint64_t sweep, int k, double* u,

@@ -380,6 +380,7 @@ cudaError_t slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, c
         if (rpt == 3) return launch_slice_f32<3, 8>(c, x, nf, l0, nsl, s);
         return launch_slice_f32<4, 4>(c, x, nf, l0, nsl, s);
     }
+    if (c->kron && !c->dense_slices) return slice_group_kron(c, x, nf, l0, nsl, false, s);
     return dispatch_panel<double, false>(c->E64, 0, c->U, nullptr, c->Y, x, c->N, c->L, l0, nsl, dtlam, 0, nf, s);
 }
 

@@ -16,12 +16,22 @@
 
 #define SLMC_MAX_N 1024
 
+namespace slmc {
+constexpr int kKronMaxLine = 32;             // longest lattice side of the circulant factors
+constexpr int kKronTab = 2 * kKronMaxLine;   // doubles per stored factor
+}  // namespace slmc
+
 struct slmc_ctx {
     slmc_params p;
     int N, L, max_fields, device;
     // exp(-dtau K), built on the device from the plane-wave eigenbasis of K.
     double* E64;
     double* Einv64;  // exp(+dtau K), for carrying G between slices in the DQMC updates
+    // One-dimensional circulant factors of exp(-+dtau K) = e^{-+dtau mu} E_x kron E_y (site
+    // i = ix + Lx iy), each stored twice over: [E_x | E_x^-1 | E_y | E_y^-1], kKronTab
+    // doubles apiece. Null when a lattice side exceeds kKronMaxLine (dense products then).
+    double* kron;
+    int dense_slices;  // 1: FP64 slice products by the dense exp(-dtau K) even where kron exists
     float* F32;      // F = E - I rounded to FP32 (reduced-precision slices use Y + F Y)
     int* lo_kidx;    // FP32 modes: [S][N] column of the S-th stencil entry of row i, then sel[S]
     float* lo_val;   // [S] FP32 rounding residual of F on the S largest-|F| displacements
@@ -58,7 +68,7 @@ struct slmc_ctx {
     int tune_slice_cols;
     int tune_slice_groups;
     int tune_qr_cluster;    // CTAs per field of the QR / formation of Q (0 = by field count)
-    int num_sms;            // multiprocessors of the device  // FP32 slice kernel column groups per CTA (0 = default 1, or 2)        // 0: by N; else 8 or 16 (FP32 slice columns per thread)
+    int num_sms;            // multiprocessors of the device
     // Tensor-core slice path (SLMC_PREC_TF32X3 / BF16X9): operand pieces of F and of the
     // running slice product (ping/pong), FP32 copies of it, and their TMA descriptors.
     int tc_npad, tc_nt;
@@ -112,6 +122,30 @@ inline int rows_per_lane_class(int N) {
 }
 
 // ---- Philox-4x32-10 (Salmon et al., SC'11), written from the published definition ----
+// One in-place circulant line transform of a strided vector v[m] = g[base + m stride],
+// m < Ld: out[d] = sum_m tab[(d - m) mod Ld] v[m] (kLeft: a circulant applied from the left)
+// or sum_m v[m] tab[(m - d) mod Ld] (from the right), with optional input scales
+// in_sc[m in_st] and output scales out_sc[d out_st] * out_mul. tab holds the factor twice
+// over so that the index needs no modulo. The outputs stay in registers until the whole line
+// has been read.
+template <int LMAX, bool kLeft>
+__device__ __forceinline__ void circ_line(double* g, int base, int stride, int Ld, const double* __restrict__ tab,
+                                          const double* in_sc, int in_st, const double* out_sc, int out_st,
+                                          double out_mul) {
+    double acc[LMAX];
+#pragma unroll
+    for (int d = 0; d < LMAX; ++d) acc[d] = 0.0;
+    for (int m = 0; m < Ld; ++m) {
+        const double v = in_sc ? g[base + m * stride] * in_sc[m * in_st] : g[base + m * stride];
+#pragma unroll
+        for (int d = 0; d < LMAX; ++d)
+            if (d < Ld) acc[d] = fma(v, tab[kLeft ? d - m + Ld : m - d + Ld], acc[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < LMAX; ++d)
+        if (d < Ld) g[base + d * stride] = out_sc ? acc[d] * (out_sc[d * out_st] * out_mul) : acc[d];
+}
+
 struct u32x4 { uint32_t x, y, z, w; };
 
 __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
@@ -167,9 +201,11 @@ cudaError_t eff_half_sweep(slmc_ctx* c, double* x, int nf, int chain0, const dou
                            cudaStream_t s, const unsigned long long* dctr = nullptr, int nsweeps = 0);
 cudaError_t eff_wolff(slmc_ctx* c, double* x, int nf, int chain0, const double* J, uint64_t sweep, int k,
                       cudaStream_t s, const unsigned long long* dctr = nullptr, int nsweeps = 0);
+cudaError_t slice_group_kron(slmc_ctx* c, const double* x, int nf, int l0, int nsl, bool transposed, cudaStream_t s);
 cudaError_t dqmc_rotate(slmc_ctx* c, const double* x, double* xr, int nf, int g0, cudaStream_t s);
-cudaError_t dqmc_slices(slmc_ctx* c, double* x, double* G, double* W, int nf, int chain0, int l0, int nsl,
-                        uint64_t sweep, long long* n_acc, cudaStream_t s);
+bool dqmc_ok(const slmc_ctx* c);  // L >= 2 and both lattice sides <= 32
+cudaError_t dqmc_slices(slmc_ctx* c, double* x, double* G, int nf, int chain0, int l0, int nsl, uint64_t sweep,
+                        long long* n_acc, cudaStream_t s);
 cudaError_t dqmc_block_propose(slmc_ctx* c, double* x, int nf, int chain0, uint64_t sweep, int k, double* u,
                                cudaStream_t s);
 cudaError_t update_draws(slmc_ctx* c, int nf, int chain0, uint64_t u_off, int* first_colour, double* u_acc,

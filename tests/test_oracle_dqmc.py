@@ -69,3 +69,21 @@ def test_block_update_reflects_whole_columns():
     n = block_updates(p, x, 6, 3, 0, 77, E)
     changed = np.any(x != x0, axis=1)
     assert np.all(x[changed] == -x0[changed]) and changed.sum() <= n
+
+
+@pytest.mark.parametrize("Lx,Ly,mu", [(4, 3, 0.3), (2, 5, 0.0), (6, 6, -0.2), (1, 4, 0.1)])
+def test_hopping_exponential_factorises_into_circulants(Lx, Ly, mu):
+    """exp(-dtau K) = e^{dtau mu} E_x kron E_y with E_x, E_y circulant one-dimensional factors (the
+    x and y hoppings commute); the GPU wrap relies on it, and the mu factors of B and B^-1 cancel."""
+    dtau, t = 0.1, 1.0
+
+    def circ(Ld, a):
+        k = 2.0 * np.pi * np.arange(Ld) / Ld
+        d = np.subtract.outer(np.arange(Ld), np.arange(Ld)) % Ld
+        return np.real(np.fft.ifft(np.exp(a * np.cos(k))))[d]
+
+    E = exp_hopping(Lx, Ly, t, mu, dtau)
+    # site i = ix + Lx iy: the y factor is the outer one of the Kronecker product
+    assert np.abs(E - math.exp(dtau * mu) * np.kron(circ(Ly, 2 * dtau * t), circ(Lx, 2 * dtau * t))).max() < 1e-14
+    Ei = exp_hopping(Lx, Ly, t, mu, -dtau)
+    assert np.abs(Ei - math.exp(-dtau * mu) * np.kron(circ(Ly, -2 * dtau * t), circ(Lx, -2 * dtau * t))).max() < 1e-14
