@@ -184,15 +184,20 @@ SLMC_API int slmc_eff_sweep(slmc_ctx* ctx, double* x, int n, const double* J, in
  * accepted with probability min(1, R^2 exp(d ln w_bose)), R = 1 + (1 - G_ii(l)) Delta_ii,
  * Delta_ii = exp(-dtau lambda d) - 1 (fast ratio of Eq. (S5); both spin species); accepted
  * moves update G(l) by Sherman-Morrison (Eq. (S6)); G is carried to the next slice by
- * G(l) = B_l G(l-1) B_l^-1 and recomputed from scratch (stabilised determinant path on the
- * time-rotated field) at the start of every group of n_s slices. Then nblock block updates
+ * G(l) = B_l G(l-1) B_l^-1 and recomputed at the start of every group of n_s slices.
+ * Then nblock block updates
  * reflect the whole column of one site (x -> -x, the paper's X -> -X - 2g/Omega^2), site and
  * acceptance uniform from Philox counter (k, sweep, chain, 4), accepted with the ratio of the
  * full weights. Sweep s uses counter sweep0 + s.
  *   x            [n][N][L] in/out
  *   n_acc_local  [n] int64 in/out: accepted local moves are added (may be NULL)
  *   n_acc_block  [n] int64 in/out: accepted block updates are added (may be NULL)
- * Requires L >= 2 and Lx, Ly <= 32 (else SLMC_ERR_UNSUPPORTED). */
+ * G(g0) comes from two stabilised FP64 products (whatever the context's precision): the
+ * transposed products B(L, g0)^T of the slices still to come, built at the start of each
+ * sweep and kept on a stack of ceil(L / n_s) x max_fields x (2 N^2 + N) doubles allocated on
+ * the first call, and the running product B(g0, 0) of the slices already updated.
+ * Requires L >= 2 and Lx, Ly <= 32 (else SLMC_ERR_UNSUPPORTED); SLMC_ERR_NOMEM if the stack
+ * cannot be allocated. */
 SLMC_API int slmc_dqmc_sweep(slmc_ctx* ctx, double* x, int n, int nsweeps, uint64_t sweep0, int nblock,
                              long long* n_acc_local, long long* n_acc_block, void* stream);
 

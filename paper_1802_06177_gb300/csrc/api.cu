@@ -243,7 +243,7 @@ void free_ctx(slmc_ctx* c) {
     if (c->prof_base) cudaEventDestroy(c->prof_base);
     void* bufs[] = {c->E64, c->Einv64, c->kron, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
                     c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err, c->dctr,
-                    c->wolff_sites,
+                    c->wolff_sites, c->dq_stack,
                     c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -545,26 +545,80 @@ int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int n
     return SLMC_OK;
 }
 
+namespace {
+// One FP64 step of the stabilised chain on the product already in Y: pivoted QR, Q, T.
+int chain_step64(slmc_ctx* c, int nf, cudaStream_t s) {
+    c->cur_units = nf;
+    if (c->p.qr_mode == SLMC_QR_PIVOTED) {
+        SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_pivoted(c, nf, s));
+        SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q(c, nf, s));
+    } else {
+        SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_blocked(c, nf, s));
+        SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q_blocked(c, nf, false, s));
+    }
+    SLMC_LAUNCH(SLMC_PROF_TUPDATE, 1, s, slmc::t_update_tiled(c, nf, s));
+    return SLMC_OK;
+}
+
+// chain state (U, T, lnD) of fields [0, nf) into stack slot k
+int stack_store(slmc_ctx* c, int k, int nf, cudaStream_t s) {
+    const size_t NN = (size_t)c->N * c->N, F = c->max_fields;
+    double* slot = c->dq_stack + (size_t)k * F * (2 * NN + c->N);
+    SLMC_CK(cudaMemcpyAsync(slot, c->U, nf * NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SLMC_CK(cudaMemcpyAsync(slot + F * NN, c->Ta, nf * NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SLMC_CK(cudaMemcpyAsync(slot + 2 * F * NN, c->lnD, nf * c->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return SLMC_OK;
+}
+}  // namespace
+
 int slmc_dqmc_sweep(slmc_ctx* c, double* x, int n, int nsweeps, uint64_t sweep0, int nblock, long long* n_acc_local,
                     long long* n_acc_block, void* stream) {
     if (!c || n < 0 || nsweeps < 0 || nblock < 0 || (n > 0 && !x)) return SLMC_ERR_ARG;
     if (!slmc::dqmc_ok(c)) return SLMC_ERR_UNSUPPORTED;
+    const int ngroups = (c->L + c->p.n_s - 1) / c->p.n_s;
+    if (!c->dq_stack) {  // the left-product stack, allocated on first use
+        const size_t NN = (size_t)c->N * c->N;
+        const size_t bytes = (size_t)ngroups * c->max_fields * (2 * NN + c->N) * sizeof(double);
+        if (cudaMalloc(reinterpret_cast<void**>(&c->dq_stack), bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->dq_stack = nullptr;
+            return SLMC_ERR_NOMEM;
+        }
+        c->dq_groups = ngroups;
+    }
     const size_t NL = (size_t)c->N * c->L;
     cudaStream_t s = as_stream(stream);
     return for_batches(c, n, [&](int f0, int nf) {
         double* xc = x + (size_t)f0 * NL;
         for (int sw = 0; sw < nsweeps; ++sw) {
             const uint64_t sweep = sweep0 + (uint64_t)sw;
-            // local updates: G recomputed at the start of every group of n_s slices, then carried
-            for (int g0 = 0; g0 < c->L; g0 += c->p.n_s) {
-                const int nsl = std::min(c->p.n_s, c->L - g0);
-                c->cur_units = nf;
-                SLMC_LAUNCH(SLMC_PROF_DQMC, 1, s, slmc::dqmc_rotate(c, xc, c->x_old, nf, g0, s));
-                SLMC_TRY(logdet_batch(c, c->x_old, nf, scal(c, 0), iscal(c, 0), c->QR, s));  // G(g0) -> QR
-                c->cur_units = nf;
+            // transposed left products B(L, g0)^T, g0 = k n_s, from the top group down
+            const int ng = (c->L + c->p.n_s - 1) / c->p.n_s;
+            c->cur_units = nf;
+            SLMC_LAUNCH(SLMC_PROF_FINAL, 1, s, slmc::set_identity(c, nf, s));
+            for (int k = ng - 1; k >= 0; --k) {
+                const int l0 = k * c->p.n_s, nsl = std::min(c->p.n_s, c->L - l0);
+                SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_group_kron(c, xc, nf, l0, nsl, true, s));
+                SLMC_TRY(chain_step64(c, nf, s));
+                SLMC_TRY(stack_store(c, k, nf, s));
+            }
+            // upward pass: G(g0) from the running product B(g0, 0) and the stored B(L, g0), local
+            // updates of the group's slices (G carried between them), then the group joins B(g0, 0)
+            SLMC_LAUNCH(SLMC_PROF_FINAL, 1, s, slmc::set_identity(c, nf, s));
+            for (int k = 0; k < ng; ++k) {
+                const int l0 = k * c->p.n_s, nsl = std::min(c->p.n_s, c->L - l0);
+                const size_t NN = (size_t)c->N * c->N, slot = (size_t)k * c->max_fields * (2 * NN + c->N);
+                const double* Ul = c->dq_stack + slot;
+                const double* Tl = Ul + (size_t)c->max_fields * NN;
+                const double* lnDl = Tl + (size_t)c->max_fields * NN;
+                SLMC_LAUNCH(SLMC_PROF_GREENS, 5, s,
+                            slmc::dqmc_combine(c, Ul, lnDl, Tl, nf, c->QR, scal(c, 6), iscal(c, 3), s));
                 SLMC_LAUNCH(SLMC_PROF_DQMC, 1, s,
-                            slmc::dqmc_slices(c, xc, c->QR, nf, f0, g0, nsl, sweep,
+                            slmc::dqmc_slices(c, xc, c->QR, nf, f0, l0, nsl, sweep,
                                               n_acc_local ? n_acc_local + f0 : nullptr, s));
+                if (k + 1 == ng) break;
+                SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_group_kron(c, xc, nf, l0, nsl, false, s));
+                SLMC_TRY(chain_step64(c, nf, s));
             }
             if (nblock == 0) continue;
             // block updates: reflect one column, accept with the ratio of the full weights

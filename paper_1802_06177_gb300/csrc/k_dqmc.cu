@@ -8,7 +8,7 @@
 // R^2 exp(d ln w_bose). An accepted move updates G by Sherman-Morrison,
 // G -= (Delta_ii / R) G[:, i] (e_i - G[i, :]) (Eq. (S6)). Between slices G(l) = B_l G(l-1) B_l^-1
 // with B_l = diag(s) exp(-dtau K); at the start of every group of n_s slices G is recomputed
-// from scratch by the stabilised determinant path on the time-rotated field.
+// from two stabilised products (dqmc_combine below).
 //
 // FP64 issue is the scarce resource on this GPU (about two FMAs per clock per SM), so the
 // kernel spends it only on the arithmetic the method needs:
@@ -37,17 +37,6 @@
 namespace {
 
 constexpr int kThreads = 256;
-
-// xr[f][i][c] = x[f][i][(c + g0) mod L]: column c of xr is the field of B_{g0 + c + 1}, so the
-// Green's function G(L) of xr is G(g0) of x.
-__global__ void k_rotate(const double* __restrict__ x, double* __restrict__ xr, int N, int L, int g0, size_t total) {
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = idx / L;
-        const int c = (int)(idx - row * L);
-        const int src = c + g0 < L ? c + g0 : c + g0 - L;
-        xr[idx] = x[row * L + src];
-    }
-}
 
 template <int LMAX>
 __global__ void __launch_bounds__(kThreads) k_dqmc_slices(double* __restrict__ x, double* __restrict__ Gall, int Lx,
@@ -163,6 +152,130 @@ __global__ void k_block_propose(double* __restrict__ x, int N, int L, uint32_t k
     if (threadIdx.x == 0) u[f] = slmc::uniform53(w.z, w.w);
 }
 
+// G(g0) from two stabilised products. With B(g0, 0) = U_R D_R T_R (the running chain of the
+// slices already visited in this sweep) and B(L, g0)^T = U_L D_L T_L (the transposed chain of
+// the slices still to come, kept from the start of the sweep), D = D_b D_s (D_b = max(D, 1),
+// D_s = min(D, 1)):
+//   I + B(g0, 0) B(L, g0) = U_R D_bR M D_bL U_L^T,
+//   M = D_bR^-1 (U_R^T U_L) D_bL^-1 + D_sR (T_R T_L^T) D_sL,
+//   G(g0) = U_L D_bL^-1 M^-1 D_bR^-1 U_R^T,
+// M bounded entry-wise by the scale split, so its LU carries no exponentially large or small
+// numbers (the same split as the final step of the determinant path).
+struct GemmTerm {
+    const double* A;   // A(i, k): A[i N + k] (kAik) or A[k N + i]
+    const double* B;   // B(k, j): B[j N + k] (kBjk) or B[k N + j]
+    const double* ra;  // optional row scales of A, [nf][sstride]
+    const double* sk;  // optional scales of the summation index, applied to B
+    const double* cb;  // optional column scales of B
+};
+struct GemmArgs {
+    GemmTerm t[2];
+    int nterms;
+};
+
+// C = sum over terms of diag(ra) A diag(sk) B diag(cb), one field per blockIdx.z, a TM x TM
+// tile per CTA (4 x 4 outputs per thread), k-tiles of 16 staged in shared memory.
+template <int TM, bool kAik, bool kBjk, bool kCrow>
+__global__ void __launch_bounds__((TM / 4) * (TM / 4)) k_gemm64(GemmArgs g, double* __restrict__ C, int N,
+                                                                int sstride) {
+    constexpr int TT = TM / 4, NT = TT * TT, BK = 16;
+    __shared__ __align__(16) double As[BK][TM];
+    __shared__ __align__(16) double Bs[BK][TM];
+    const int f = blockIdx.z, i0 = blockIdx.y * TM, j0 = blockIdx.x * TM;
+    const int tid = threadIdx.x, tx = tid % TT, ty = tid / TT;
+    const size_t NN = (size_t)N * N;
+    double acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        if (t >= g.nterms) break;
+        const double* A = g.t[t].A + f * NN;
+        const double* B = g.t[t].B + f * NN;
+        const double* ra = g.t[t].ra ? g.t[t].ra + (size_t)f * sstride : nullptr;
+        const double* sk = g.t[t].sk ? g.t[t].sk + (size_t)f * sstride : nullptr;
+        const double* cb = g.t[t].cb ? g.t[t].cb + (size_t)f * sstride : nullptr;
+        for (int k0 = 0; k0 < N; k0 += BK) {
+            for (int q = tid; q < TM * BK; q += NT) {
+                const int ii = kAik ? q / BK : q % TM, kk = kAik ? q % BK : q / TM;
+                const int i = i0 + ii, k = k0 + kk;
+                double v = 0.0;
+                if (i < N && k < N) {
+                    v = kAik ? A[(size_t)i * N + k] : A[(size_t)k * N + i];
+                    if (ra) v *= ra[i];
+                }
+                As[kk][ii] = v;
+            }
+            for (int q = tid; q < TM * BK; q += NT) {
+                const int jj = kBjk ? q / BK : q % TM, kk = kBjk ? q % BK : q / TM;
+                const int j = j0 + jj, k = k0 + kk;
+                double v = 0.0;
+                if (j < N && k < N) {
+                    v = kBjk ? B[(size_t)j * N + k] : B[(size_t)k * N + j];
+                    if (sk) v *= sk[k];
+                    if (cb) v *= cb[j];
+                }
+                Bs[kk][jj] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                const double2 a01 = *reinterpret_cast<const double2*>(&As[kk][ty * 4]);
+                const double2 a23 = *reinterpret_cast<const double2*>(&As[kk][ty * 4 + 2]);
+                const double2 b01 = *reinterpret_cast<const double2*>(&Bs[kk][tx * 4]);
+                const double2 b23 = *reinterpret_cast<const double2*>(&Bs[kk][tx * 4 + 2]);
+                const double a[4] = {a01.x, a01.y, a23.x, a23.y}, b[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty * 4 + r;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + tx * 4 + q;
+            if (i < N && j < N) C[f * NN + (kCrow ? (size_t)i * N + j : (size_t)j * N + i)] = acc[r][q];
+        }
+    }
+}
+
+// S[f] = [D_bR^-1 | D_sR | D_bL^-1 | D_sL], each [N], from the ln D of both products
+__global__ void k_split_scales(const double* __restrict__ lnR, const double* __restrict__ lnL, double* __restrict__ S,
+                               int N) {
+    const int f = blockIdx.x;
+    double* Sf = S + (size_t)f * 4 * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double r = lnR[(size_t)f * N + i], l = lnL[(size_t)f * N + i];
+        Sf[i] = exp(-fmax(r, 0.0));
+        Sf[N + i] = exp(fmin(r, 0.0));
+        Sf[2 * N + i] = exp(-fmax(l, 0.0));
+        Sf[3 * N + i] = exp(fmin(l, 0.0));
+    }
+}
+
+template <int TM, bool kAik, bool kBjk, bool kCrow>
+cudaError_t launch_gemm(const GemmArgs& g, double* C, int N, int nf, int sstride, cudaStream_t s) {
+    dim3 grid((N + TM - 1) / TM, (N + TM - 1) / TM, nf);
+    k_gemm64<TM, kAik, kBjk, kCrow><<<grid, (TM / 4) * (TM / 4), 0, s>>>(g, C, N, sstride);
+    return cudaGetLastError();
+}
+
+// the tile (32, 48 or 64) that pads N least, the larger on ties
+template <bool kAik, bool kBjk, bool kCrow>
+cudaError_t gemm64(const GemmArgs& g, double* C, int N, int nf, int sstride, cudaStream_t s) {
+    const int p32 = (N + 31) / 32 * 32, p48 = (N + 47) / 48 * 48, p64 = (N + 63) / 64 * 64;
+    if (p64 <= p48 && p64 <= p32) return launch_gemm<64, kAik, kBjk, kCrow>(g, C, N, nf, sstride, s);
+    if (p48 <= p32) return launch_gemm<48, kAik, kBjk, kCrow>(g, C, N, nf, sstride, s);
+    return launch_gemm<32, kAik, kBjk, kCrow>(g, C, N, nf, sstride, s);
+}
+
 size_t dqmc_smem_bytes(int N, bool g_in_smem) {
     return ((g_in_smem ? (size_t)N * N : 0) + 8 * (size_t)N + 4 * slmc::kKronTab) * sizeof(double);
 }
@@ -191,14 +304,30 @@ cudaError_t launch_slices(slmc_ctx* c, double* x, double* G, int nf, int chain0,
 
 namespace slmc {
 
-cudaError_t dqmc_rotate(slmc_ctx* c, const double* x, double* xr, int nf, int g0, cudaStream_t s) {
-    const size_t total = (size_t)nf * c->N * c->L;
-    k_rotate<<<(unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096), 256, 0, s>>>(x, xr, c->N, c->L, g0,
-                                                                                                  total);
-    return cudaGetLastError();
-}
-
 bool dqmc_ok(const slmc_ctx* c) { return dqmc_supported(c); }
+
+cudaError_t dqmc_combine(slmc_ctx* c, const double* Ul, const double* lnDl, const double* Tl, int nf, double* G,
+                         double* lndet_scratch, int* sign_scratch, cudaStream_t s) {
+    const int N = c->N;
+    double* S = c->Sws;  // [nf][4][N]: free between the steps of a chain
+    k_split_scales<<<nf, 256, 0, s>>>(c->lnD, lnDl, S, N);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    GemmArgs m{};
+    m.nterms = 2;
+    m.t[0] = GemmTerm{c->U, Ul, S, nullptr, S + 2 * N};     // D_bR^-1 U_R^T U_L D_bL^-1
+    m.t[1] = GemmTerm{c->Ta, Tl, S + N, nullptr, S + 3 * N};  // D_sR T_R T_L^T D_sL
+    e = gemm64<true, true, false>(m, c->Y, N, nf, 4 * N, s);  // M column-major, as the LU expects
+    if (e != cudaSuccess) return e;
+    e = final_lu(c, nf, lndet_scratch, sign_scratch, s);
+    if (e != cudaSuccess) return e;
+    e = final_greens(c, nf, c->Tb, s);  // X = M^-1 D_bR^-1 U_R^T, row-major, in the idle T buffer
+    if (e != cudaSuccess) return e;
+    GemmArgs gg{};
+    gg.nterms = 1;
+    gg.t[0] = GemmTerm{Ul, c->Tb, nullptr, S + 2 * N, nullptr};  // U_L D_bL^-1 X
+    return gemm64<false, false, true>(gg, G, N, nf, 4 * N, s);
+}
 
 cudaError_t dqmc_slices(slmc_ctx* c, double* x, double* G, int nf, int chain0, int l0, int nsl, uint64_t sweep,
                         long long* n_acc, cudaStream_t s) {

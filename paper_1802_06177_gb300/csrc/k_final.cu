@@ -490,9 +490,9 @@ __global__ void __launch_bounds__(256) k_greens_blk(const double* __restrict__ L
 }
 
 template <int MAXR>
-cudaError_t launch_final(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s) {
+cudaError_t launch_final(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s, bool assemble) {
     const int N = c->N;
-    k_assemble_M<<<nf, kThreads, 2 * N * sizeof(double), s>>>(c->U, c->Ta, c->lnD, c->Y, N);
+    if (assemble) k_assemble_M<<<nf, kThreads, 2 * N * sizeof(double), s>>>(c->U, c->Ta, c->lnD, c->Y, N);
     const size_t smem = (size_t)N * kLS * sizeof(double);
     if (smem <= 227 * 1024) {  // blocked LU (the panel fits in shared memory)
         cudaError_t e = cudaFuncSetAttribute(k_lu_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -519,17 +519,27 @@ cudaError_t launch_greens(slmc_ctx* c, int nf, double* G, cudaStream_t s) {
 
 namespace slmc {
 
-cudaError_t final_logdet(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s) {
+namespace {
+cudaError_t final_dispatch(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s, bool assemble) {
     switch (rows_per_lane_class(c->N)) {
-        case 1: return launch_final<1>(c, nf, lndet, sign, s);
-        case 2: return launch_final<2>(c, nf, lndet, sign, s);
-        case 4: return launch_final<4>(c, nf, lndet, sign, s);
-        case 5: return launch_final<5>(c, nf, lndet, sign, s);
-        case 8: return launch_final<8>(c, nf, lndet, sign, s);
-        case 12: return launch_final<12>(c, nf, lndet, sign, s);
-        case 18: return launch_final<18>(c, nf, lndet, sign, s);
-        default: return launch_final<32>(c, nf, lndet, sign, s);
+        case 1: return launch_final<1>(c, nf, lndet, sign, s, assemble);
+        case 2: return launch_final<2>(c, nf, lndet, sign, s, assemble);
+        case 4: return launch_final<4>(c, nf, lndet, sign, s, assemble);
+        case 5: return launch_final<5>(c, nf, lndet, sign, s, assemble);
+        case 8: return launch_final<8>(c, nf, lndet, sign, s, assemble);
+        case 12: return launch_final<12>(c, nf, lndet, sign, s, assemble);
+        case 18: return launch_final<18>(c, nf, lndet, sign, s, assemble);
+        default: return launch_final<32>(c, nf, lndet, sign, s, assemble);
     }
+}
+}  // namespace
+
+cudaError_t final_logdet(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s) {
+    return final_dispatch(c, nf, lndet, sign, s, true);
+}
+
+cudaError_t final_lu(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s) {
+    return final_dispatch(c, nf, lndet, sign, s, false);
 }
 
 cudaError_t final_greens(slmc_ctx* c, int nf, double* G, cudaStream_t s) {

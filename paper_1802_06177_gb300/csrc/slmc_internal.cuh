@@ -31,6 +31,8 @@ struct slmc_ctx {
     // i = ix + Lx iy), each stored twice over: [E_x | E_x^-1 | E_y | E_y^-1], kKronTab
     // doubles apiece. Null when a lattice side exceeds kKronMaxLine (dense products then).
     double* kron;
+    double* dq_stack;     // DQMC: [groups][max_fields] (U | T | lnD) of the transposed left products
+    int dq_groups;        // groups the stack holds
     int dense_slices;  // 1: FP64 slice products by the dense exp(-dtau K) even where kron exists
     float* F32;      // F = E - I rounded to FP32 (reduced-precision slices use Y + F Y)
     int* lo_kidx;    // FP32 modes: [S][N] column of the S-th stencil entry of row i, then sel[S]
@@ -191,6 +193,8 @@ cudaError_t form_q(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t set_identity(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t u_to_f32(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t final_logdet(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s);
+// LU of the matrix already in c->Y (the step of final_logdet after assembling M)
+cudaError_t final_lu(slmc_ctx* c, int nf, double* lndet, int* sign, cudaStream_t s);
 cudaError_t final_greens(slmc_ctx* c, int nf, double* G, cudaStream_t s);
 cudaError_t bose_log_weight(slmc_ctx* c, const double* x, int nf, const double* lndet, double* lnw,
                             cudaStream_t s);
@@ -202,7 +206,10 @@ cudaError_t eff_half_sweep(slmc_ctx* c, double* x, int nf, int chain0, const dou
 cudaError_t eff_wolff(slmc_ctx* c, double* x, int nf, int chain0, const double* J, uint64_t sweep, int k,
                       cudaStream_t s, const unsigned long long* dctr = nullptr, int nsweeps = 0);
 cudaError_t slice_group_kron(slmc_ctx* c, const double* x, int nf, int l0, int nsl, bool transposed, cudaStream_t s);
-cudaError_t dqmc_rotate(slmc_ctx* c, const double* x, double* xr, int nf, int g0, cudaStream_t s);
+// G(g0) = [I + B(g0,0) B(L,g0)]^-1 into G (row-major) from the running product in (U, lnD, Ta)
+// and the transposed left product (Ul column-major, lnDl, Tl row-major); uses Y, Tb, Sws, piv.
+cudaError_t dqmc_combine(slmc_ctx* c, const double* Ul, const double* lnDl, const double* Tl, int nf, double* G,
+                         double* lndet_scratch, int* sign_scratch, cudaStream_t s);
 bool dqmc_ok(const slmc_ctx* c);  // L >= 2 and both lattice sides <= 32
 cudaError_t dqmc_slices(slmc_ctx* c, double* x, double* G, int nf, int chain0, int l0, int nsl, uint64_t sweep,
                         long long* n_acc, cudaStream_t s);
