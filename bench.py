@@ -130,8 +130,10 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # algorithmic work per launch call of each kernel class (flops or bytes), per field
 # ---------------------------------------------------------------------------------------
-def class_work(cls, wl, nsl_mean):
+def class_work(cls, wl, nsl_mean, precision="fp32"):
     N, L = wl.N, wl.L
+    if cls == "slice" and precision == "fp64":  # separable exp(-dtau K): N^2 (Lx + Ly) FMAs per slice
+        return 2.0 * N ** 2 * (2 * wl.Lx) * nsl_mean, "flop"
     if cls == "slice":
         return 2.0 * N ** 3 * nsl_mean, "flop"
     if cls == "qr":
@@ -426,7 +428,7 @@ def run_gpu(args):
     # (union of their call intervals) and divide the class's work by it
     dom = max(prof, key=lambda k: prof[k][2])
     dom_ms, dom_calls, dom_busy, dom_units = prof[dom]
-    work, kind = class_work(dom, wl, nsl_mean)
+    work, kind = class_work(dom, wl, nsl_mean, args.precision)
     roof = None
     if work:
         fields_per_call = dom_units / max(dom_calls, 1)
@@ -552,17 +554,139 @@ def run_uneven_batch(args, dev, seed):
             "acceptance": acc, "tuned": tuned}
 
 
+# ---------------------------------------------------------------------------------------
+# DQMC sweeps (the conventional updates the self-learning method is compared with)
+# ---------------------------------------------------------------------------------------
+def _oracle_dqmc_worker(args):
+    wl_name, chain, seed = args
+    from oracle import HolsteinParams
+    from oracle.dqmc import dqmc_sweeps
+    from oracle.lattice import exp_hopping
+    from paper_1802_06177_gb300 import inputs
+    from paper_1802_06177_gb300.workloads import WORKLOADS
+    wl = WORKLOADS[wl_name]
+    p = HolsteinParams(wl.Lx, wl.Lx, wl.L, n_s=wl.n_s)
+    E = exp_hopping(wl.Lx, wl.Lx, 1.0, 0.0, 0.1)
+    x = inputs.mixed_fields(2, wl.Lx, wl.Lx, wl.L, seed=wl.seed + 7 * chain)[chain % 2]
+    t0 = time.perf_counter()
+    dqmc_sweeps(p, x, 1, 0, chain, seed, 0.5, E=E)
+    return time.perf_counter() - t0
+
+
+DQMC_METRIC = "DQMC sweeps (local updates, fast ratio + Sherman-Morrison + wrapping) per second on one GB300"
+DQMC_UNIT = "chain-sweeps/s"
+
+
+def run_dqmc(args):
+    import torch
+
+    from paper_1802_06177_gb300 import inputs
+    from paper_1802_06177_gb300.slmc import Context
+    from paper_1802_06177_gb300.workloads import WORKLOADS
+
+    rank, local, world = dist_setup(args)
+    wl = WORKLOADS[args.workload]
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nproc = min(16, os.cpu_count() or 1)
+    pool = oracle_pool(nproc) if rank == 0 and not args.no_cpu_baseline else None
+    nf = args.fields or torch.cuda.get_device_properties(dev).multi_processor_count  # one chain per SM
+    seed = wl.seed + 1000003 * rank
+    ctx = Context(wl.Lx, wl.Lx, wl.L, n_s=wl.n_s, precision="fp64", max_fields=nf, seed=seed, sweep_delta=0.5,
+                  device=dev)
+    x = torch.from_numpy(inputs.mixed_fields(nf, wl.Lx, wl.Lx, wl.L, seed=seed)).to(dev)
+    n_loc = torch.zeros(nf, dtype=torch.int64, device=dev)
+    n_blk = torch.zeros(nf, dtype=torch.int64, device=dev)
+    ctx.dqmc_sweep(x, args.warmup, sweep0=0, nblock=args.dqmc_block, n_acc_local=n_loc, n_acc_block=n_blk)
+    torch.cuda.synchronize()
+    barrier(world)
+    acc0 = int(n_loc.sum().item())
+    sampler = ClockSampler(local)
+    ctx.profile(True)
+    n0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    ctx.dqmc_sweep(x, args.steps, sweep0=args.warmup, nblock=args.dqmc_block, n_acc_local=n_loc, n_acc_block=n_blk)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    launches = ctx.launch_count() - n0
+    prof = ctx.profile_read_detail()
+    ctx.profile(False)
+    clk = sampler.stop()
+    accepted = int(n_loc.sum().item()) - acc0
+    ctx.get_error()
+    # e2e: fields from pinned host memory, one sweep, fields and counts back
+    xh = torch.from_numpy(x.cpu().numpy()).pin_memory()
+    nh = torch.empty(nf, dtype=torch.int64).pin_memory()
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(max(1, min(args.steps, 2))):
+        x.copy_(xh, non_blocking=True)
+        ctx.dqmc_sweep(x, 1, sweep0=10 ** 6 + k, nblock=args.dqmc_block, n_acc_local=n_loc, n_acc_block=n_blk)
+        xh.copy_(x, non_blocking=True)
+        nh.copy_(n_loc, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / max(1, min(args.steps, 2)), world, dev)
+    ctx.close()
+    barrier(world)
+    if rank != 0:
+        return 0
+    N, Lx, L = wl.N, wl.Lx, wl.L
+    ms_step = ms / args.steps
+    value = nf * world / (ms_step / 1e3)
+    # k_dqmc_slices: per slice 2 N^2 (Lx + Ly) FMAs of the wrap (four circulant passes), N^2 per
+    # accepted move (Sherman-Morrison); FP64 pipe (alu)
+    flops = 2.0 * (2.0 * N * N * (2 * Lx) * L * nf * args.steps + float(N) * N * accepted)
+    dq_ms, dq_calls, dq_busy, dq_units = prof["dqmc"]
+    achieved = flops / (dq_busy / 1e3) / 1e12
+    roof = {"kernel_class": "dqmc", "kernel": "k_dqmc_slices", "bound": "alu", "pipe": "fp64",
+            "algorithmic_per_launch": flops / max(dq_calls, 1), "launches_timed": dq_calls, "busy_ms": dq_busy,
+            "achieved": achieved, "peak": NOMINAL["fp64_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / NOMINAL["fp64_tflops"], "peak_probed": PROBED["fp64_tflops"],
+            "frac_of_probed": achieved / PROBED["fp64_tflops"], "traffic": None,
+            "peak_source": "nominal FP64 1.25 TFLOP/s (alu, not in MEASURED_PEAKS.json); probed DFMA rate beside it"}
+    total_prof = sum(v[2] for v in prof.values())
+    shares = {k: round(v[2] / total_prof, 4) for k, v in prof.items() if v[2] > 0}
+    cpu = None
+    if pool is not None:
+        t0 = time.perf_counter()
+        pool.map(_oracle_dqmc_worker, [(wl.name, c, seed) for c in range(nproc)])
+        wall = time.perf_counter() - t0
+        pool.close()
+        cpu = {"value": nproc / wall, "unit": DQMC_UNIT, "cores": nproc, "kind": "oracle",
+               "sample": "%d chains (one per core, 1 BLAS thread each), one oracle DQMC sweep each on %s"
+                         % (nproc, wl.name)}
+    h2d = nf * N * L * 8
+    line = {"metric": DQMC_METRIC, "value": value, "unit": DQMC_UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "model": "holstein_2d", "N": N, "Lx": Lx, "L": L, "n_s": wl.n_s,
+                       "chains_per_gpu": nf, "block_updates_per_sweep": args.dqmc_block, "sweep_delta": 0.5,
+                       "parallelism": "replicas x%d" % world,
+                       "l2": "per-chain G in shared memory (N <= 160) or L2; fields %.0f MB" % (h2d / 1e6)},
+            "e2e": {"value": nf * world / (e2e_ms / 1e3), "unit": DQMC_UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": h2d + 8 * nf},
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "acceptance_local": accepted / float(nf * args.steps * N * L), "time_shares": shares, "mode": "dqmc"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="slmc", choices=["slmc", "reference"])
-    ap.add_argument("--workload", default="holstein_16x16_L160")
+    ap.add_argument("--workload", default=None, help="default holstein_16x16_L160 (dqmc mode: holstein_12x12_L120)")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32x3", "bf16x9"])
     ap.add_argument("--nsweeps", type=int, default=20)
     ap.add_argument("--fields", type=int, default=0, help="override chains per GPU (small profiling cases)")
-    ap.add_argument("--mode", default="step", choices=["step", "logdet"])
+    ap.add_argument("--mode", default="step", choices=["step", "logdet", "dqmc"])
+    ap.add_argument("--dqmc-block", type=int, default=0, help="DQMC mode: block updates per sweep")
     ap.add_argument("--acc-fields", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -575,8 +699,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "slmc":
         args.warmup = 3
+    if args.workload is None:
+        args.workload = "holstein_12x12_L120" if args.mode == "dqmc" else "holstein_16x16_L160"
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "dqmc":
+        return run_dqmc(args)
     return run_gpu(args)
 
 
