@@ -6,11 +6,16 @@ Steps (Sec. "SLMC" and Suppl. Sec. "SLMC for the Holstein model"):
      J_k = omega0^2/4 + 1/(2 dtau^2), J_nn' = omega0^2/2) plus a small double-well term;
   2. self-learning: propose configurations with effective-model sweeps under the current
      couplings (the proposals of the cumulative update), score each with the exact ln w and
-     refit E_eff on them (Eq. (5)) -- the training data is generated by the method itself,
-     since the DQMC configurations of the paper are not available -- and repeat;
+     refit E_eff on them (Eq. (5)), and repeat; or (--train-source dqmc, as the paper does)
+     train on configurations of conventional DQMC chains (Suppl. Eqs. (S3)-(S6)) after
+     thermalisation, one per chain every --dqmc-gap sweeps, then refine with the remaining
+     self-learning rounds;
   3. production: cumulative updates (Eq. (6)) with the learned couplings, measuring the CDW
      structure factor S(pi, pi) after every update and counting acceptances.
 Error bars: the per-chain time series are averaged over chains, then binned in time.
+--dqmc-only runs the conventional DQMC chains instead and measures S(pi, pi) after every sweep:
+the baseline whose autocorrelation time and cost per sweep the self-learning method is
+compared with (Sec. "Results").
 Under torchrun every process runs its own chains on its own GPU (Philox key = seed + rank);
 the regression is fitted over all processes' configurations (paper_1802_06177_gb300.dist)
 and the measurements are summed over processes; rank 0 prints the result.
@@ -58,8 +63,68 @@ def binned_error(series, nbins=10):
     return float(means.std(ddof=1) / math.sqrt(nb))
 
 
+def dqmc_configurations(ctx, x, therm, gap, count, sweep0=0):
+    """Thermalise the DQMC chains x in place for `therm` sweeps, then take `count` snapshots
+    of every chain, `gap` sweeps apart. Returns the stacked snapshots, the sweep counter
+    reached and the local acceptance."""
+    chains = x.shape[0]
+    n_loc = torch.zeros(chains, dtype=torch.int64, device=x.device)
+    ctx.dqmc_sweep(x, therm, sweep0=sweep0, n_acc_local=n_loc)
+    snaps = []
+    ctr = sweep0 + therm
+    for _ in range(count):
+        ctx.dqmc_sweep(x, gap, sweep0=ctr, n_acc_local=n_loc)
+        ctr += gap
+        snaps.append(x.clone())
+    moves = chains * (therm + gap * count) * ctx.N * ctx.L
+    return torch.cat(snaps), ctr, float(n_loc.sum().item()) / max(moves, 1)
+
+
+def run_dqmc(Lx, L, n_s=8, chains=32, sweeps=500, precision="fp64", dtau=0.1, lam=1.0, omega0=1.0,
+             sweep_delta=0.5, seed=0x1802061774, device="cuda", rank=0, world=1, nblock=0):
+    """Conventional DQMC chains: S(pi, pi) from G after every sweep, its integrated
+    autocorrelation time in sweeps and the time per sweep."""
+    dev = torch.device(device)
+    seed = seed + rank
+    ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
+                  sweep_delta=sweep_delta, seed=seed, max_fields=chains, device=dev)
+    x = torch.from_numpy(inputs.gaussian_fields(chains, Lx, Lx, L, sigma=1.0, seed=seed)).to(dev)
+    n_loc = torch.zeros(chains, dtype=torch.int64, device=dev)
+    n_blk = torch.zeros(chains, dtype=torch.int64, device=dev)
+    G = torch.empty(chains, ctx.N, ctx.N, dtype=torch.float64, device=dev)
+    obs = torch.empty(sweeps, chains, dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sweep_ms = 0.0
+    for k in range(sweeps):
+        e0.record()
+        ctx.dqmc_sweep(x, 1, sweep0=k, nblock=nblock, n_acc_local=n_loc, n_acc_block=n_blk)
+        e1.record()
+        ctx.greens(x, G)
+        obs[k] = ctx.measure_cdw(G)
+        torch.cuda.synchronize()
+        sweep_ms += e0.elapsed_time(e1)
+    ctx.get_error()
+    therm = sweeps // 5
+    tau = integrated_autocorrelation(obs.cpu().numpy()[therm:])
+    S_sum = sum_over_processes(obs.sum(dim=1))
+    acc = sum_over_processes(torch.stack([n_loc.sum(), n_blk.sum()]))
+    series = (S_sum / (chains * world)).cpu().numpy()[therm:]
+    N = Lx * Lx
+    res = {"method": "dqmc", "lattice": "%dx%d" % (Lx, Lx), "N": N, "L": L, "beta": L * dtau, "n_s": n_s,
+           "lambda": lam, "omega0": omega0, "chains": chains * world, "sweeps": sweeps, "block_updates": nblock,
+           "S_pipi_mean": float(series.mean()), "S_pipi_err": binned_error(series),
+           "S_pipi_tau_int_sweeps": tau, "S_pipi_halves": [float(h.mean()) for h in np.array_split(series, 2)],
+           "local_acceptance": float(acc[0].item()) / (chains * world * sweeps * N * L),
+           "block_acceptance": float(acc[1].item()) / max(1, chains * world * sweeps * nblock),
+           "ms_per_sweep": sweep_ms / sweeps, "chain_sweeps_per_s": chains * world * sweeps / (sweep_ms / 1e3),
+           "ms_per_independent_sample": 2.0 * tau * sweep_ms / sweeps}
+    ctx.close()
+    return res
+
+
 def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision="fp32", dtau=0.1, lam=1.0,
-        omega0=1.0, sweep_delta=0.3, seed=0x1802061774, rounds=2, device="cuda", rank=0, world=1, wolff=0):
+        omega0=1.0, sweep_delta=0.3, seed=0x1802061774, rounds=2, device="cuda", rank=0, world=1, wolff=0,
+        train_source="self", dqmc_therm=50, dqmc_gap=5):
     dev = torch.device(device)
     seed = seed + rank
     ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
@@ -76,6 +141,19 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
     per_round = max(1, math.ceil(train / (chains * world)))
     history = []
     sweep_ctr = 1 << 30  # training proposals use Philox sweep counters far from the production ones
+    xp = None
+    if train_source == "dqmc":  # the paper's training data: equilibrated DQMC configurations
+        xd = x.clone()
+        X, _, dacc = dqmc_configurations(ctx, xd, dqmc_therm, dqmc_gap, per_round, sweep0=1 << 40)
+        Y, _, _ = ctx.log_weight(X)
+        J, resid = fit_eff_distributed(ctx, X.contiguous(), Y.contiguous())
+        history.append({"round": "dqmc", "configs": int(X.shape[0]) * world, "dqmc_thermalisation": dqmc_therm,
+                        "dqmc_gap": dqmc_gap, "dqmc_local_acceptance": dacc, "J": J.cpu().tolist(),
+                        "rms_resid": float(resid.item())})
+        x = xd  # the self-learning rounds and production start from the DQMC chains
+        xp = xd
+        del X, Y
+        rounds = max(0, rounds - 1)
     for r in range(rounds):
         xs, ys = [], []
         xp = x.clone()
@@ -137,6 +215,50 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
     return res
 
 
+def power_law_exponent(sizes, values):
+    """Least-squares slope of ln(value) against ln(size)."""
+    lx, ly = np.log(np.asarray(sizes, dtype=np.float64)), np.log(np.asarray(values, dtype=np.float64))
+    if len(lx) < 2 or not np.all(np.isfinite(ly)):
+        return float("nan")
+    return float(np.polyfit(lx, ly, 1)[0])
+
+
+def autocorrelation_study(sizes, beta=4.1, dtau=0.1, lam=1.0, omega0=0.5, n_s=10, chains=64, steps=2000,
+                          sweeps=10, train=1024, seed=0x1802061774, device="cuda", rank=0, world=1, nblock=4,
+                          wolff=1):
+    """Autocorrelation time tau_L of S(pi, pi) against the linear size for DQMC and SLMC with the
+    paper's Monte Carlo steps (Sec. "Results"): a DQMC step is a sweep of local updates plus
+    `nblock` block updates; an SLMC step is a sweep of local updates of E_eff plus `wolff` Wolff
+    cluster updates, so tau in SLMC steps is tau in cumulative updates times `sweeps`. Also the
+    GPU time per statistically independent configuration, 2 tau_L times the time per step, and
+    the power-law exponents of both against the size. Defaults: the paper's critical point
+    (lambda = 0.5 from g = 1, Omega = 0.5; beta = 1 / T_c = 4.1)."""
+    L = 2 * max(1, int(round(beta / (2.0 * dtau))))  # the checkerboard sweeps of E_eff need an even L
+    dtau = beta / L
+    rows = []
+    for Lx in sizes:
+        d = run_dqmc(Lx, L, min(n_s, L), chains, steps, "fp64", dtau=dtau, lam=lam, omega0=omega0, seed=seed,
+                     device=device, rank=rank, world=world, nblock=nblock)
+        m = run(Lx, L, min(n_s, L), chains, train, max(4, steps // sweeps), sweeps, "fp32", dtau=dtau, lam=lam,
+                omega0=omega0, seed=seed, rounds=2, device=device, rank=rank, world=world, wolff=wolff,
+                train_source="dqmc")
+        s_ms = 1e3 * m["production_seconds"] / m["updates"] / sweeps  # per SLMC step
+        rows.append({"Lx": Lx, "dqmc_tau_steps": d["S_pipi_tau_int_sweeps"], "dqmc_ms_per_step": d["ms_per_sweep"],
+                     "dqmc_ms_per_independent": d["ms_per_independent_sample"], "dqmc_S": d["S_pipi_mean"],
+                     "dqmc_S_err": d["S_pipi_err"], "dqmc_S_halves": d["S_pipi_halves"],
+                     "dqmc_block_acceptance": d["block_acceptance"],
+                     "slmc_tau_steps": m["S_pipi_tau_int_updates"] * sweeps, "slmc_ms_per_step": s_ms,
+                     "slmc_ms_per_independent": 2.0 * m["S_pipi_tau_int_updates"] * sweeps * s_ms,
+                     "slmc_S": m["S_pipi_mean"], "slmc_S_err": m["S_pipi_err"], "slmc_S_halves": m["S_pipi_halves"],
+                     "slmc_acceptance": m["acceptance"], "slmc_mean_cluster": m["wolff_mean_cluster"]})
+    fit = {k: power_law_exponent([r["Lx"] for r in rows], [r[k] for r in rows])
+           for k in ("dqmc_tau_steps", "slmc_tau_steps", "dqmc_ms_per_independent", "slmc_ms_per_independent")}
+    return {"study": "autocorrelation", "beta": beta, "L": L, "dtau": dtau, "g": lam, "omega0": omega0,
+            "lambda_dimensionless": lam ** 2 / (8.0 * omega0 ** 2), "chains": chains * world, "steps": steps,
+            "sweeps_per_update": sweeps, "dqmc_block_updates_per_step": nblock, "wolff_per_sweep": wolff,
+            "sizes": rows, "exponents": fit}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--Lx", type=int, default=24)
@@ -152,6 +274,18 @@ def main():
     ap.add_argument("--lam", type=float, default=1.0, help="electron-phonon coupling g")
     ap.add_argument("--omega0", type=float, default=1.0, help="phonon frequency")
     ap.add_argument("--seed", type=int, default=0x1802061774)
+    ap.add_argument("--train-source", default="self", choices=["self", "dqmc"],
+                    help="training configurations: self-generated proposals, or DQMC chains (the paper's way)")
+    ap.add_argument("--dqmc-therm", type=int, default=50, help="DQMC thermalisation sweeps before the training set")
+    ap.add_argument("--dqmc-gap", type=int, default=5, help="DQMC sweeps between training configurations")
+    ap.add_argument("--dqmc-only", action="store_true", help="run DQMC chains and measure S(pi,pi) every sweep")
+    ap.add_argument("--dqmc-block", type=int, default=0, help="DQMC block updates per sweep (--dqmc-only)")
+    ap.add_argument("--autocorr", default=None,
+                    help="comma-separated linear sizes: tau_L of S(pi,pi) for DQMC and SLMC (paper's MC steps)")
+    ap.add_argument("--beta", type=float, default=4.1, help="--autocorr: inverse temperature")
+    ap.add_argument("--steps", type=int, default=2000, help="--autocorr: MC steps per method and size")
+    ap.add_argument("--sweep-delta", type=float, default=None,
+                    help="proposal width (default 0.3 for E_eff sweeps, 0.5 for DQMC sweeps)")
     a = ap.parse_args()
     import os
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -161,9 +295,20 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    res = run(a.Lx, a.L, a.n_s, a.chains, a.train, a.updates, a.sweeps, a.precision, rounds=a.rounds,
-              device="cuda:%d" % local, rank=rank, world=world, wolff=a.wolff, lam=a.lam, omega0=a.omega0,
-              seed=a.seed)
+    if a.autocorr:
+        res = autocorrelation_study([int(v) for v in a.autocorr.split(",")], beta=a.beta, lam=a.lam,
+                                    omega0=a.omega0, n_s=a.n_s, chains=a.chains, steps=a.steps, sweeps=a.sweeps,
+                                    train=a.train, seed=a.seed, device="cuda:%d" % local, rank=rank, world=world,
+                                    nblock=a.dqmc_block if a.dqmc_block else 4, wolff=a.wolff if a.wolff else 1)
+    elif a.dqmc_only:
+        res = run_dqmc(a.Lx, a.L, a.n_s, a.chains, a.updates, "fp64", lam=a.lam, omega0=a.omega0,
+                       sweep_delta=0.5 if a.sweep_delta is None else a.sweep_delta, seed=a.seed,
+                       device="cuda:%d" % local, rank=rank, world=world, nblock=a.dqmc_block)
+    else:
+        res = run(a.Lx, a.L, a.n_s, a.chains, a.train, a.updates, a.sweeps, a.precision, rounds=a.rounds,
+                  device="cuda:%d" % local, rank=rank, world=world, wolff=a.wolff, lam=a.lam, omega0=a.omega0,
+                  seed=a.seed, sweep_delta=0.3 if a.sweep_delta is None else a.sweep_delta,
+                  train_source=a.train_source, dqmc_therm=a.dqmc_therm, dqmc_gap=a.dqmc_gap)
     if rank == 0:
         print(json.dumps(res))
     if world > 1:

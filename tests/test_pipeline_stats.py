@@ -24,3 +24,10 @@ def test_binned_error_of_white_noise():
     rng = np.random.default_rng(1)
     x = rng.normal(scale=2.0, size=40000)
     assert abs(binned_error(x, nbins=20) / (2.0 / math.sqrt(len(x))) - 1.0) < 0.5
+
+
+def test_power_law_exponent():
+    from paper_1802_06177_gb300.pipeline import power_law_exponent
+    sizes = [4, 6, 8, 12]
+    assert abs(power_law_exponent(sizes, [3.0 * s ** 2.5 for s in sizes]) - 2.5) < 1e-12
+    assert math.isnan(power_law_exponent([4], [1.0]))
