@@ -63,6 +63,15 @@ def binned_error(series, nbins=10):
     return float(means.std(ddof=1) / math.sqrt(nb))
 
 
+def initial_fields(init, chains, Lx, L, alpha, seed):
+    """Starting fields: iid N(0, 1) ("gaussian"), or the checkerboard CDW state at the minima
+    of the double well, alpha (-1)^(ix+iy) + N(0, 0.3^2) ("cdw": the ordered state the model
+    develops below T_c, so that chains near the transition need not order first)."""
+    if init == "cdw":
+        return torch.from_numpy(inputs.cdw_fields(chains, Lx, Lx, L, amp=alpha, noise=0.3, seed=seed))
+    return torch.from_numpy(inputs.gaussian_fields(chains, Lx, Lx, L, sigma=1.0, seed=seed))
+
+
 def dqmc_configurations(ctx, x, therm, gap, count, sweep0=0):
     """Thermalise the DQMC chains x in place for `therm` sweeps, then take `count` snapshots
     of every chain, `gap` sweeps apart. Returns the stacked snapshots, the sweep counter
@@ -81,14 +90,14 @@ def dqmc_configurations(ctx, x, therm, gap, count, sweep0=0):
 
 
 def run_dqmc(Lx, L, n_s=8, chains=32, sweeps=500, precision="fp64", dtau=0.1, lam=1.0, omega0=1.0,
-             sweep_delta=0.5, seed=0x1802061774, device="cuda", rank=0, world=1, nblock=0):
+             sweep_delta=0.5, seed=0x1802061774, device="cuda", rank=0, world=1, nblock=0, init="gaussian"):
     """Conventional DQMC chains: S(pi, pi) from G after every sweep, its integrated
     autocorrelation time in sweeps and the time per sweep."""
     dev = torch.device(device)
     seed = seed + rank
     ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
                   sweep_delta=sweep_delta, seed=seed, max_fields=chains, device=dev)
-    x = torch.from_numpy(inputs.gaussian_fields(chains, Lx, Lx, L, sigma=1.0, seed=seed)).to(dev)
+    x = initial_fields(init, chains, Lx, L, lam / omega0 ** 2, seed).to(dev)
     n_loc = torch.zeros(chains, dtype=torch.int64, device=dev)
     n_blk = torch.zeros(chains, dtype=torch.int64, device=dev)
     G = torch.empty(chains, ctx.N, ctx.N, dtype=torch.float64, device=dev)
@@ -124,14 +133,14 @@ def run_dqmc(Lx, L, n_s=8, chains=32, sweeps=500, precision="fp64", dtau=0.1, la
 
 def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision="fp32", dtau=0.1, lam=1.0,
         omega0=1.0, sweep_delta=0.3, seed=0x1802061774, rounds=2, device="cuda", rank=0, world=1, wolff=0,
-        train_source="self", dqmc_therm=50, dqmc_gap=5):
+        train_source="self", dqmc_therm=50, dqmc_gap=5, init="gaussian"):
     dev = torch.device(device)
     seed = seed + rank
     ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
                   sweep_delta=sweep_delta, seed=seed, max_fields=chains, device=dev)
     ctx.set_wolff(wolff)  # Wolff cluster updates between the colours of every sweep
     N = Lx * Lx
-    x = torch.from_numpy(inputs.gaussian_fields(chains, Lx, Lx, L, sigma=1.0, seed=seed)).to(dev)
+    x = initial_fields(init, chains, Lx, L, lam / omega0 ** 2, seed).to(dev)
     J = torch.tensor([0.0, omega0 ** 2 / 4 + 1.0 / (2 * dtau ** 2), 0.1, 0.0, 0.0, omega0 ** 2 / 2],
                      dtype=torch.float64, device=dev)
     t0 = time.perf_counter()
@@ -225,7 +234,7 @@ def power_law_exponent(sizes, values):
 
 def autocorrelation_study(sizes, beta=4.1, dtau=0.1, lam=1.0, omega0=0.5, n_s=10, chains=64, steps=2000,
                           sweeps=10, train=1024, seed=0x1802061774, device="cuda", rank=0, world=1, nblock=4,
-                          wolff=1):
+                          wolff=1, init="cdw", dqmc_therm=200):
     """Autocorrelation time tau_L of S(pi, pi) against the linear size for DQMC and SLMC with the
     paper's Monte Carlo steps (Sec. "Results"): a DQMC step is a sweep of local updates plus
     `nblock` block updates; an SLMC step is a sweep of local updates of E_eff plus `wolff` Wolff
@@ -238,10 +247,10 @@ def autocorrelation_study(sizes, beta=4.1, dtau=0.1, lam=1.0, omega0=0.5, n_s=10
     rows = []
     for Lx in sizes:
         d = run_dqmc(Lx, L, min(n_s, L), chains, steps, "fp64", dtau=dtau, lam=lam, omega0=omega0, seed=seed,
-                     device=device, rank=rank, world=world, nblock=nblock)
+                     device=device, rank=rank, world=world, nblock=nblock, init=init)
         m = run(Lx, L, min(n_s, L), chains, train, max(4, steps // sweeps), sweeps, "fp32", dtau=dtau, lam=lam,
                 omega0=omega0, seed=seed, rounds=2, device=device, rank=rank, world=world, wolff=wolff,
-                train_source="dqmc")
+                train_source="dqmc", dqmc_therm=dqmc_therm, init=init)
         s_ms = 1e3 * m["production_seconds"] / m["updates"] / sweeps  # per SLMC step
         rows.append({"Lx": Lx, "dqmc_tau_steps": d["S_pipi_tau_int_sweeps"], "dqmc_ms_per_step": d["ms_per_sweep"],
                      "dqmc_ms_per_independent": d["ms_per_independent_sample"], "dqmc_S": d["S_pipi_mean"],
@@ -256,6 +265,7 @@ def autocorrelation_study(sizes, beta=4.1, dtau=0.1, lam=1.0, omega0=0.5, n_s=10
     return {"study": "autocorrelation", "beta": beta, "L": L, "dtau": dtau, "g": lam, "omega0": omega0,
             "lambda_dimensionless": lam ** 2 / (8.0 * omega0 ** 2), "chains": chains * world, "steps": steps,
             "sweeps_per_update": sweeps, "dqmc_block_updates_per_step": nblock, "wolff_per_sweep": wolff,
+            "init": init, "slmc_training_dqmc_thermalisation": dqmc_therm,
             "sizes": rows, "exponents": fit}
 
 
@@ -284,6 +294,8 @@ def main():
                     help="comma-separated linear sizes: tau_L of S(pi,pi) for DQMC and SLMC (paper's MC steps)")
     ap.add_argument("--beta", type=float, default=4.1, help="--autocorr: inverse temperature")
     ap.add_argument("--steps", type=int, default=2000, help="--autocorr: MC steps per method and size")
+    ap.add_argument("--init", default=None, choices=["gaussian", "cdw"],
+                    help="starting fields (default gaussian; cdw for --autocorr)")
     ap.add_argument("--sweep-delta", type=float, default=None,
                     help="proposal width (default 0.3 for E_eff sweeps, 0.5 for DQMC sweeps)")
     a = ap.parse_args()
@@ -299,16 +311,19 @@ def main():
         res = autocorrelation_study([int(v) for v in a.autocorr.split(",")], beta=a.beta, lam=a.lam,
                                     omega0=a.omega0, n_s=a.n_s, chains=a.chains, steps=a.steps, sweeps=a.sweeps,
                                     train=a.train, seed=a.seed, device="cuda:%d" % local, rank=rank, world=world,
-                                    nblock=a.dqmc_block if a.dqmc_block else 4, wolff=a.wolff if a.wolff else 1)
+                                    nblock=a.dqmc_block if a.dqmc_block else 4, wolff=a.wolff if a.wolff else 1,
+                                    init=a.init or "cdw", dqmc_therm=a.dqmc_therm)
     elif a.dqmc_only:
         res = run_dqmc(a.Lx, a.L, a.n_s, a.chains, a.updates, "fp64", lam=a.lam, omega0=a.omega0,
                        sweep_delta=0.5 if a.sweep_delta is None else a.sweep_delta, seed=a.seed,
-                       device="cuda:%d" % local, rank=rank, world=world, nblock=a.dqmc_block)
+                       device="cuda:%d" % local, rank=rank, world=world, nblock=a.dqmc_block,
+                       init=a.init or "gaussian")
     else:
         res = run(a.Lx, a.L, a.n_s, a.chains, a.train, a.updates, a.sweeps, a.precision, rounds=a.rounds,
                   device="cuda:%d" % local, rank=rank, world=world, wolff=a.wolff, lam=a.lam, omega0=a.omega0,
                   seed=a.seed, sweep_delta=0.3 if a.sweep_delta is None else a.sweep_delta,
-                  train_source=a.train_source, dqmc_therm=a.dqmc_therm, dqmc_gap=a.dqmc_gap)
+                  train_source=a.train_source, dqmc_therm=a.dqmc_therm, dqmc_gap=a.dqmc_gap,
+                  init=a.init or "gaussian")
     if rank == 0:
         print(json.dumps(res))
     if world > 1:
