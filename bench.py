@@ -260,7 +260,9 @@ def config_of(wl, args, precision):
             "n_s": wl.n_s, "chains_per_gpu": args.fields or wl.nfields, "nsweeps": args.nsweeps,
             "sub_batches": getattr(args, "sub_batches", 0) or 3,
             "slice_groups": getattr(args, "slice_groups", 0) or (4 if wl.N <= 256 else 1),
-            "precision": precision, "global_batch": (args.fields or wl.nfields) * args.gpus,
+            "precision": precision,
+            "fp64_slices": "dense" if getattr(args, "dense_slices", False) else "separable",
+            "global_batch": (args.fields or wl.nfields) * args.gpus,
             "parallelism": "replicas x%d" % args.gpus,
             "l2": "inputs larger than L2 (fields %.0f MB + workspace), no flush" % (
                 (args.fields or wl.nfields) * wl.N * wl.L * 8 / 1e6)}
@@ -300,6 +302,8 @@ def run_gpu(args):
             c.set_sub_batch_priorities(args.sub_priorities)
         if args.qr_cluster:
             c.set_qr_cluster(args.qr_cluster)
+        if args.dense_slices:
+            c.set_dense_slices(1)
         return c
 
     def setup(ctx):
@@ -696,6 +700,7 @@ def main():
     ap.add_argument("--slice-groups", type=int, default=0, help="FP32 slice kernel column groups (0 = default)")
     ap.add_argument("--sub-priorities", type=int, default=-1, help="descending sub-batch stream priorities (1/0)")
     ap.add_argument("--qr-cluster", type=int, default=0, help="CTAs per field of the QR (0 = automatic, 1, 2, 4)")
+    ap.add_argument("--dense-slices", action="store_true", help="FP64 mode: dense exp(-dtau K) slice products")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "slmc":
         args.warmup = 3

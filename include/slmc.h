@@ -260,6 +260,15 @@ SLMC_API int slmc_set_sub_batch_priorities(slmc_ctx* ctx, int on);
  * split over the CTAs. Results are bit-identical for every value. */
 SLMC_API int slmc_set_qr_cluster(slmc_ctx* ctx, int ctas);
 
+/* FP64 mode. dense = 0 (default): the slice products go through the separable
+ * exp(-dtau K) = e^{dtau mu} E_x kron E_y of the periodic lattice [Suppl. Eq. (S2); the x and
+ * y hoppings commute], N (Lx + Ly) FMAs per column and slice; dense = 1: dense N^2 products
+ * with exp(-dtau K). Both agree to rounding; lattices with a side above 32 always take the
+ * dense products. The reduced-precision modes always use their dense F = E - I kernels and
+ * the DQMC updates always use the separable factors. SLMC_ERR_ARG for values other than 0
+ * and 1. */
+SLMC_API int slmc_set_dense_slices(slmc_ctx* ctx, int dense);
+
 /* Thread layout of the FP32 slice kernel: 1: one column group of 256 row threads; 2: two such
  * groups (512 threads); 4 (N <= 256): four column groups of 64 row threads, each thread up to
  * 4 rows x 8 columns. 0 (default) selects 4 for N <= 256 and 1 above. The 256-thread layouts (about 104 KB of shared memory

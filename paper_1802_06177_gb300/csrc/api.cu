@@ -696,6 +696,12 @@ int slmc_set_qr_cluster(slmc_ctx* c, int ctas) {
     return SLMC_OK;
 }
 
+int slmc_set_dense_slices(slmc_ctx* c, int dense) {
+    if (!c || dense < 0 || dense > 1) return SLMC_ERR_ARG;
+    c->dense_slices = dense;
+    return SLMC_OK;
+}
+
 int slmc_set_sub_batch_priorities(slmc_ctx* c, int on) {
     if (!c || on < 0 || on > 1) return SLMC_ERR_ARG;
     if (on && c->nsub_avail == 0) return SLMC_ERR_UNSUPPORTED;

@@ -269,3 +269,24 @@ def test_qr_cluster_bit_identical(Lx, Ly, L, n_s, nf, precision):
     for f in range(nf):
         ref = fermion_logdet(p, x[f], E=E, want_G=False)[0]
         assert abs(res[0][1][f] - ref) <= tol, (f, res[0][1][f], ref)
+
+
+@pytest.mark.parametrize("Lx,Ly,L,n_s", [(16, 16, 40, 8), (6, 4, 30, 7), (2, 5, 12, 5)])
+def test_fp64_separable_and_dense_slices_agree(Lx, Ly, L, n_s):
+    # FP64 slices through exp(-dtau K) = e^{dtau mu} E_x kron E_y against the dense products
+    # (mu != 0 exercises the scalar factor), both against the oracle.
+    x = inputs.mixed_fields(4, Lx, Ly, L, seed=Lx + 7 * L)
+    out = {}
+    for dense in (0, 1):
+        ctx = make_ctx(Lx, L, n_s, Ly=Ly, max_fields=4, mu=0.3)
+        ctx.set_dense_slices(dense)
+        G, lndet, sign = ctx.greens(cuda(x))
+        out[dense] = (G.cpu().numpy(), lndet.cpu().numpy(), sign.cpu().numpy())
+    assert np.abs(out[0][1] - out[1][1]).max() <= 1e-10
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-11
+    p = HolsteinParams(Lx, Ly, L, n_s=n_s, mu=0.3)
+    E = exp_hopping(Lx, Ly, 1.0, 0.3, 0.1)
+    for f in range(4):
+        l_ref, s_ref, G_ref = fermion_logdet(p, x[f], E=E)
+        assert abs(out[0][1][f] - l_ref) <= TOL_LNDET_FP64 and out[0][2][f] == s_ref
+        assert np.abs(out[0][0][f] - G_ref).max() <= 1e-9
