@@ -23,6 +23,8 @@ pytestmark = pytest.mark.gpu
     (2, 2, 2, 1, 3, 2, 64),    # recomputation at every slice
     (6, 6, 20, 10, 1, 4, 2),   # two internal batches of chains
     (8, 6, 16, 5, 1, 2, 64),
+    (13, 13, 6, 3, 1, 1, 64),  # N = 169: G no longer fits in shared memory (kept in global memory)
+    (16, 16, 4, 2, 1, 1, 64),  # N = 256, the benchmark lattice
 ])
 def test_dqmc_sweeps_reproduce_oracle(Lx, Ly, L, n_s, nsweeps, nblock, max_fields):
     nf, seed, delta, sweep0 = 3, 0xD0C5EED, 0.7, 11
