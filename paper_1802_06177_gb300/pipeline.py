@@ -133,7 +133,7 @@ def run_dqmc(Lx, L, n_s=8, chains=32, sweeps=500, precision="fp64", dtau=0.1, la
 
 def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision="fp32", dtau=0.1, lam=1.0,
         omega0=1.0, sweep_delta=0.3, seed=0x1802061774, rounds=2, device="cuda", rank=0, world=1, wolff=0,
-        train_source="self", dqmc_therm=50, dqmc_gap=5, init="gaussian"):
+        train_source="self", dqmc_therm=50, dqmc_gap=5, init="gaussian", J0=None):
     dev = torch.device(device)
     seed = seed + rank
     ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
@@ -141,8 +141,8 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
     ctx.set_wolff(wolff)  # Wolff cluster updates between the colours of every sweep
     N = Lx * Lx
     x = initial_fields(init, chains, Lx, L, lam / omega0 ** 2, seed).to(dev)
-    J = torch.tensor([0.0, omega0 ** 2 / 4 + 1.0 / (2 * dtau ** 2), 0.1, 0.0, 0.0, omega0 ** 2 / 2],
-                     dtype=torch.float64, device=dev)
+    J = torch.tensor([0.0, omega0 ** 2 / 4 + 1.0 / (2 * dtau ** 2), 0.1, 0.0, 0.0, omega0 ** 2 / 2] if J0 is None
+                     else list(J0), dtype=torch.float64, device=dev)
     t0 = time.perf_counter()
     lnw, s = ctx.chain_init(x)
     ctx.set_update_counter(0)
@@ -185,7 +185,7 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
             del xp
     # production starts from the last self-generated configurations (inside the training
     # distribution); the initial Gaussian field is atypical for both weights
-    x = xp.contiguous()
+    x = (xp if xp is not None else x).contiguous()
     lnw, s = ctx.chain_init(x)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
@@ -208,7 +208,8 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
     series = (S_sum / (chains * world)).cpu().numpy()[therm:]
     res = {
         "lattice": "%dx%d" % (Lx, Lx), "N": N, "L": L, "beta": L * dtau, "n_s": n_s, "precision": precision,
-        "chains": chains * world, "processes": world, "training_configs": history[-1]["configs"],
+        "chains": chains * world, "processes": world,
+        "training_configs": history[-1]["configs"] if history else 0,
         "training_rounds": history,
         "updates": updates, "sweeps_per_update": sweeps,
         "S_pipi_mean": float(series.mean()), "S_pipi_err": binned_error(series),
@@ -269,6 +270,58 @@ def autocorrelation_study(sizes, beta=4.1, dtau=0.1, lam=1.0, omega0=0.5, n_s=10
             "sizes": rows, "exponents": fit}
 
 
+def crossings(sizes, temps, curves):
+    """Temperatures where the curves of consecutive sizes cross (linear interpolation between the
+    scanned temperatures where their difference changes sign)."""
+    out = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        d = [curves[b][k] - curves[a][k] for k in range(len(temps))]
+        for k in range(len(temps) - 1):
+            if d[k] == 0.0 or d[k] * d[k + 1] < 0.0:
+                f = d[k] / (d[k] - d[k + 1]) if d[k] != d[k + 1] else 0.0
+                out.append({"sizes": [a, b], "T": temps[k] + f * (temps[k + 1] - temps[k])})
+    return out
+
+
+def fss_scan(sizes, betas, dtau=0.1, lam=1.0, omega0=0.5, n_s=10, chains=64, updates=300, sweeps=10, train=1024,
+             dqmc_therm=300, seed=0x1802061774, device="cuda", rank=0, world=1, wolff=1):
+    """Finite-size scaling of the CDW structure factor (Sec. "Results", Fig. 3(a)): S(pi, pi) L^{-7/4}
+    against T for each linear size L, whose crossings estimate T_c (2D Ising: 2 beta/nu = 1/4). Per
+    size, E_eff is learned once from DQMC configurations at the middle inverse temperature (the
+    paper's training data); the cumulative updates at the other temperatures stay exact with those
+    couplings and only accept less often. Inverse temperatures are multiples of 2 dtau (the E_eff
+    checkerboard needs an even number of slices); every run starts from the CDW state."""
+    betas = sorted(betas)
+    Ls = [2 * max(1, int(round(b / (2.0 * dtau)))) for b in betas]
+    mid = Ls[len(Ls) // 2]
+    rows, curves, training = [], {}, {}
+    temps = [1.0 / (l * dtau) for l in Ls]
+    for Lx in sizes:
+        # DQMC fit, then one self-learning refinement (as in the autocorrelation study)
+        tr = run(Lx, mid, min(n_s, mid), chains, train, 4, sweeps, "fp32", dtau=dtau, lam=lam, omega0=omega0,
+                 seed=seed, rounds=2, device=device, rank=rank, world=world, wolff=wolff, train_source="dqmc",
+                 dqmc_therm=dqmc_therm, init="cdw")
+        training[Lx] = {"rms_resid": [h["rms_resid"] for h in tr["training_rounds"]], "J": tr["J_final"],
+                        "acceptance_at_training_beta": tr["acceptance"]}
+        curves[Lx] = []
+        for L, T in zip(Ls, temps):
+            m = run(Lx, L, min(n_s, L), chains, 0, updates, sweeps, "fp32", dtau=dtau, lam=lam, omega0=omega0,
+                    seed=seed + 7919 * L, rounds=0, device=device, rank=rank, world=world, wolff=wolff,
+                    init="cdw", J0=tr["J_final"])
+            y = m["S_pipi_mean"] * Lx ** (-1.75)
+            curves[Lx].append(y)
+            rows.append({"Lx": Lx, "L": L, "beta": L * dtau, "T": T, "S_pipi": m["S_pipi_mean"],
+                         "S_pipi_err": m["S_pipi_err"], "S_L_minus_7_4": y, "S_L_minus_7_4_err":
+                         m["S_pipi_err"] * Lx ** (-1.75), "S_halves": m["S_pipi_halves"],
+                         "tau_int_updates": m["S_pipi_tau_int_updates"], "acceptance": m["acceptance"],
+                         "production_seconds": m["production_seconds"]})
+    return {"study": "fss", "g": lam, "omega0": omega0, "lambda_dimensionless": lam ** 2 / (8.0 * omega0 ** 2),
+            "dtau": dtau, "chains": chains * world, "updates": updates, "sweeps_per_update": sweeps,
+            "wolff_per_sweep": wolff, "training_beta": mid * dtau, "training": training, "temperatures": temps,
+            "points": rows,
+            "crossings": crossings(list(sizes), temps, curves)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--Lx", type=int, default=24)
@@ -293,6 +346,8 @@ def main():
     ap.add_argument("--autocorr", default=None,
                     help="comma-separated linear sizes: tau_L of S(pi,pi) for DQMC and SLMC (paper's MC steps)")
     ap.add_argument("--beta", type=float, default=4.1, help="--autocorr: inverse temperature")
+    ap.add_argument("--fss", default=None, help="comma-separated linear sizes: S(pi,pi) L^-7/4 against T")
+    ap.add_argument("--betas", default="3.6,3.8,4.0,4.2,4.4,4.6", help="--fss: inverse temperatures")
     ap.add_argument("--steps", type=int, default=2000, help="--autocorr: MC steps per method and size")
     ap.add_argument("--init", default=None, choices=["gaussian", "cdw"],
                     help="starting fields (default gaussian; cdw for --autocorr)")
@@ -307,7 +362,12 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    if a.autocorr:
+    if a.fss:
+        res = fss_scan([int(v) for v in a.fss.split(",")], [float(v) for v in a.betas.split(",")], lam=a.lam,
+                       omega0=a.omega0, n_s=a.n_s, chains=a.chains, updates=a.updates, sweeps=a.sweeps,
+                       train=a.train, dqmc_therm=a.dqmc_therm, seed=a.seed, device="cuda:%d" % local, rank=rank,
+                       world=world, wolff=a.wolff if a.wolff else 1)
+    elif a.autocorr:
         res = autocorrelation_study([int(v) for v in a.autocorr.split(",")], beta=a.beta, lam=a.lam,
                                     omega0=a.omega0, n_s=a.n_s, chains=a.chains, steps=a.steps, sweeps=a.sweeps,
                                     train=a.train, seed=a.seed, device="cuda:%d" % local, rank=rank, world=world,

@@ -52,3 +52,12 @@ def test_autocorrelation_study_runs_both_methods():
         assert 0.0 <= r["dqmc_block_acceptance"] <= 1.0 and 0.0 <= r["slmc_acceptance"] <= 1.0
     assert set(res["exponents"]) == {"dqmc_tau_steps", "slmc_tau_steps", "dqmc_ms_per_independent",
                                      "slmc_ms_per_independent"}
+
+
+def test_fss_scan_runs():
+    require_gpu()
+    res = pipeline.fss_scan([2, 4], [0.8, 1.0, 1.2], chains=8, updates=6, sweeps=2, train=16, dqmc_therm=4)
+    assert res["training_beta"] == 1.0 and len(res["points"]) == 6
+    for pt in res["points"]:
+        assert math.isfinite(pt["S_pipi"]) and pt["S_pipi"] > 0.0 and 0.0 <= pt["acceptance"] <= 1.0
+        assert abs(pt["S_L_minus_7_4"] - pt["S_pipi"] * pt["Lx"] ** -1.75) < 1e-12

@@ -31,3 +31,14 @@ def test_power_law_exponent():
     sizes = [4, 6, 8, 12]
     assert abs(power_law_exponent(sizes, [3.0 * s ** 2.5 for s in sizes]) - 2.5) < 1e-12
     assert math.isnan(power_law_exponent([4], [1.0]))
+
+
+def test_crossings_of_scaled_curves():
+    from paper_1802_06177_gb300.pipeline import crossings
+    temps = [0.20, 0.25, 0.30]
+    curves = {4: [1.0, 0.8, 0.6], 8: [1.2, 0.8, 0.4], 12: [1.3, 0.9, 0.5]}
+    out = crossings([4, 8, 12], temps, curves)
+    assert out[0]["sizes"] == [4, 8] and abs(out[0]["T"] - 0.25) < 1e-12  # exact touch at a scanned point
+    assert all(c["sizes"] != [8, 12] for c in out)  # 12 stays above 8: no crossing
+    out = crossings([4, 8], temps, {4: [1.0, 0.8, 0.6], 8: [1.1, 0.75, 0.5]})
+    assert len(out) == 1 and 0.20 < out[0]["T"] < 0.25
