@@ -46,8 +46,9 @@ __global__ void __launch_bounds__(kThreads) k_dqmc_slices(double* __restrict__ x
                                                           uint32_t key1, uint32_t sweep, int chain0, int g_in_smem,
                                                           unsigned long long* __restrict__ n_acc) {
     extern __shared__ double dsm[];
+    constexpr int QMAX = (LMAX * LMAX + 31) / 32;  // columns per lane in the rank-1 update
     const int N = Lx * Ly;
-    const int f = blockIdx.x, tid = threadIdx.x;
+    const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t NN = (size_t)N * N;
     double* G = g_in_smem ? dsm : Gall + f * NN;
     double* p = g_in_smem ? dsm + NN : dsm;
@@ -123,14 +124,17 @@ __global__ void __launch_bounds__(kThreads) k_dqmc_slices(double* __restrict__ x
                 ++accepted;
             }
             __syncthreads();
-            int j = tid / N, k = tid - (tid / N) * N;
-            for (size_t idx = tid; idx < NN; idx += kThreads) {
-                G[idx] = fma(ac[j], rw[k], G[idx]);
-                k += kThreads;
-                while (k >= N) {
-                    k -= N;
-                    ++j;
-                }
+            // rank-1 update, one row per warp at a time: the row's coefficient is loaded once and
+            // the lane's entries of e_i - G[i, :] stay in registers (N <= LMAX^2 = 32 QMAX)
+            double r[QMAX];
+#pragma unroll
+            for (int q = 0; q < QMAX; ++q) r[q] = lane + 32 * q < N ? rw[lane + 32 * q] : 0.0;
+            for (int j = warp; j < N; j += kThreads / 32) {
+                const double cj = ac[j];
+                double* Gj = G + (size_t)j * N;
+#pragma unroll
+                for (int q = 0; q < QMAX; ++q)
+                    if (lane + 32 * q < N) Gj[lane + 32 * q] = fma(cj, r[q], Gj[lane + 32 * q]);
             }
             __syncthreads();
         }

@@ -137,6 +137,7 @@ __device__ __forceinline__ void circ_line(double* g, int base, int stride, int L
     double acc[LMAX];
 #pragma unroll
     for (int d = 0; d < LMAX; ++d) acc[d] = 0.0;
+#pragma unroll 2
     for (int m = 0; m < Ld; ++m) {
         const double v = in_sc ? g[base + m * stride] * in_sc[m * in_st] : g[base + m * stride];
 #pragma unroll
