@@ -54,3 +54,18 @@ def test_dqmc_counts_accumulate_and_need_two_slices():
     ctx1 = make_ctx(2, 1, 1, seed=3)
     with pytest.raises(SlmcError):
         ctx1.dqmc_sweep(cuda(inputs.mixed_fields(1, 2, 2, 1, seed=1)), 1)
+
+
+def test_dqmc_local_updates_are_fp64_in_every_precision_mode():
+    # the local updates and the recomputation of G run in FP64 whatever the context's precision
+    Lx, L, n_s, nf = 6, 20, 5, 3
+    x = inputs.mixed_fields(nf, Lx, Lx, L, seed=9)
+    out = []
+    for prec in ("fp64", "fp32"):
+        ctx = make_ctx(Lx, L, n_s, precision=prec, seed=4, sweep_delta=0.6, max_fields=nf)
+        xg = cuda(x.copy())
+        nl = torch.zeros(nf, dtype=torch.int64, device="cuda")
+        ctx.dqmc_sweep(xg, 2, sweep0=5, n_acc_local=nl)
+        torch.cuda.synchronize()
+        out.append((xg.cpu().numpy(), nl.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
