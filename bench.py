@@ -16,6 +16,10 @@ on the batch. value = ln det evaluations per second = chains / step time, in the
 precision mode (slice products in --precision, FP64 QR / D scales / LU / log-ratio).
 
 --impl reference times the CPU oracle (plain FP64 numpy) on the host cores instead.
+
+--mode dqmc measures the conventional DQMC updates instead (chain-sweeps/s, one chain per SM,
+12x12 / L = 120 by default) with the roofline of its local-update kernel; with --impl reference
+it times the DQMC oracle.
 """
 import argparse
 import json
@@ -202,6 +206,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.mode == "dqmc":
+        return run_reference_dqmc(args)
     from paper_1802_06177_gb300.workloads import WORKLOADS
     wl = WORKLOADS[args.workload]
     nproc = min(16, os.cpu_count() or 1)
@@ -579,6 +585,38 @@ def _oracle_dqmc_worker(args):
 
 DQMC_METRIC = "DQMC sweeps (local updates, fast ratio + Sherman-Morrison + wrapping) per second on one GB300"
 DQMC_UNIT = "chain-sweeps/s"
+
+
+def run_reference_dqmc(args):
+    """The DQMC oracle on the host cores (one chain per core, one sweep each per step), with the
+    metric, unit and config of the DQMC mode's GPU line."""
+    from paper_1802_06177_gb300.workloads import WORKLOADS
+    wl = WORKLOADS[args.workload]
+    nproc = min(16, os.cpu_count() or 1)
+    pool = oracle_pool(nproc)
+    seed = wl.seed
+    done, wall = 0, 0.0
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        pool.map(_oracle_dqmc_worker, [(wl.name, c, seed) for c in range(nproc)])
+        if s >= args.warmup:
+            done += nproc
+            wall += time.perf_counter() - t0
+    pool.close()
+    value = done / wall
+    sample = "per step: %d chains (one per core, 1 BLAS thread each), one oracle DQMC sweep each on %s" % (
+        nproc, wl.name)
+    line = {"impl": "reference", "metric": DQMC_METRIC, "value": value, "unit": DQMC_UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "model": "holstein_2d", "N": wl.N, "Lx": wl.Lx, "L": wl.L,
+                       "n_s": wl.n_s, "chains_per_step": nproc, "block_updates_per_sweep": 0, "sweep_delta": 0.5,
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": DQMC_UNIT, "cores": nproc, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": DQMC_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "mode": "dqmc"}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_dqmc(args):
