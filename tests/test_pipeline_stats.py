@@ -42,3 +42,17 @@ def test_crossings_of_scaled_curves():
     assert all(c["sizes"] != [8, 12] for c in out)  # 12 stays above 8: no crossing
     out = crossings([4, 8], temps, {4: [1.0, 0.8, 0.6], 8: [1.1, 0.75, 0.5]})
     assert len(out) == 1 and 0.20 < out[0]["T"] < 0.25
+
+
+def test_cdw_initial_fields_sit_at_the_double_well_minima():
+    import numpy as np
+    from paper_1802_06177_gb300.pipeline import initial_fields
+    alpha, Lx, L = 4.0, 4, 10
+    x = initial_fields("cdw", 3, Lx, L, alpha, seed=1).numpy()
+    i = np.arange(Lx * Lx)
+    stag = np.where(((i % Lx) + (i // Lx)) % 2 == 0, 1.0, -1.0)
+    assert x.shape == (3, Lx * Lx, L)
+    assert abs((x * stag[None, :, None]).mean() - alpha) < 0.05  # staggered pattern at +-alpha
+    assert abs(x.std(axis=(0, 2)).mean() - 0.3) < 0.05           # noise 0.3 per site
+    g = initial_fields("gaussian", 3, Lx, L, alpha, seed=1).numpy()
+    assert abs(g.mean()) < 0.1 and abs(g.std() - 1.0) < 0.1
