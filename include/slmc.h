@@ -67,8 +67,17 @@ extern "C" {
  * log-ratio are FP64 in all modes. */
 #define SLMC_PREC_FP64 0    /* FP64 FMA */
 #define SLMC_PREC_FP32 1    /* FP32 FMA (SIMT) */
-#define SLMC_PREC_TF32X3 2  /* tensor cores, 3 x TF32 split products, FP32 accumulation */
-#define SLMC_PREC_BF16X9 3  /* tensor cores, 9 x BF16 split products, FP32 accumulation */
+/* Tensor cores (tcgen05), the literature's split TF32: two TF32 pieces per operand, three
+ * products accumulated in FP32. The tensor cores' FP32 accumulation truncates and its error
+ * adds up over the slices of a chain: this mode misses |d ln w| <= 1e-4 (about 2e-3 in ln det
+ * at 16x16, beta = 16). */
+#define SLMC_PREC_TF32X3 2
+/* Tensor cores (tcgen05), exact sliced BF16: F = E - I in four and Y in three 7-bit fixed-point
+ * BF16 slices (per-row / per-column powers of two), the nine products with a + b <= 3 summed
+ * per level a + b into FP32 accumulators whose every partial sum is an integer below 2^24
+ * (bound checked at slmc_init), so the accumulation is exact; |d ln det| ~ 5e-6 at 16x16,
+ * beta = 16. A whole stabilisation group runs in one launch with Y resident on chip. */
+#define SLMC_PREC_BF16X9 3
 
 /* Model, discretisation and algorithm parameters. */
 typedef struct slmc_params {
@@ -100,7 +109,8 @@ SLMC_API const char* slmc_status_string(int status);
  * internal batch (calls with more fields are processed in batches of max_fields).
  * Workspace is about (6 N^2 + 4 N L) * 8 bytes per field. On success *out owns it.
  * Errors: SLMC_ERR_ARG (p or out NULL, sizes out of range), SLMC_ERR_UNSUPPORTED
- * (N > 1024), SLMC_ERR_NOMEM, SLMC_ERR_CUDA. */
+ * (N > 1024; in SLMC_PREC_BF16X9, slices of exp(-dtau K) - I that could let a tensor-core partial
+ * sum exceed 2^24; the worst case allows that only for N > 819), SLMC_ERR_NOMEM, SLMC_ERR_CUDA. */
 SLMC_API int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out);
 
 /* Frees the context and its workspace (synchronises the device first). NULL is a no-op. */

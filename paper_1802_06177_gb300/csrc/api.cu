@@ -133,8 +133,10 @@ int logdet_run(slmc_ctx* c, slmc_ctx* v, const double* x, int nf, double* lndet,
     if (v->p.precision != SLMC_PREC_FP64) SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_scales(v, x, nf, s));
     for (int l0 = 0; l0 < v->L; l0 += v->p.n_s) {
         const int nsl = std::min(v->p.n_s, v->L - l0);
-        if (v->p.precision == SLMC_PREC_TF32X3 || v->p.precision == SLMC_PREC_BF16X9)
+        if (v->p.precision == SLMC_PREC_TF32X3)
             SLMC_LAUNCH(SLMC_PROF_SLICE, slmc::tc_launches(nsl), s, slmc::tc_slice_group(v, x, nf, l0, nsl, s));
+        else if (v->p.precision == SLMC_PREC_BF16X9)
+            SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::tcx_slice_group(v, nf, l0, nsl, s));
         else
             SLMC_LAUNCH(SLMC_PROF_SLICE, 1, s, slmc::slice_group(v, x, nf, l0, nsl, s));
         if (v->p.qr_mode == SLMC_QR_PIVOTED) {
@@ -176,6 +178,10 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
     v.lo_kidx = c->lo_kidx;
     v.lo_val = c->lo_val;
     v.lo_S = c->lo_S;
+    v.tcx_F = c->tcx_F;
+    v.tcx_eF = c->tcx_eF;
+    v.tcx_npad = c->tcx_npad;
+    v.tcx_mapF = c->tcx_mapF;
     v.sc32 = c->sc32 ? c->sc32 + F0 * c->L * N : nullptr;
     v.Y = c->Y + F0 * NN;
     v.QR = c->QR + F0 * NN;
@@ -204,7 +210,7 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
 }
 
 int logdet_batch(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, double* G, cudaStream_t s) {
-    const bool tc = c->p.precision == SLMC_PREC_TF32X3 || c->p.precision == SLMC_PREC_BF16X9;
+    const bool tc = c->p.precision == SLMC_PREC_TF32X3;  // per-slice workspace not split into views
     const int nsub = std::min(c->nsub, nf / kMinSubFields);
     if (nsub < 2 || tc) return logdet_run(c, c, x, nf, lndet, sign, G, s);
     const size_t NL = (size_t)c->N * c->L, NN = (size_t)c->N * c->N;
@@ -241,7 +247,7 @@ void free_ctx(slmc_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
     if (c->prof_base) cudaEventDestroy(c->prof_base);
-    void* bufs[] = {c->E64, c->Einv64, c->kron, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->Ftf, c->Fbf, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
+    void* bufs[] = {c->E64, c->Einv64, c->kron, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->tcx_F, c->tcx_eF, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
                     c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err, c->dctr,
                     c->wolff_sites, c->dq_stack,
                     c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
@@ -309,8 +315,12 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
         alloc(&c->lo_val, (size_t)c->lo_S * sizeof(float));
     }
     if (p->precision != SLMC_PREC_FP64) alloc(&c->sc32, F * L * N * sizeof(float));
-    if (p->precision == SLMC_PREC_TF32X3) alloc(&c->Ftf, 2 * NN * sizeof(uint32_t));
-    if (p->precision == SLMC_PREC_BF16X9) alloc(&c->Fbf, 3 * NN * sizeof(uint16_t));
+    if (p->precision == SLMC_PREC_BF16X9) {
+        int mt = 0, nt = 0, npad = 0;
+        slmc::tcx_geometry(c->N, &mt, &nt, &npad);
+        alloc(&c->tcx_F, slmc::tcx_F_bytes(c->N));
+        alloc(&c->tcx_eF, (size_t)mt * 128 * sizeof(int));
+    }
     alloc(&c->Y, F * NN * sizeof(double));
     alloc(&c->QR, F * NN * sizeof(double));
     alloc(&c->U, F * NN * sizeof(double));
@@ -333,11 +343,11 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     if (ok && cudaMemset(c->dctr, 0, sizeof(unsigned long long)) != cudaSuccess) ok = false;
     alloc(&c->wolff_sites, sizeof(unsigned long long));
     if (ok && cudaMemset(c->wolff_sites, 0, sizeof(unsigned long long)) != cudaSuccess) ok = false;
-    const bool tc = p->precision == SLMC_PREC_TF32X3 || p->precision == SLMC_PREC_BF16X9;
+    const bool tc = p->precision == SLMC_PREC_TF32X3;
     if (tc) {
         size_t es = 0;
         int np = 0;
-        slmc::tc_geometry(c->N, p->precision, &c->tc_npad, &c->tc_nt, &es, &np);
+        slmc::tc_geometry(c->N, &c->tc_npad, &c->tc_nt, &es, &np);
         const size_t Np = c->tc_npad;
         alloc(&c->tc_F, np * Np * Np * es);
         for (int b = 0; b < 2; ++b) {
@@ -377,6 +387,14 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
         cudaDeviceSynchronize() != cudaSuccess) {
         free_ctx(c);
         return SLMC_ERR_CUDA;
+    }
+    if (p->precision == SLMC_PREC_BF16X9) {
+        const cudaError_t e = slmc::tcx_init(c, nullptr);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_ctx(c);
+            return e == cudaErrorNotSupported ? SLMC_ERR_UNSUPPORTED : SLMC_ERR_CUDA;
+        }
     }
     *out = c;
     return SLMC_OK;
@@ -491,7 +509,7 @@ int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int n
     // its updates (sweeps, E_eff, ln w with G, Eq. (6), S) on its own forked stream, so the sweeps of one
     // sub-batch overlap the determinants of another.
     SLMC_TRY(for_batches(c, n, [&](int f0, int nf) {
-        const bool tc = c->p.precision == SLMC_PREC_TF32X3 || c->p.precision == SLMC_PREC_BF16X9;
+        const bool tc = c->p.precision == SLMC_PREC_TF32X3;
         int nsub = std::min(c->nsub, nf / kMinSubFields);
         if (nsub < 2 || tc) nsub = 1;
         if (nsub > 1) SLMC_CK(cudaEventRecord(c->sub_fork, s));

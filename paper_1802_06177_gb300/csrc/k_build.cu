@@ -3,9 +3,7 @@
 //   E_ij = (1/N) sum_k cos(k . (r_i - r_j)) exp(-dtau eps_k),  eps_k = -2t (cos kx + cos ky) - mu,
 // k = 2 pi (nx/Lx, ny/Ly). Phases are formed as exact rationals and evaluated with cospi.
 // Reduced-precision modes multiply by F = E - I (identity added exactly afterwards); its
-// FP32 copy, the stencil of its FP32 rounding residual and the tensor-core operand splits are
-// derived from the FP64 matrix.
-#include <cuda_bf16.h>
+// FP32 copy and the stencil of its FP32 rounding residual are derived from the FP64 matrix.
 
 #include "slmc_internal.cuh"
 
@@ -45,36 +43,11 @@ __global__ void k_kron_tables(double* __restrict__ tab, int Lx, int Ly, double d
     tab[q * slmc::kKronTab + d + Ld] = acc / Ld;
 }
 
-__device__ __forceinline__ uint32_t to_tf32(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return r;
-}
-
-__global__ void k_split_F(const double* __restrict__ E, float* __restrict__ F32, uint32_t* __restrict__ Ftf,
-                          uint16_t* __restrict__ Fbf, int N) {
+__global__ void k_split_F(const double* __restrict__ E, float* __restrict__ F32, int N) {
     const int NN = N * N;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= NN) return;
-    const double fd = E[idx] - ((idx % (N + 1) == 0) ? 1.0 : 0.0);
-    const float v = (float)fd;
-    F32[idx] = v;
-    if (Ftf) {
-        const uint32_t hi = to_tf32(v);
-        const uint32_t lo = to_tf32(v - __uint_as_float(hi));
-        Ftf[idx] = hi;
-        Ftf[NN + idx] = lo;
-    }
-    if (Fbf) {
-        const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
-        const float r1 = v - __bfloat162float(b0);
-        const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-        const float r2 = r1 - __bfloat162float(b1);
-        const __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
-        Fbf[idx] = __bfloat16_as_ushort(b0);
-        Fbf[NN + idx] = __bfloat16_as_ushort(b1);
-        Fbf[2 * NN + idx] = __bfloat16_as_ushort(b2);
-    }
+    F32[idx] = (float)(E[idx] - ((idx % (N + 1) == 0) ? 1.0 : 0.0));
 }
 
 // F is translation invariant on the periodic lattice (E_ij depends on r_i - r_j only), so its
@@ -119,7 +92,7 @@ cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s) {
     if (c->Einv64)  // exp(+dtau K): the same plane-wave sum with -dtau
         k_hopping_exp<<<(NN + 255) / 256, 256, 0, s>>>(c->Einv64, c->p.Lx, c->p.Ly, -c->p.dtau, c->p.t, c->p.mu);
     if (c->kron) k_kron_tables<<<4, kKronMaxLine, 0, s>>>(c->kron, c->p.Lx, c->p.Ly, 2.0 * c->p.dtau * c->p.t);
-    k_split_F<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->F32, c->Ftf, c->Fbf, N);
+    k_split_F<<<(NN + 255) / 256, 256, 0, s>>>(c->E64, c->F32, N);
     if (c->lo_kidx) {
         int* sel = c->lo_kidx + (size_t)c->lo_S * N;
         k_lo_select<<<1, 1024, 0, s>>>(c->E64, N, c->lo_S, sel, c->lo_val);

@@ -39,9 +39,6 @@ struct slmc_ctx {
     float* lo_val;   // [S] FP32 rounding residual of F on the S largest-|F| displacements
     int lo_S;        // stencil size min(kLoStencil, N)
     float* sc32;     // [max_fields][L][N] slice scales exp(-dtau lambda x), FP64-computed, rounded to FP32
-    // tensor-core operand splits of F (filled only in the matching precision modes)
-    uint32_t* Ftf;   // [2][N][N] TF32 hi / lo bit patterns
-    uint16_t* Fbf;   // [3][N][N] BF16 three-way split
     // Per-field workspace, [max_fields][N][N] column-major unless stated.
     double* Y;       // slice-group product; reused for M in the final step
     double* QR;      // packed pivoted-QR output; reused for G in the cumulative update
@@ -71,8 +68,14 @@ struct slmc_ctx {
     int tune_slice_groups;
     int tune_qr_cluster;    // CTAs per field of the QR / formation of Q (0 = by field count)
     int num_sms;            // multiprocessors of the device
-    // Tensor-core slice path (SLMC_PREC_TF32X3 / BF16X9): operand pieces of F and of the
-    // running slice product (ping/pong), FP32 copies of it, and their TMA descriptors.
+    // Exact sliced tensor-core slice path (SLMC_PREC_BF16X9): fixed-point BF16 slices of F
+    // [4][128 MT][tcx_npad], their row exponents and the TMA descriptor of the slices.
+    void* tcx_F;
+    int* tcx_eF;
+    int tcx_npad;
+    CUtensorMap tcx_mapF;
+    // Split-TF32 slice path (SLMC_PREC_TF32X3): operand pieces of F and of the running slice
+    // product (ping/pong), FP32 copies of it, and their TMA descriptors.
     int tc_npad, tc_nt;
     void* tc_F;         // [pieces][Npad][Npad]
     void* tc_p[2];      // [pieces][max_fields * N][Npad]
@@ -182,8 +185,12 @@ cudaError_t build_hopping_exp(slmc_ctx* c, cudaStream_t s);
 cudaError_t slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s);
 cudaError_t tc_slice_group(slmc_ctx* c, const double* x, int nf, int l0, int nsl, cudaStream_t s);
 cudaError_t tc_init(slmc_ctx* c, cudaStream_t s);
+void tcx_geometry(int N, int* mt, int* nt, int* npad);
+size_t tcx_F_bytes(int N);
+cudaError_t tcx_init(slmc_ctx* c, cudaStream_t s);
+cudaError_t tcx_slice_group(slmc_ctx* c, int nf, int l0, int nsl, cudaStream_t s);
 cudaError_t slice_scales(slmc_ctx* c, const double* x, int nf, cudaStream_t s);
-void tc_geometry(int N, int precision, int* npad, int* nt, size_t* piece_bytes, int* npieces);
+void tc_geometry(int N, int* npad, int* nt, size_t* piece_bytes, int* npieces);
 int tc_launches(int nsl);
 cudaError_t t_update_tiled(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s);

@@ -196,7 +196,7 @@ def test_mixed_both_qr_modes(qr_mode):
     assert np.array_equal(sign.cpu().numpy(), s_ref)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x9"])
 def test_sub_batch_split_is_bit_identical_and_profiled(precision):
     """Splitting a batch over 1-4 forked streams changes only which stream runs a field:
     ln det, sign and G are bit-identical; the profiler counts every field once per launch
