@@ -279,6 +279,20 @@ SLMC_API int slmc_set_qr_cluster(slmc_ctx* ctx, int ctas);
  * and 1. */
 SLMC_API int slmc_set_dense_slices(slmc_ctx* ctx, int dense);
 
+/* How the stabilisation updates T <- (D^-1 R) P^T T after each pivoted QR (the T factor of the
+ * UDT chain; the paper defers stabilisation to the DQMC literature), in every precision mode:
+ *   path = 0 (default): on the tensor cores, FP64-accurate. D^-1 R and P^T T are cut into seven
+ *            7-bit fixed-point BF16 slices (a power of two per row and per column), the 28 slice
+ *            products with a + b <= 6 are summed per level in FP32 accumulators that provably
+ *            hold every partial sum exactly (the bound is checked per row on the actual slices;
+ *            a 128-row tile whose bound could exceed 2^24 is computed with FP64 FMAs instead),
+ *            and each entry is rounded once to FP64. Entries differ from the FP64 product by
+ *            below 2^-48 of their row and column scales.
+ *   path = 1: FP64 FMAs (tiled triangular GEMM).
+ *   path = 2: the tensor-core kernel with every tile on its FP64 fallback (for tests).
+ * The DQMC updates always use path 1. Errors: SLMC_ERR_ARG for other values. */
+SLMC_API int slmc_set_tupdate_path(slmc_ctx* ctx, int path);
+
 /* Thread layout of the FP32 slice kernel: 1: one column group of 256 row threads; 2: two such
  * groups (512 threads); 4 (N <= 256): four column groups of 64 row threads, each thread up to
  * 4 rows x 8 columns. 0 (default) selects 4 for N <= 256 and 1 above. The 256-thread layouts (about 104 KB of shared memory
@@ -409,11 +423,14 @@ SLMC_API int slmc_autotune(const slmc_params* p, int ntune, double tol, slmc_tun
  *   p       model parameters as for slmc_init; precision SLMC_PREC_FP64 or SLMC_PREC_FP32
  *   x, n, lndet, sign  as for slmc_logdet (device pointers, results on `stream`)
  * Size limit: the 16 MiB must hold E, F and at least one field's workspace, about
- * 52 N^2 + 300 N bytes, so N <= 560 (a 16x16 or 20x20 lattice, not 24x24); larger N returns
+ * 52 N^2 + 300 N bytes (+ 2 KB), so N <= 560 (a 16x16 or 20x20 lattice, not 24x24); larger N returns
  * SLMC_ERR_UNSUPPORTED before anything is enqueued. Fields beyond the array's capacity are
  * processed in consecutive batches.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- * and caches it; make that first call before any stream capture. All calls share the array
+ * and caches it; make that first call before any stream capture. A device reset
+ * (cudaDeviceReset) or a new primary context on that device invalidates the cached address:
+ * do not use this entry point on that device afterwards in the same process. The arithmetic
+ * is that of slmc_logdet (FP64 slices through the separable factors for sides <= 32). All calls share the array
  * and it keeps the last call's contents; each call clears the error word it uses on the
  * stream. Calls that overlap on the GPU race on the array: serialise them. Device-side
  * failures are reported only through the outputs (lndet NaN, sign 0). */

@@ -151,7 +151,7 @@ int logdet_run(slmc_ctx* c, slmc_ctx* v, const double* x, int nf, double* lndet,
             const bool q32 = v->p.precision != SLMC_PREC_FP64 && l0 + nsl < v->L;
             SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::form_q_blocked(v, nf, q32, s));
         }
-        SLMC_LAUNCH(SLMC_PROF_TUPDATE, 1, s, slmc::t_update_tiled(v, nf, s));
+        SLMC_LAUNCH(SLMC_PROF_TUPDATE, slmc::t_update_launches(v), s, slmc::t_update(v, nf, s));
     }
     SLMC_LAUNCH(SLMC_PROF_FINAL, 2, s, slmc::final_logdet(v, nf, lndet, sign, s));
     if (G) SLMC_LAUNCH(SLMC_PROF_GREENS, 1, s, slmc::final_greens(v, nf, G, s));
@@ -182,6 +182,17 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
     v.tcx_eF = c->tcx_eF;
     v.tcx_npad = c->tcx_npad;
     v.tcx_mapF = c->tcx_mapF;
+    v.tt_A = c->tt_A;
+    v.tt_B = c->tt_B;
+    v.tt_eA = c->tt_eA;
+    v.tt_eB = c->tt_eB;
+    v.tt_flag = c->tt_flag;
+    v.tt_mpad = c->tt_mpad;
+    v.tt_npad = c->tt_npad;
+    v.tt_path = c->tt_path;
+    v.tt_mapA = c->tt_mapA;
+    v.tt_mapB = c->tt_mapB;
+    v.fbase = c->fbase + f0;
     v.sc32 = c->sc32 ? c->sc32 + F0 * c->L * N : nullptr;
     v.Y = c->Y + F0 * NN;
     v.QR = c->QR + F0 * NN;
@@ -247,7 +258,7 @@ void free_ctx(slmc_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
     if (c->prof_base) cudaEventDestroy(c->prof_base);
-    void* bufs[] = {c->E64, c->Einv64, c->kron, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->tcx_F, c->tcx_eF, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
+    void* bufs[] = {c->E64, c->Einv64, c->kron, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->tcx_F, c->tcx_eF, c->tt_A, c->tt_B, c->tt_eA, c->tt_eB, c->tt_flag, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
                     c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err, c->dctr,
                     c->wolff_sites, c->dq_stack,
                     c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
@@ -321,6 +332,14 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
         alloc(&c->tcx_F, slmc::tcx_F_bytes(c->N));
         alloc(&c->tcx_eF, (size_t)mt * 128 * sizeof(int));
     }
+    {  // tensor-core T update: slices of Rt and P^T T, exponents, exactness flags
+        const size_t npad = (N + 63) / 64 * 64, mpad = (N + 127) / 128 * 128;
+        alloc(&c->tt_A, slmc::tt_slices() * F * mpad * npad * 2);
+        alloc(&c->tt_B, slmc::tt_slices() * F * npad * npad * 2);
+        alloc(&c->tt_eA, F * mpad * sizeof(int));
+        alloc(&c->tt_eB, F * npad * sizeof(int));
+        alloc(&c->tt_flag, F * (mpad / 128) * sizeof(int));
+    }
     alloc(&c->Y, F * NN * sizeof(double));
     alloc(&c->QR, F * NN * sizeof(double));
     alloc(&c->U, F * NN * sizeof(double));
@@ -384,6 +403,7 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     }
     if (cudaMemset(c->err, 0, sizeof(unsigned int)) != cudaSuccess ||
         slmc::build_hopping_exp(c, nullptr) != cudaSuccess || (tc && slmc::tc_init(c, nullptr) != cudaSuccess) ||
+        slmc::tt_init(c) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         free_ctx(c);
         return SLMC_ERR_CUDA;
@@ -717,6 +737,13 @@ int slmc_set_qr_cluster(slmc_ctx* c, int ctas) {
 int slmc_set_dense_slices(slmc_ctx* c, int dense) {
     if (!c || dense < 0 || dense > 1) return SLMC_ERR_ARG;
     c->dense_slices = dense;
+    return SLMC_OK;
+}
+
+int slmc_set_tupdate_path(slmc_ctx* c, int path) {
+    if (!c || path < 0 || path > 2) return SLMC_ERR_ARG;
+    if (path != 1 && !c->tt_A) return SLMC_ERR_UNSUPPORTED;
+    c->tt_path = path;
     return SLMC_OK;
 }
 

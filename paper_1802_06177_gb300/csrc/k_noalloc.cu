@@ -9,7 +9,8 @@
 //
 // The array lives in every GPU that loads the library until the process exits. Its device
 // address is looked up once per device (cudaGetSymbolAddress on the first call with that
-// device current) and cached; in host code the symbol itself is only a host-side stand-in
+// device current) and cached, so a device reset (cudaDeviceReset) or a new primary context on
+// that device invalidates it for the rest of the process; in host code the symbol itself is only a host-side stand-in
 // and must never be passed to a kernel. The first call on a device should therefore happen
 // before any stream capture. Every call reuses the same array: the parts that must start
 // at zero (the error word) are cleared on the stream at the start of each call, everything
@@ -27,15 +28,17 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 unsigned char* g_scratch_addr[kMaxDevices];
+int g_num_sms[kMaxDevices];
 std::mutex g_scratch_mutex;
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Bytes of the per-context part (E, F, error word) and of one field's workspace.
+// Bytes of the per-context part (E, F, the circulant factors, error word) and of one field's workspace.
 size_t fixed_bytes(size_t N) {
     const size_t S = N < (size_t)slmc::kLoStencil ? N : (size_t)slmc::kLoStencil;
     return align256(N * N * sizeof(double)) + align256(N * N * sizeof(float)) +
-           align256((S * N + S) * sizeof(int)) + align256(S * sizeof(float)) + 256;
+           align256((S * N + S) * sizeof(int)) + align256(S * sizeof(float)) +
+           align256(4 * slmc::kKronTab * sizeof(double)) + 256;
 }
 // L > 0 (FP32 mode): also the FP32 slice scales and the FP32 orthogonal factor.
 size_t field_bytes(size_t N, size_t L) {
@@ -43,15 +46,22 @@ size_t field_bytes(size_t N, size_t L) {
            sizeof(int) + L * N * sizeof(float) + (L ? N * N * sizeof(float) : 0);
 }
 
-int scratch_address(int device, unsigned char** out) {
+// Device address of the array and the multiprocessor count of the current device, looked up
+// once per device (with that device current) and cached.
+int scratch_address(int device, unsigned char** out, int* num_sms) {
     if (device < 0 || device >= kMaxDevices) return SLMC_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_addr[device]) {
         void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return SLMC_ERR_CUDA;
+        int sms = 0;
+        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+            return SLMC_ERR_CUDA;
         g_scratch_addr[device] = static_cast<unsigned char*>(ptr);
+        g_num_sms[device] = sms;
     }
     *out = g_scratch_addr[device];
+    *num_sms = g_num_sms[device];
     return SLMC_OK;
 }
 
@@ -75,7 +85,8 @@ int slmc_logdet_noalloc(const slmc_params* p, const double* x, int n, double* ln
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return SLMC_ERR_CUDA;
     unsigned char* base = nullptr;
-    st = scratch_address(device, &base);
+    int num_sms = 0;
+    st = scratch_address(device, &base, &num_sms);
     if (st != SLMC_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
@@ -86,6 +97,7 @@ int slmc_logdet_noalloc(const slmc_params* p, const double* x, int n, double* ln
     c.L = p->L;
     c.max_fields = capacity < n ? capacity : n;
     c.device = device;
+    c.num_sms = num_sms;  // lets few fields spread their QR over clusters of CTAs, as in slmc_logdet
     const size_t NN = N * N, F = (size_t)c.max_fields;
     unsigned char* q = base;
     auto take = [&](size_t bytes) { unsigned char* r = q; q += align256(bytes); return r; };
@@ -96,6 +108,9 @@ int slmc_logdet_noalloc(const slmc_params* p, const double* x, int n, double* ln
         c.lo_kidx = reinterpret_cast<int*>(take(((size_t)c.lo_S * N + c.lo_S) * sizeof(int)));
         c.lo_val = reinterpret_cast<float*>(take((size_t)c.lo_S * sizeof(float)));
     }
+    // the circulant factors of exp(-dtau K): FP64 slice products through them, as in slmc_logdet
+    if (p->Lx <= slmc::kKronMaxLine && p->Ly <= slmc::kKronMaxLine)
+        c.kron = reinterpret_cast<double*>(take(4 * slmc::kKronTab * sizeof(double)));
     c.err = reinterpret_cast<unsigned int*>(take(sizeof(unsigned int)));
     c.Y = reinterpret_cast<double*>(q);
     c.QR = c.Y + F * NN;

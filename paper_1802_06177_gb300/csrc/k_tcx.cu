@@ -51,23 +51,6 @@ __host__ __device__ constexpr uint32_t tmem_cols(int c) {
 
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
-__device__ __forceinline__ void named_sync(int id, int n) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
-// Named barrier that returns the OR of v over its n threads: every participant gets the same
-// answer, so they all take the same branch afterwards.
-__device__ __forceinline__ bool named_sync_or(int id, int n, bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
-        : "=r"(r)
-        : "r"((uint32_t)v), "r"(id), "r"(n)
-        : "memory");
-    return r != 0;
-}
-
 // Exponent of the power of two of the largest |v| whose bit pattern is m (clamped so that
 // every scale 2^(6 - e) and 2^(eF + e - 12) stays a normal FP32 number).
 __device__ __forceinline__ int col_exponent(uint32_t m) {

@@ -74,6 +74,18 @@ struct slmc_ctx {
     int* tcx_eF;
     int tcx_npad;
     CUtensorMap tcx_mapF;
+    // T update on the tensor cores (k_tupd_tc.cu): 7-bit BF16 slices of Rt [6][fields * tt_mpad][tt_npad]
+    // and of P^T T [6][fields * tt_npad][tt_npad] (K-major), their row / column exponents, one
+    // exactness flag per field and 128-row tile, and the TMA descriptors. tt_path: 0 tensor cores,
+    // 1 the FP64 tiled kernel, 2 the tensor kernel with every tile on its FP64 fallback (tests).
+    void* tt_A;
+    void* tt_B;
+    int* tt_eA;
+    int* tt_eB;
+    int* tt_flag;
+    int tt_mpad, tt_npad, tt_path;
+    CUtensorMap tt_mapA, tt_mapB;
+    int fbase;  // first field of this context's workspace within the owner's (views of sub-batches)
     // Split-TF32 slice path (SLMC_PREC_TF32X3): operand pieces of F and of the running slice
     // product (ping/pong), FP32 copies of it, and their TMA descriptors.
     int tc_npad, tc_nt;
@@ -193,6 +205,12 @@ cudaError_t slice_scales(slmc_ctx* c, const double* x, int nf, cudaStream_t s);
 void tc_geometry(int N, int* npad, int* nt, size_t* piece_bytes, int* npieces);
 int tc_launches(int nsl);
 cudaError_t t_update_tiled(slmc_ctx* c, int nf, cudaStream_t s);
+// T <- Rt P^T T by the context's path (tensor cores where set up, else t_update_tiled), and the
+// number of kernels that enqueues.
+cudaError_t t_update(slmc_ctx* c, int nf, cudaStream_t s);
+int t_update_launches(const slmc_ctx* c);
+size_t tt_slices();  // BF16 slices per operand of the tensor-core T update
+cudaError_t tt_init(slmc_ctx* c);
 cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t form_q_blocked(slmc_ctx* c, int nf, bool fp32, cudaStream_t s);
 int qr_panel_width(const slmc_ctx* c);

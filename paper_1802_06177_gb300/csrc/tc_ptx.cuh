@@ -140,6 +140,24 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                  : "r"(taddr));
 }
 
+// Named barrier over n threads of the CTA (barrier 0 is __syncthreads).
+__device__ __forceinline__ void named_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Named barrier that returns the OR of v over its n threads: every participant gets the same
+// answer, so they all take the same branch afterwards.
+__device__ __forceinline__ bool named_sync_or(int id, int n, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
 // TMA descriptor of a 3-D array [d2][d1][d0] (d0 contiguous) of 2- or 4-byte elements with a box
 // of one 128-byte swizzle row (128 / element bytes) by box_rows by 1.
 inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {

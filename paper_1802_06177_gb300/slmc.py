@@ -40,7 +40,7 @@ EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", 
            "slmc_fit_eff_state", "slmc_fit_eff_merge", "slmc_profile_read_detail",
            "slmc_set_sub_batches", "slmc_set_slice_groups",
            "slmc_set_sub_batch_priorities", "slmc_set_qr_cluster", "slmc_set_wolff", "slmc_get_wolff_sites",
-           "slmc_dqmc_sweep", "slmc_set_dense_slices")
+           "slmc_dqmc_sweep", "slmc_set_dense_slices", "slmc_set_tupdate_path")
 
 UPDATE_CONTINUE = (1 << 64) - 1
 FIT_STATE_DOUBLES = 64
@@ -104,6 +104,7 @@ def load_library(path=LIB_PATH):
         "slmc_set_sub_batch_priorities": ([P, I], I),
         "slmc_set_qr_cluster": ([P, I], I),
         "slmc_set_dense_slices": ([P, I], I),
+        "slmc_set_tupdate_path": ([P, I], I),
         "slmc_set_wolff": ([P, I], I),
         "slmc_get_wolff_sites": ([P, ctypes.POINTER(ctypes.c_longlong), I, V], I),
         "slmc_dqmc_sweep": ([P, P, I, I, U64, I, P, P, V], I),
@@ -341,6 +342,11 @@ class Context:
     def set_dense_slices(self, dense):
         """FP64 mode: 1 = dense exp(-dtau K) slice products; 0 (default) = through its separable factors."""
         self._check("slmc_set_dense_slices", self.lib.slmc_set_dense_slices(self._ctx, int(dense)))
+
+    def set_tupdate_path(self, path):
+        """0: T update on the tensor cores (exact slices, FP64-accurate); 1: FP64 FMAs; 2: the
+        tensor kernel with every tile on its FP64 fallback."""
+        self._check("slmc_set_tupdate_path", self.lib.slmc_set_tupdate_path(self._ctx, int(path)))
 
     def set_sub_batch_priorities(self, on):
         """Descending stream priorities for the sub-batches (1) or equal priorities (0)."""

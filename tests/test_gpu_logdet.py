@@ -290,3 +290,30 @@ def test_fp64_separable_and_dense_slices_agree(Lx, Ly, L, n_s):
         l_ref, s_ref, G_ref = fermion_logdet(p, x[f], E=E)
         assert abs(out[0][1][f] - l_ref) <= TOL_LNDET_FP64 and out[0][2][f] == s_ref
         assert np.abs(out[0][0][f] - G_ref).max() <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("Lx,Ly,L,n_s,nf", [(4, 4, 40, 10, 6), (6, 4, 37, 8, 3), (10, 10, 30, 7, 3),
+                                            (12, 12, 120, 10, 3), (16, 16, 160, 8, 3), (18, 18, 36, 9, 2),
+                                            (24, 24, 48, 8, 2)])
+def test_tupdate_paths(precision, Lx, Ly, L, n_s, nf):
+    """T <- (D^-1 R) P^T T on the tensor cores (exact 7-bit slices, path 0), with FP64 FMAs
+    (path 1) and through the tensor kernel's per-tile FP64 fallback (path 2): each within the
+    bars of the oracle, and the three within the FP64 bars (1e-8 ln det, 1e-9 G) of one another."""
+    x = inputs.mixed_fields(nf, Lx, Ly, L, seed=400 + L)
+    ctx = make_ctx(Lx, L, n_s, Ly=Ly, precision=precision, max_fields=nf)
+    out = []
+    for path in (0, 1, 2):
+        ctx.set_tupdate_path(path)
+        G, ld, sg = ctx.greens(cuda(x))
+        ctx.get_error()
+        out.append((G.cpu().numpy(), ld.cpu().numpy(), sg.cpu().numpy()))
+    l_ref, s_ref, G_ref = oracle_many(HolsteinParams(Lx, Ly, L, n_s=n_s), x)
+    tl, tg = (TOL_LNDET_FP64, TOL_G_FP64) if precision == "fp64" else (TOL_LNDET_MIXED, 1e-6)
+    for G, ld, sg in out:
+        assert np.abs(ld - l_ref).max() <= tl
+        assert np.array_equal(sg, s_ref)
+        assert np.abs(G - G_ref).max() <= tg
+    for G, ld, sg in out[1:]:
+        assert np.abs(ld - out[0][1]).max() <= TOL_LNDET_FP64
+        assert np.abs(G - out[0][0]).max() <= TOL_G_FP64

@@ -2,8 +2,10 @@
 ABI: it serves callers that cannot allocate device memory (graph capture, allocator-free
 hot loops, hosts owning the memory budget), keeping its workspace in a fixed device array.
 Its results must equal those of the regular slmc_logdet on the same fields, on two calls
-in a row (the array is reused and keeps the previous call's contents). This file is
-collected last so that a failure here cannot hide the other tests' results."""
+in a row (the array is reused and keeps the previous call's contents). The entry point runs
+the T update of the stabilisation with FP64 FMAs (it has no room for the tensor-core slices),
+so the regular context it is compared with is set to the same path. This file is collected
+last so that a failure here cannot hide the other tests' results."""
 import ctypes
 
 import numpy as np
@@ -24,6 +26,7 @@ def test_noalloc_matches_logdet_twice(Lx, L, n_s, nf):
     lib = load_library()
     assert lib.slmc_logdet_noalloc_scratch_bytes() == 16 << 20
     ctx = make_ctx(Lx, L, n_s, max_fields=nf)
+    ctx.set_tupdate_path(1)
     p = Params(Lx, Lx, L, 0.1, 1.0, 0.0, 1.0, 1.0, n_s, 0, 0.0, 0)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
@@ -55,6 +58,7 @@ def test_noalloc_fp32_matches_logdet(Lx, L, n_s, nf):
     from paper_1802_06177_gb300.slmc import Params, load_library
     lib = load_library()
     ctx = make_ctx(Lx, L, n_s, precision="fp32", max_fields=nf)
+    ctx.set_tupdate_path(1)
     p = Params(Lx, Lx, L, 0.1, 1.0, 0.0, 1.0, 1.0, n_s, 1, 0.0, 0)
     x = cuda(inputs.mixed_fields(nf, Lx, Lx, L, seed=7))
     ref_l, ref_s = ctx.logdet(x)
@@ -66,3 +70,19 @@ def test_noalloc_fp32_matches_logdet(Lx, L, n_s, nf):
     torch.cuda.synchronize()
     assert np.abs(lndet.cpu().numpy() - ref_l.cpu().numpy()).max() <= 1e-10
     assert np.array_equal(sign.cpu().numpy(), ref_s.cpu().numpy())
+
+
+def test_noalloc_reuse_across_lattices_and_chunks():
+    """A 16x16 FP32 call with more fields than the array holds (processed in chunks), then a 4x4
+    FP64 call that reuses the same regions of the array for a smaller lattice: each equals the
+    regular entry point on the same fields."""
+    from paper_1802_06177_gb300.slmc import logdet_noalloc
+    for Lx, L, n_s, nf, prec, tol in ((16, 160, 8, 7, "fp32", 1e-10), (4, 40, 10, 9, "fp64", 1e-12)):
+        ctx = make_ctx(Lx, L, n_s, precision=prec, max_fields=nf)
+        ctx.set_tupdate_path(1)
+        x = cuda(inputs.mixed_fields(nf, Lx, Lx, L, seed=31 + Lx))
+        ref_l, ref_s = ctx.logdet(x)
+        lndet, sign = logdet_noalloc(x, Lx, Lx, L, n_s=n_s, precision=prec)
+        torch.cuda.synchronize()
+        assert np.abs(lndet.cpu().numpy() - ref_l.cpu().numpy()).max() <= tol, (Lx, prec)
+        assert np.array_equal(sign.cpu().numpy(), ref_s.cpu().numpy())
