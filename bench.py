@@ -13,7 +13,13 @@ One step = one pass of the whole hot path over the batch: a cumulative update of
 chain (effective-model checkerboard sweeps, E_eff, exact ln w with the stabilised
 determinant and G, the Eq. (6) acceptance, S(pi,pi)) followed by the regression of E_eff
 on the batch. value = ln det evaluations per second = chains / step time, in the mixed
-precision mode (slice products in --precision, FP64 QR / D scales / LU / log-ratio).
+precision mode (slice products in --precision, default the exact sliced BF16x9 mode on the
+tensor cores; FP64 QR / D scales / LU / log-ratio; the T update of the stabilisation FP64-accurate
+on the tensor cores). Every mode's ln det is scored against the oracle over the whole batch
+(max and RMS of |d ln det|), and the FP64 mode's full step is timed beside the headline.
+
+--probe prints the cuBLAS FP64 / FP32 / TF32 / BF16 GEMM rates and the copy bandwidth of the
+GPU (the rates the bench reports beside its nominal alu peaks) and exits.
 
 --impl reference times the CPU oracle (plain FP64 numpy) on the host cores instead.
 
@@ -39,12 +45,55 @@ if ROOT not in sys.path:
 METRIC = "stabilised ln det(I+B_L...B_1) evals/s, mixed vs FP64 on one GB300, % of peak"
 UNIT = "evals/s"
 
-# Roofline denominators. HBM and BF16 come from MEASURED_PEAKS.json when present. The FP64,
-# FP32 and TF32 pipes are not in that file: "alu" peaks are the nominal figures (FP64
-# 1.25 TFLOP/s), with the throughput probe of profiles/hw_probe_gb300.md reported beside
-# them (FP64 DFMA 1.01, FP32 FFMA 73.3, cuBLAS TF32 1062 TFLOP/s).
-NOMINAL = {"fp64_tflops": 1.25, "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "hbm_gbs": 6800.0}
-PROBED = {"fp64_tflops": 1.01, "fp32_tflops": 73.3, "tf32_tflops": 1062.0, "bf16_tflops": 2056.0}
+# Roofline denominators. HBM and BF16 come from MEASURED_PEAKS.json when present (the tensor
+# kernels are taken against its BF16 burst rate; TF32 against that rate times the nominal
+# TF32 / BF16 ratio 1.1 / 2.25). The FP64 and FP32 pipes are not in that file: "alu" peaks are the
+# nominal figures (FP64 1.25 TFLOP/s), with the rates that this run measures with cuBLAS
+# (probe_rates, also `python bench.py --probe`) reported beside them.
+NOMINAL = {"fp64_tflops": 1.25, "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "hbm_gbs": 6800.0,
+           "tf32_per_bf16": 1.1 / 2.25}
+MIXED_BAR_DLNW = 1e-4  # |d ln w| of a mixed-precision mode against the FP64 oracle
+
+
+def probe_rates(dev):
+    """Pipe rates measured now with library GEMMs (cuBLAS through torch.matmul; CUDA events, best
+    of a few repetitions after a warm-up): FP64, FP32 (TF32 off), TF32 and BF16 in TFLOP/s, and a
+    device-to-device copy of 1 Gi BF16 elements in GB/s (bytes read + written)."""
+    import torch
+
+    def best_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    def gemm(n, dtype, reps, tf32=False):
+        a = torch.randn(n, n, device=dev).to(dtype)
+        b = torch.randn(n, n, device=dev).to(dtype)
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        try:
+            ms = best_ms(lambda: torch.matmul(a, b), reps)
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = old
+        return 2.0 * n ** 3 / (ms / 1e3) / 1e12
+
+    out = {"fp64_tflops": gemm(4096, torch.float64, 3), "fp32_tflops": gemm(8192, torch.float32, 3),
+           "tf32_tflops": gemm(8192, torch.float32, 5, tf32=True), "bf16_tflops": gemm(8192, torch.bfloat16, 5)}
+    src = torch.empty(1 << 30, dtype=torch.bfloat16, device=dev)
+    dst = torch.empty_like(src)
+    out["copy_gbs"] = 2.0 * src.numel() * 2 / (best_ms(lambda: dst.copy_(src), 5) / 1e3) / 1e9
+    out["how"] = "torch.matmul 4096^3 FP64, 8192^3 FP32 / TF32 / BF16 (2 n^3 flop), copy of 1 Gi BF16; best of 3-5"
+    del src, dst
+    torch.cuda.empty_cache()
+    return out
 
 
 def load_peaks():
@@ -66,17 +115,22 @@ def load_peaks():
 # CPU oracle timing (spawned workers, one BLAS thread each)
 # ---------------------------------------------------------------------------------------
 def _oracle_logdet_worker(args):
-    wl_name, nf, fid = args
+    wl_name, nf, fids = args
     from oracle import HolsteinParams
     from oracle.fermion import fermion_logdet
+    from oracle.lattice import exp_hopping
     from paper_1802_06177_gb300 import inputs
     from paper_1802_06177_gb300.workloads import WORKLOADS
     wl = WORKLOADS[wl_name]
     p = HolsteinParams(wl.Lx, wl.Lx, wl.L, n_s=wl.n_s)
+    E = exp_hopping(wl.Lx, wl.Lx, 1.0, 0.0, 0.1)
     gen = inputs.mixed_fields if wl.fields == "mixed" else inputs.gaussian_fields
-    x = gen(nf, wl.Lx, wl.Lx, wl.L, seed=wl.seed)[fid]
-    lndet, sign, _ = fermion_logdet(p, x, want_G=False)
-    return fid, lndet, sign
+    x = gen(nf, wl.Lx, wl.Lx, wl.L, seed=wl.seed)
+    out = []
+    for fid in fids:
+        lndet, sign, _ = fermion_logdet(p, x[fid], E=E, want_G=False)
+        out.append((fid, lndet, sign))
+    return out
 
 
 def oracle_pool(nproc):
@@ -88,7 +142,11 @@ def oracle_pool(nproc):
 
 def oracle_logdets(pool, wl_name, nf, field_ids):
     """Oracle ln|det| of fields of the benchmark batch (seeded exactly as on rank 0)."""
-    return {f: (l, sg) for f, l, sg in pool.map(_oracle_logdet_worker, [(wl_name, nf, f) for f in field_ids])}
+    ids = list(field_ids)
+    nchunk = max(1, min(len(ids), 64))
+    chunks = [ids[k::nchunk] for k in range(nchunk)]
+    return {f: (l, sg) for part in pool.map(_oracle_logdet_worker, [(wl_name, nf, c) for c in chunks if c])
+            for f, l, sg in part}
 
 
 # ---------------------------------------------------------------------------------------
@@ -224,7 +282,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(wl, args, "f64 oracle"),
+            "config": config_of(wl, args, args.precision),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle",
                              "sample": "per step: %d chains (one per core), one oracle cumulative update each "
                                        "(%d E_eff sweeps, exact ln w with UDT log-det and G, Eq. 6 accept) on %s"
@@ -272,6 +330,46 @@ def config_of(wl, args, precision):
             "parallelism": "replicas x%d" % args.gpus,
             "l2": "inputs larger than L2 (fields %.0f MB + workspace), no flush" % (
                 (args.fields or wl.nfields) * wl.N * wl.L * 8 / 1e6)}
+
+
+def tensor_use(wl, nf, ngroups, precision, prof, peaks):
+    """Tensor-pipe use of the tensor-core kernel classes over a profiled region: issued MMA flops
+    (every slice product the kernels issue, padding included) of all the class's calls (the
+    profiler counts the fields of each call; one call per stabilisation group) over the class's
+    busy time, against the measured BF16 burst rate (TF32: times the nominal TF32 / BF16 ratio)."""
+    bf16 = peaks.get("bf16_tflops")
+    if not bf16:
+        return {}
+    N = wl.N
+    npad, mtiles = -(-N // 64) * 64, -(-N // 128)
+    nsl_mean = wl.L / ngroups
+    out = {}
+    src = "MEASURED_PEAKS.json bf16_tflops (burst)"
+    sl = prof.get("slice")
+    if precision in ("bf16x9", "tf32x3") and sl and sl[2] > 0:
+        if precision == "bf16x9":  # 9 products of 128-row tiles x K chunks of 64 per slice
+            nt = 128 if mtiles == 1 and N > 64 else (64 if mtiles <= 2 else (32 if mtiles <= 4 else 16))
+            per_field_slice = 9 * 2.0 * (128 * mtiles) * npad * (nt * -(-N // nt))
+            peak, how = bf16, src
+        else:  # 3 products, K padded to 32
+            per_field_slice = 3 * 2.0 * (128 * mtiles) * (-(-N // 32) * 32) * N
+            peak, how = bf16 * NOMINAL["tf32_per_bf16"], src + " x 1.1/2.25 (nominal TF32/BF16)"
+        issued = per_field_slice * nsl_mean * sl[3]
+        t = issued / (sl[2] / 1e3) / 1e12
+        out["slice:" + precision] = {"issued_tflops": t, "peak_tflops": peak, "frac_of_peak": t / peak,
+                                     "busy_ms": sl[2], "dense_fp32_equivalent_tflops":
+                                     2.0 * N ** 3 * nsl_mean * sl[3] / (sl[2] / 1e3) / 1e12, "peak_source": how}
+    tu = prof.get("tupdate")
+    if tu and tu[2] > 0:
+        nk = npad // 64
+        chunks = sum(nk - 2 * mt for mt in range(mtiles))  # K chunks per column tile (triangular start)
+        issued = chunks * (npad // 64) * 28 * 2.0 * 128 * 64 * 64 * tu[3]
+        t = issued / (tu[2] / 1e3) / 1e12
+        out["tupdate:" + precision] = {"issued_tflops": t, "peak_tflops": bf16, "frac_of_peak": t / bf16,
+                                       "busy_ms": tu[2], "includes": "the two slicing kernels",
+                                       "fp64_equivalent_tflops": float(N) ** 3 * tu[3] / (tu[2] / 1e3) / 1e12,
+                                       "peak_source": src}
+    return out
 
 
 def run_gpu(args):
@@ -355,6 +453,9 @@ def run_gpu(args):
         barrier(world)
         return max_over_ranks(ms, world, dev), launches, prof, clk
 
+    # ---- pipe rates of this GPU (cuBLAS), reported beside the nominal alu peaks -----------
+    probed = probe_rates(dev)
+
     # ---- headline: mixed precision --------------------------------------------------
     ctx = make(args.precision)
     st = setup(ctx)
@@ -362,15 +463,15 @@ def run_gpu(args):
     ms_step = ms / args.steps
     value = nf * world / (ms_step / 1e3)
 
-    # ---- e2e through host buffers -----------------------------------------------------
+    # ---- e2e through host buffers, over as many steps as the device-timed value ------------
     xh_pin = torch.from_numpy(st["x"].cpu().numpy()).pin_memory()
     lnw_h = torch.empty(nf, dtype=torch.float64).pin_memory()
     s_h = torch.empty(nf, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
+    barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(1, min(args.steps, 3))
     e0.record()
-    for k in range(e2e_steps):
+    for k in range(args.steps):
         st["x"].copy_(xh_pin, non_blocking=True)
         step(ctx, st, 10 ** 6 + k)
         xh_pin.copy_(st["x"], non_blocking=True)
@@ -378,51 +479,37 @@ def run_gpu(args):
         s_h.copy_(st["s"], non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     h2d = nf * wl.N * wl.L * 8
     d2h = h2d + 2 * nf * 8
 
-    # ---- logdet-only rates and accuracy of each mode ------------------------------------
-    h = args.acc_fields // 2
-    acc_ids = sorted(set(list(range(min(h, nf))) + list(range(nf // 2, min(nf, nf // 2 + args.acc_fields - h)))))
-    xs = x0[acc_ids].contiguous()
-    rates, lndets = {}, {}
+    # ---- logdet-only rates, tensor-pipe use and ln det of every mode over the whole batch -----
+    peaks = load_peaks()
+    ngroups = math.ceil(wl.L / wl.n_s)
+    rates, lndets, tensor = {}, {}, {}
     old_mode = args.mode
     args.mode = "logdet"
-    ms_ld, _, _, _ = timed(ctx, {"x": x0.clone()}, 1, 1, 0)
-    rates[args.precision] = nf * world / (ms_ld / 1e3)
-    lndets[args.precision] = ctx.logdet(xs)[0].cpu().numpy()
+
+    def logdet_mode(c, m):
+        ms_l, _, pr, _ = timed(c, {"x": x0.clone()}, 1, 2, 0, profile=True)
+        rates[m] = nf * world / (ms_l / 1e3)
+        lndets[m] = c.logdet(x0)[0].cpu().numpy()
+        tensor.update(tensor_use(wl, nf, ngroups, m, pr, peaks))
+
+    logdet_mode(ctx, args.precision)
     ctx.close()
     fp64_value = None
-    tensor_modes = {}
-    for extra in ([] if args.no_fp64 else ["tf32x3", "bf16x9"]):
+    for extra in ([] if args.no_fp64 else ["fp64", "fp32", "tf32x3", "bf16x9"]):
         if extra == args.precision:
             continue
         ce = make(extra)
-        ms_e, _, prof_e, _ = timed(ce, {"x": x0.clone()}, 1, 1, 0, profile=True)
-        rates[extra] = nf * world / (ms_e / 1e3)
-        lndets[extra] = ce.logdet(xs)[0].cpu().numpy()
-        ce.close()
-        # tensor-core slice products: dense work 2 N^3 per slice and field; the split products
-        # issue 3 (TF32) or 9 (BF16) MMAs per product, against that pipe's probed peak
-        busy = prof_e["slice"][2] / 1e3
-        dense = 2.0 * float(wl.N) ** 3 * wl.L * nf / max(busy, 1e-12) / 1e12
-        pieces, peak = (3, PROBED["tf32_tflops"]) if extra == "tf32x3" else (9, PROBED["bf16_tflops"])
-        tensor_modes[extra] = {"slice_busy_ms": prof_e["slice"][2], "dense_tflops": dense,
-                               "issued_tflops": dense * pieces, "tensor_peak_tflops": peak,
-                               "frac_of_tensor_peak": dense * pieces / peak,
-                               "peak_source": "probed tcgen05 rate of this pipe (profiles/hw_probe_gb300.md)"}
-    if not args.no_fp64 and args.precision != "fp64":
-        c64 = make("fp64")
-        ms64, _, _, _ = timed(c64, {"x": x0.clone()}, 1, 1, 0)
-        rates["fp64"] = nf * world / (ms64 / 1e3)
-        lndets["fp64"] = c64.logdet(xs)[0].cpu().numpy()
-        args.mode = old_mode
-        if old_mode == "step":
-            st64 = setup(c64)
-            ms64s, _, _, _ = timed(c64, st64, 1, 1, 0)
+        logdet_mode(ce, extra)
+        if extra == "fp64" and old_mode == "step":
+            args.mode = old_mode
+            ms64s, _, _, _ = timed(ce, setup(ce), 1, 2, 0)
             fp64_value = nf * world / (ms64s / 1e3)
-        c64.close()
+            args.mode = "logdet"
+        ce.close()
     args.mode = old_mode
 
     batched = None if args.no_batch else run_uneven_batch(args, dev, seed)
@@ -431,8 +518,6 @@ def run_gpu(args):
         return 0
 
     # ---- roofline of the dominant kernel class -------------------------------------------
-    peaks = load_peaks()
-    ngroups = math.ceil(wl.L / wl.n_s)
     nsl_mean = wl.L / ngroups
     # calls of one class on concurrent sub-batch streams overlap: rank classes by busy time
     # (union of their call intervals) and divide the class's work by it
@@ -444,24 +529,29 @@ def run_gpu(args):
         fields_per_call = dom_units / max(dom_calls, 1)
         per_call = work * fields_per_call
         busy_s = dom_busy / 1e3
-        fp64_cls = dom in ("qr", "formq", "tupdate", "greens") or (dom == "slice" and args.precision == "fp64")
+        fp64_cls = dom in ("qr", "formq", "greens") or (dom == "slice" and args.precision == "fp64")
         traffic = kernel_traffic(dom, fields_per_call)
         common = {"kernel_class": dom, "algorithmic_per_launch": per_call, "fields_per_launch": fields_per_call,
                   "launches_timed": dom_calls, "busy_ms": dom_busy, "sum_launch_ms": dom_ms,
                   "avg_launch_ms": dom_ms / max(dom_calls, 1),
                   "timing": "achieved = work of all timed launches / their busy time (union of launch "
                             "intervals on the sub-batch streams, CUDA events on the launching streams)"}
-        if kind == "flop":
+        if kind == "flop" and (fp64_cls or dom == "slice"):
             achieved = work * dom_units / busy_s / 1e12
             if fp64_cls:
-                peak, pk, src = NOMINAL["fp64_tflops"], PROBED["fp64_tflops"], \
-                    "nominal FP64 1.25 TFLOP/s (alu, not in MEASURED_PEAKS.json); probed DFMA rate beside it"
+                peak, pk, src = NOMINAL["fp64_tflops"], probed["fp64_tflops"], \
+                    "nominal FP64 1.25 TFLOP/s (alu, not in MEASURED_PEAKS.json); cuBLAS DGEMM rate of this run beside it"
             else:
-                peak, pk, src = NOMINAL["fp32_tflops"], PROBED["fp32_tflops"], \
-                    "nominal FP32 SIMT rate 152 SM x 128 lanes x 2 x 2.07 GHz (alu); probed FFMA rate beside it"
+                peak, pk, src = NOMINAL["fp32_tflops"], probed["fp32_tflops"], \
+                    "nominal FP32 SIMT rate 152 SM x 128 lanes x 2 x 2.07 GHz (alu); cuBLAS SGEMM rate beside it"
             roof = dict(common, bound="alu", pipe="fp64" if fp64_cls else "fp32", achieved=achieved, peak=peak,
                         unit="TFLOP/s", frac=achieved / peak, peak_probed=pk, frac_of_probed=achieved / pk,
                         traffic=traffic, peak_source=src)
+        elif kind == "flop":  # tensor-core classes: issued BF16 flops against the measured BF16 rate
+            t = tensor_use(wl, nf, ngroups, args.precision, prof, peaks).get(dom + ":" + args.precision)
+            if t:
+                roof = dict(common, bound="tensor", achieved=t["issued_tflops"], peak=t["peak_tflops"],
+                            unit="TFLOP/s", frac=t["frac_of_peak"], traffic=None, peak_source=t["peak_source"])
         else:
             achieved = work * dom_units / busy_s / 1e9
             roof = dict(common, bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
@@ -475,14 +565,25 @@ def run_gpu(args):
                       "peak_source": peaks["source"]}
     total_prof = sum(v[2] for v in prof.values())
     shares = {k: round(v[2] / total_prof, 4) for k, v in prof.items() if v[2] > 0}
+    step_tensor = tensor_use(wl, nf, ngroups, args.precision, prof, peaks)
 
-    # ---- accuracy against the FP64 oracle and CPU baseline ----------------------------
+    # ---- accuracy of every mode against the FP64 oracle over the batch, and CPU baseline ----
     acc = None
     cpu = None
     if pool is not None:
-        ref = oracle_logdets(pool, wl.name, nf, acc_ids)
-        acc = {m: float(np.max(np.abs(v - np.array([ref[i][0] for i in acc_ids])))) for m, v in lndets.items()}
-        acc["sample_fields"] = acc_ids
+        ids = list(range(nf)) if not args.acc_fields else \
+            sorted(set(range(min(args.acc_fields // 2, nf))) |
+                   set(range(nf // 2, min(nf, nf // 2 + args.acc_fields - args.acc_fields // 2))))
+        ref = oracle_logdets(pool, wl.name, nf, ids)
+        r = np.array([ref[i][0] for i in ids])
+        acc = {}
+        for m, v in lndets.items():
+            d = np.abs(v[ids] - r)
+            acc[m] = {"max": float(d.max()), "rms": float(np.sqrt(np.mean(d ** 2))), "n": len(ids),
+                      "max_dlnw": float(2 * d.max()), "rms_dlnw": float(2 * np.sqrt(np.mean(d ** 2))),
+                      "meets_mixed_bar": bool(2 * d.max() <= MIXED_BAR_DLNW)}
+        acc["fields"] = "all %d fields of the batch" % nf if len(ids) == nf else ids
+        acc["note"] = "|d ln w| = 2 |d ln det| (two spin species; the bosonic part is exact FP64 in both)"
         done, busy, wall = time_oracle_step(pool, nproc, wl.name, args.nsweeps)
         done2, busy2, wall2 = time_oracle_step(pool, nproc, wl.name, args.nsweeps)
         cpu = {"value": (done + done2) / (wall + wall2), "unit": UNIT, "cores": nproc, "kind": "oracle",
@@ -491,27 +592,32 @@ def run_gpu(args):
                          % (nproc, args.nsweeps, wl.name)}
         pool.close()
 
-    # FP64 work of one evaluation of the step (QR and T update per group, Q of the final group
-    # (FP64 in every mode; the other groups' Q is FP64 only in FP64 mode), final LU, G) against the
-    # step time: how close the whole step runs to the FP64 roof while the FP32 work overlaps it
+    # FP64-pipe work of one evaluation of the step (QR per group, Q of the final group (FP64 in
+    # every mode; the other groups' Q is FP64 only in FP64 mode), final LU, G, and FP64 slices in
+    # FP64 mode; the T update runs on the tensor cores) against the step time
     N3 = float(wl.N) ** 3
-    w64 = ngroups * (4.0 / 3.0 + 1.0) * N3 + (4.0 / 3.0) * N3 * (ngroups if args.precision == "fp64" else 1) \
+    w64 = ngroups * (4.0 / 3.0) * N3 + (4.0 / 3.0) * N3 * (ngroups if args.precision == "fp64" else 1) \
         + (2.0 / 3.0 + (2.0 if args.mode == "step" else 0.0)) * N3
     if args.precision == "fp64":  # slices through the separable exp(-dtau K): N^2 (Lx + Ly) FMAs each
         w64 += 2.0 * float(wl.N) ** 2 * (2 * wl.Lx) * wl.L
     ach64 = w64 * nf * world / (ms_step / 1e3) / 1e12 / world
     fp64_step = {"flop_per_eval": w64, "achieved_per_gpu": ach64, "unit": "TFLOP/s",
-                 "frac_of_nominal": ach64 / NOMINAL["fp64_tflops"], "frac_of_probed": ach64 / PROBED["fp64_tflops"]}
+                 "frac_of_nominal": ach64 / NOMINAL["fp64_tflops"], "frac_of_probed": ach64 / probed["fp64_tflops"],
+                 "excludes": "T update (tensor cores)"}
+    dtype = {"fp64": "f64", "fp32": "f32 slices + f64 stabilisation",
+             "tf32x3": "tf32x3 slices (tensor cores) + f64 stabilisation",
+             "bf16x9": "bf16x9 exact-sliced slices (tensor cores) + f64 stabilisation"}[args.precision] + \
+        "; T update f64-accurate on the tensor cores (bf16 slices)"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 slices + f64 stabilisation" if args.precision != "fp64" else "f64",
-            "data": "synthetic", "config": config_of(wl, args, args.precision),
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config_of(wl, args, args.precision),
             "e2e": {"value": nf * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, "steps": args.steps},
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
             "fp64_value": fp64_value, "logdet_only_evals_per_s": rates, "accuracy_max_abs_dlndet": acc,
-            "fp64_step": fp64_step, "sweep_roofline": sweep_roof, "tensor_modes": tensor_modes,
-            "time_shares": shares, "mode": args.mode, "batched_uneven": batched}
+            "fp64_step": fp64_step, "sweep_roofline": sweep_roof, "tensor_step": step_tensor,
+            "tensor_logdet_only": tensor, "probed_rates": probed, "time_shares": shares, "mode": args.mode,
+            "batched_uneven": batched}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -630,6 +736,7 @@ def run_dqmc(args):
     wl = WORKLOADS[args.workload]
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    probed = probe_rates(dev)
     nproc = min(16, os.cpu_count() or 1)
     pool = oracle_pool(nproc) if rank == 0 and not args.no_cpu_baseline else None
     nf = args.fields or torch.cuda.get_device_properties(dev).multi_processor_count  # one chain per SM
@@ -687,9 +794,9 @@ def run_dqmc(args):
     roof = {"kernel_class": "dqmc", "kernel": "k_dqmc_slices", "bound": "alu", "pipe": "fp64",
             "algorithmic_per_launch": flops / max(dq_calls, 1), "launches_timed": dq_calls, "busy_ms": dq_busy,
             "achieved": achieved, "peak": NOMINAL["fp64_tflops"], "unit": "TFLOP/s",
-            "frac": achieved / NOMINAL["fp64_tflops"], "peak_probed": PROBED["fp64_tflops"],
-            "frac_of_probed": achieved / PROBED["fp64_tflops"], "traffic": None,
-            "peak_source": "nominal FP64 1.25 TFLOP/s (alu, not in MEASURED_PEAKS.json); probed DFMA rate beside it"}
+            "frac": achieved / NOMINAL["fp64_tflops"], "peak_probed": probed["fp64_tflops"],
+            "frac_of_probed": achieved / probed["fp64_tflops"], "traffic": None,
+            "peak_source": "nominal FP64 1.25 TFLOP/s (alu, not in MEASURED_PEAKS.json); cuBLAS DGEMM rate of this run beside it"}
     total_prof = sum(v[2] for v in prof.values())
     shares = {k: round(v[2] / total_prof, 4) for k, v in prof.items() if v[2] > 0}
     cpu = None
@@ -724,16 +831,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="slmc", choices=["slmc", "reference"])
     ap.add_argument("--workload", default=None, help="default holstein_16x16_L160 (dqmc mode: holstein_12x12_L120)")
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32x3", "bf16x9"])
+    ap.add_argument("--precision", default="bf16x9", choices=["fp64", "fp32", "tf32x3", "bf16x9"])
     ap.add_argument("--nsweeps", type=int, default=20)
     ap.add_argument("--fields", type=int, default=0, help="override chains per GPU (small profiling cases)")
     ap.add_argument("--mode", default="step", choices=["step", "logdet", "dqmc"])
     ap.add_argument("--dqmc-block", type=int, default=0, help="DQMC mode: block updates per sweep")
-    ap.add_argument("--acc-fields", type=int, default=4)
+    ap.add_argument("--acc-fields", type=int, default=0, help="oracle-scored fields (0 = the whole batch)")
+    ap.add_argument("--probe", action="store_true", help="print the cuBLAS / copy rates of this GPU and exit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--batch-rounds", type=int, default=20)
+    ap.add_argument("--batch-rounds", type=int, default=100)
     ap.add_argument("--sub-batches", type=int, default=0, help="forked streams per batch (0 = library default)")
     ap.add_argument("--slice-groups", type=int, default=0, help="FP32 slice kernel column groups (0 = default)")
     ap.add_argument("--sub-priorities", type=int, default=-1, help="descending sub-batch stream priorities (1/0)")
@@ -744,6 +852,10 @@ def main():
         args.warmup = 3
     if args.workload is None:
         args.workload = "holstein_12x12_L120" if args.mode == "dqmc" else "holstein_16x16_L160"
+    if args.probe:
+        import torch
+        print(json.dumps(probe_rates(torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0"))))), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "dqmc":
