@@ -90,9 +90,11 @@ def dqmc_configurations(ctx, x, therm, gap, count, sweep0=0):
 
 
 def run_dqmc(Lx, L, n_s=8, chains=32, sweeps=500, precision="fp64", dtau=0.1, lam=1.0, omega0=1.0,
-             sweep_delta=0.5, seed=0x1802061774, device="cuda", rank=0, world=1, nblock=0, init="gaussian"):
+             sweep_delta=0.5, seed=0x1802061774, device="cuda", rank=0, world=1, nblock=0, init="gaussian",
+             want_series=False):
     """Conventional DQMC chains: S(pi, pi) from G after every sweep, its integrated
-    autocorrelation time in sweeps and the time per sweep."""
+    autocorrelation time in sweeps and the time per sweep (want_series: also the per-sweep,
+    per-chain S(pi, pi) and the acceptance counts of this process)."""
     dev = torch.device(device)
     seed = seed + rank
     ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
@@ -127,13 +129,20 @@ def run_dqmc(Lx, L, n_s=8, chains=32, sweeps=500, precision="fp64", dtau=0.1, la
            "block_acceptance": float(acc[1].item()) / max(1, chains * world * sweeps * nblock),
            "ms_per_sweep": sweep_ms / sweeps, "chain_sweeps_per_s": chains * world * sweeps / (sweep_ms / 1e3),
            "ms_per_independent_sample": 2.0 * tau * sweep_ms / sweeps}
+    if want_series:
+        res["S_series"] = obs.cpu().numpy().tolist()
+        res["accepted_local"] = n_loc.cpu().numpy().tolist()
+        res["accepted_block"] = n_blk.cpu().numpy().tolist()
     ctx.close()
     return res
 
 
 def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision="fp32", dtau=0.1, lam=1.0,
         omega0=1.0, sweep_delta=0.3, seed=0x1802061774, rounds=2, device="cuda", rank=0, world=1, wolff=0,
-        train_source="self", dqmc_therm=50, dqmc_gap=5, init="gaussian", J0=None):
+        train_source="self", dqmc_therm=50, dqmc_gap=5, init="gaussian", J0=None, want_series=False):
+    """One SLMC run: self-learning (or DQMC) training of E_eff, then `updates` cumulative updates
+    of every chain measuring S(pi, pi) after each (want_series: also the per-update, per-chain
+    S(pi, pi), the acceptance counts and the couplings of every training round)."""
     dev = torch.device(device)
     seed = seed + rank
     ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
@@ -221,6 +230,9 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
         "production_seconds": ms / 1e3, "training_seconds": t_train,
         "evals_per_s": chains * world * updates / (ms / 1e3), "J_final": J.cpu().tolist(),
     }
+    if want_series:
+        res["S_series"] = obs.cpu().numpy().tolist()
+        res["accepted"] = n_acc.cpu().numpy().tolist()
     ctx.close()
     return res
 
@@ -235,23 +247,24 @@ def power_law_exponent(sizes, values):
 
 def autocorrelation_study(sizes, beta=4.1, dtau=0.1, lam=1.0, omega0=0.5, n_s=10, chains=64, steps=2000,
                           sweeps=10, train=1024, seed=0x1802061774, device="cuda", rank=0, world=1, nblock=4,
-                          wolff=1, init="cdw", dqmc_therm=200):
+                          wolff=1, init="cdw", dqmc_therm=200, precision="fp32", want_series=False):
     """Autocorrelation time tau_L of S(pi, pi) against the linear size for DQMC and SLMC with the
     paper's Monte Carlo steps (Sec. "Results"): a DQMC step is a sweep of local updates plus
     `nblock` block updates; an SLMC step is a sweep of local updates of E_eff plus `wolff` Wolff
     cluster updates, so tau in SLMC steps is tau in cumulative updates times `sweeps`. Also the
     GPU time per statistically independent configuration, 2 tau_L times the time per step, and
     the power-law exponents of both against the size. Defaults: the paper's critical point
-    (lambda = 0.5 from g = 1, Omega = 0.5; beta = 1 / T_c = 4.1)."""
+    (lambda = 0.5 from g = 1, Omega = 0.5; beta = 1 / T_c = 4.1). precision: the slice products of
+    the SLMC runs (the DQMC chains are FP64); want_series: the per-step S(pi, pi) of every run."""
     L = 2 * max(1, int(round(beta / (2.0 * dtau))))  # the checkerboard sweeps of E_eff need an even L
     dtau = beta / L
     rows = []
     for Lx in sizes:
         d = run_dqmc(Lx, L, min(n_s, L), chains, steps, "fp64", dtau=dtau, lam=lam, omega0=omega0, seed=seed,
-                     device=device, rank=rank, world=world, nblock=nblock, init=init)
-        m = run(Lx, L, min(n_s, L), chains, train, max(4, steps // sweeps), sweeps, "fp32", dtau=dtau, lam=lam,
+                     device=device, rank=rank, world=world, nblock=nblock, init=init, want_series=want_series)
+        m = run(Lx, L, min(n_s, L), chains, train, max(4, steps // sweeps), sweeps, precision, dtau=dtau, lam=lam,
                 omega0=omega0, seed=seed, rounds=2, device=device, rank=rank, world=world, wolff=wolff,
-                train_source="dqmc", dqmc_therm=dqmc_therm, init=init)
+                train_source="dqmc", dqmc_therm=dqmc_therm, init=init, want_series=want_series)
         s_ms = 1e3 * m["production_seconds"] / m["updates"] / sweeps  # per SLMC step
         rows.append({"Lx": Lx, "dqmc_tau_steps": d["S_pipi_tau_int_sweeps"], "dqmc_ms_per_step": d["ms_per_sweep"],
                      "dqmc_ms_per_independent": d["ms_per_independent_sample"], "dqmc_S": d["S_pipi_mean"],
@@ -261,6 +274,10 @@ def autocorrelation_study(sizes, beta=4.1, dtau=0.1, lam=1.0, omega0=0.5, n_s=10
                      "slmc_ms_per_independent": 2.0 * m["S_pipi_tau_int_updates"] * sweeps * s_ms,
                      "slmc_S": m["S_pipi_mean"], "slmc_S_err": m["S_pipi_err"], "slmc_S_halves": m["S_pipi_halves"],
                      "slmc_acceptance": m["acceptance"], "slmc_mean_cluster": m["wolff_mean_cluster"]})
+        if want_series:
+            rows[-1].update({"dqmc_series": d["S_series"], "dqmc_accepted_local": d["accepted_local"],
+                             "dqmc_accepted_block": d["accepted_block"], "slmc_series": m["S_series"],
+                             "slmc_accepted": m["accepted"], "slmc_J": m["J_final"]})
     fit = {k: power_law_exponent([r["Lx"] for r in rows], [r[k] for r in rows])
            for k in ("dqmc_tau_steps", "slmc_tau_steps", "dqmc_ms_per_independent", "slmc_ms_per_independent")}
     return {"study": "autocorrelation", "beta": beta, "L": L, "dtau": dtau, "g": lam, "omega0": omega0,
@@ -284,13 +301,15 @@ def crossings(sizes, temps, curves):
 
 
 def fss_scan(sizes, betas, dtau=0.1, lam=1.0, omega0=0.5, n_s=10, chains=64, updates=300, sweeps=10, train=1024,
-             dqmc_therm=300, seed=0x1802061774, device="cuda", rank=0, world=1, wolff=1):
+             dqmc_therm=300, seed=0x1802061774, device="cuda", rank=0, world=1, wolff=1, precision="fp32",
+             want_series=False):
     """Finite-size scaling of the CDW structure factor (Sec. "Results", Fig. 3(a)): S(pi, pi) L^{-7/4}
     against T for each linear size L, whose crossings estimate T_c (2D Ising: 2 beta/nu = 1/4). Per
     size, E_eff is learned once from DQMC configurations at the middle inverse temperature (the
     paper's training data); the cumulative updates at the other temperatures stay exact with those
     couplings and only accept less often. Inverse temperatures are multiples of 2 dtau (the E_eff
-    checkerboard needs an even number of slices); every run starts from the CDW state."""
+    checkerboard needs an even number of slices); every run starts from the CDW state. precision:
+    the slice products of the SLMC runs; want_series: the per-update S(pi, pi) of every run."""
     betas = sorted(betas)
     Ls = [2 * max(1, int(round(b / (2.0 * dtau)))) for b in betas]
     mid = Ls[len(Ls) // 2]
@@ -298,16 +317,16 @@ def fss_scan(sizes, betas, dtau=0.1, lam=1.0, omega0=0.5, n_s=10, chains=64, upd
     temps = [1.0 / (l * dtau) for l in Ls]
     for Lx in sizes:
         # DQMC fit, then one self-learning refinement (as in the autocorrelation study)
-        tr = run(Lx, mid, min(n_s, mid), chains, train, 4, sweeps, "fp32", dtau=dtau, lam=lam, omega0=omega0,
+        tr = run(Lx, mid, min(n_s, mid), chains, train, 4, sweeps, precision, dtau=dtau, lam=lam, omega0=omega0,
                  seed=seed, rounds=2, device=device, rank=rank, world=world, wolff=wolff, train_source="dqmc",
                  dqmc_therm=dqmc_therm, init="cdw")
         training[Lx] = {"rms_resid": [h["rms_resid"] for h in tr["training_rounds"]], "J": tr["J_final"],
                         "acceptance_at_training_beta": tr["acceptance"]}
         curves[Lx] = []
         for L, T in zip(Ls, temps):
-            m = run(Lx, L, min(n_s, L), chains, 0, updates, sweeps, "fp32", dtau=dtau, lam=lam, omega0=omega0,
+            m = run(Lx, L, min(n_s, L), chains, 0, updates, sweeps, precision, dtau=dtau, lam=lam, omega0=omega0,
                     seed=seed + 7919 * L, rounds=0, device=device, rank=rank, world=world, wolff=wolff,
-                    init="cdw", J0=tr["J_final"])
+                    init="cdw", J0=tr["J_final"], want_series=want_series)
             y = m["S_pipi_mean"] * Lx ** (-1.75)
             curves[Lx].append(y)
             rows.append({"Lx": Lx, "L": L, "beta": L * dtau, "T": T, "S_pipi": m["S_pipi_mean"],
@@ -315,6 +334,8 @@ def fss_scan(sizes, betas, dtau=0.1, lam=1.0, omega0=0.5, n_s=10, chains=64, upd
                          m["S_pipi_err"] * Lx ** (-1.75), "S_halves": m["S_pipi_halves"],
                          "tau_int_updates": m["S_pipi_tau_int_updates"], "acceptance": m["acceptance"],
                          "production_seconds": m["production_seconds"]})
+            if want_series:
+                rows[-1].update({"series": m["S_series"], "accepted": m["accepted"], "J": tr["J_final"]})
     return {"study": "fss", "g": lam, "omega0": omega0, "lambda_dimensionless": lam ** 2 / (8.0 * omega0 ** 2),
             "dtau": dtau, "chains": chains * world, "updates": updates, "sweeps_per_update": sweeps,
             "wolff_per_sweep": wolff, "training_beta": mid * dtau, "training": training, "temperatures": temps,

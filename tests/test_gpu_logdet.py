@@ -142,7 +142,8 @@ def test_full_size_16x16_L160_sampled():
 TOL_LNDET_MIXED = 5e-5  # |d ln w| = 2 |d ln det| <= 1e-4
 
 
-@pytest.mark.parametrize("Lx,L,n_s,nf", [(12, 120, 10, 8), (16, 160, 8, 4), (24, 48, 8, 1), (4, 40, 10, 8)])
+@pytest.mark.parametrize("Lx,L,n_s,nf", [(12, 120, 10, 8), (16, 160, 8, 32), (24, 48, 8, 1), (4, 40, 10, 8),
+                                         (24, 240, 8, 2)])
 def test_fp32_slices_meet_mixed_bar(Lx, L, n_s, nf):
     # FP32 slice products as D_l (Y + F Y), F = E - I split into two FP32 terms, block-compensated
     # accumulation (FP64 QR / LU): |d ln w| <= 1e-4.
