@@ -625,11 +625,10 @@ def run_gpu(args):
 def run_uneven_batch(args, dev, seed):
     """Uneven batch: 64 chains each of 8x8/L=80, 10x10/L=100, 12x12/L=120, 16x16/L=160 (beta = L dtau),
     FP32 slices, n_s and tiles autotuned per class, advanced round by round (one cumulative update of
-    every chain per round, 20 E_eff sweeps each) by replaying one captured CUDA graph."""
-    import torch
-
-    from paper_1802_06177_gb300 import inputs
-    from paper_1802_06177_gb300.slmc import Batch, autotune
+    every chain per round, 20 E_eff sweeps each) by replaying one captured CUDA graph. Per update the
+    E_eff sweeps of all 256 chains run in one persistent queue launch; the same batch with each
+    class's kernel-per-half-sweep sequence instead is timed beside it."""
+    from paper_1802_06177_gb300.slmc import autotune
     from paper_1802_06177_gb300.workloads import UNEVEN_BATCH
     tuned, classes = {}, []
     for Lx, L, n in UNEVEN_BATCH:
@@ -638,7 +637,19 @@ def run_uneven_batch(args, dev, seed):
                                             "slice_cols": r["slice_cols"], "max_abs_dlndet": r["max_abs_dlndet"]}
         classes.append(dict(Lx=Lx, L=L, nchains=n, n_s=r["n_s"], precision="fp32", seed=seed, sweep_delta=0.3,
                             tuning=(r["qr_panel"], r["slice_cols"])))
+    out = _time_uneven(args, dev, seed, classes, queue=True)
+    out["per_class_kernels"] = _time_uneven(args, dev, seed, classes, queue=False)
+    out["tuned"] = tuned
+    return out
+
+
+def _time_uneven(args, dev, seed, classes, queue):
+    import torch
+
+    from paper_1802_06177_gb300 import inputs
+    from paper_1802_06177_gb300.slmc import Batch
     b = Batch([{k: v for k, v in cl.items() if k != "tuning"} for cl in classes], device=dev)
+    b.set_sweep_queue(queue)
     keep = []
     with torch.cuda.stream(b.stream):
         for q, cl in enumerate(classes):
@@ -652,7 +663,7 @@ def run_uneven_batch(args, dev, seed):
             n_acc = torch.zeros(cl["nchains"], dtype=torch.int64, device=dev)
             ctx.set_update_counter(0)
             b.bind(q, x, J, lnw, s, n_acc)
-            keep.append((x, J, lnw, s, n_acc))
+            keep.append((x, J, lnw, s, n_acc, ctx))
     b.stream.synchronize()
     b.capture(args.nsweeps, 1)
     b.launch(2)
@@ -662,12 +673,15 @@ def run_uneven_batch(args, dev, seed):
     e1.record(b.stream)
     b.stream.synchronize()
     ms = e0.elapsed_time(e1)
+    with torch.cuda.stream(b.stream):
+        for k in keep:
+            k[5].get_error()
     nch = sum(cl["nchains"] for cl in classes)
     acc = sum(int(k[4].sum().item()) for k in keep) / float(nch * (args.batch_rounds + 2))
     b.close()
     return {"evals_per_s": nch * args.batch_rounds / (ms / 1e3), "chains": nch, "rounds_timed": args.batch_rounds,
             "ms_per_round": ms / args.batch_rounds, "graph_launch_per_round": 1, "nsweeps": args.nsweeps,
-            "acceptance": acc, "tuned": tuned}
+            "sweep_queue": queue, "acceptance": acc}
 
 
 # ---------------------------------------------------------------------------------------

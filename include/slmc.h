@@ -378,12 +378,21 @@ SLMC_API int slmc_profile_read_detail(slmc_ctx* ctx, double* ms, long long* call
 /* ---- Batches of chains of uneven size in one CUDA graph ----------------------------------
  * A batch owns one context per lattice class (nclasses parameter sets, nchains[c] chains
  * each) and one non-blocking stream per class. After the chain buffers of every class are
- * bound, slmc_batch_capture records one round -- nupdates cumulative updates of every class,
- * the classes as concurrent branches forked from and joined back to `stream` -- into a CUDA
- * graph; slmc_batch_launch replays it. Each round continues every class's device-side update
- * counter, so replays reproduce exactly the random streams of successive direct calls to
- * slmc_cumulative_update with SLMC_UPDATE_CONTINUE. `stream` must be a created stream (not the
- * legacy default stream). Buffer layouts and ownership are those of slmc_cumulative_update. */
+ * bound, slmc_batch_capture records one round -- nupdates cumulative updates of every class
+ * [Eq. (6)] -- into a CUDA graph; slmc_batch_launch replays it. Each update of the round runs
+ * (1) the classes' draws and F(x) as concurrent branches forked from and joined back to `stream`,
+ * (2) ONE persistent launch for the E_eff Markov chain of every chain of every class: the CTAs
+ * pull half-sweep slabs and Wolff updates from a device work queue that lists, phase after
+ * phase, the chains in order of decreasing N L; an item waits (bounded, about 2 s) until its
+ * chain's earlier items are done, and a wait that gives up sets SLMC_ERR_TIMEOUT in every
+ * class's context (slmc_get_error) and stops the queue; and (3) the classes' ln w with G,
+ * acceptances and S(pi, pi) as concurrent branches. Each round continues every class's
+ * device-side update counter, so replays reproduce bit for bit the random streams and results
+ * of successive direct calls to slmc_cumulative_update with SLMC_UPDATE_CONTINUE (the queue
+ * runs the same site and Wolff arithmetic). `stream` must be a created stream (not the legacy
+ * default stream). Buffer layouts and ownership are those of slmc_cumulative_update. The queue
+ * table (16 bytes per item; an item is 1024 sites of a half-sweep or one Wolff update of one
+ * chain) is allocated at capture. */
 typedef struct slmc_batch slmc_batch;
 SLMC_API int slmc_batch_create(const slmc_params* classes, const int* nchains, int nclasses, slmc_batch** out);
 SLMC_API int slmc_batch_destroy(slmc_batch* batch);
@@ -392,6 +401,14 @@ SLMC_API slmc_ctx* slmc_batch_context(slmc_batch* batch, int cls);
 SLMC_API int slmc_batch_bind(slmc_batch* batch, int cls, double* x, const double* J, double* lnw, double* s_cdw,
                              long long* n_acc, long long* n_sweep_acc);
 SLMC_API int slmc_batch_capture(slmc_batch* batch, int nsweeps, int nupdates, void* stream);
+/* on = 1 (default): step (2) above is the persistent queue launch; on = 0: each class runs its
+ * own kernel-per-half-sweep sequence on its branch. Takes effect at the next capture. */
+SLMC_API int slmc_batch_set_sweep_queue(slmc_batch* batch, int on);
+/* Test hook of the bounded waits: with wait_cycles > 0 the next capture's first queue item
+ * waits for a completion count that no item reaches, and every queue wait gives up after
+ * wait_cycles clock cycles, so the replay ends with SLMC_ERR_TIMEOUT in every class's context
+ * and the device stays usable. 0 restores the normal queue at the next capture. */
+SLMC_API int slmc_batch_inject_stall(slmc_batch* batch, long long wait_cycles);
 SLMC_API int slmc_batch_launch(slmc_batch* batch, int nrounds, void* stream);
 
 /* ---- Autotuner ------------------------------------------------------------------------------

@@ -276,6 +276,79 @@ int validate_params(const slmc_params* p) { return validate(p); }
 int logdet_fields(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, cudaStream_t s) {
     return logdet_batch(c, x, nf, lndet, sign, nullptr, s);
 }
+
+// Updates [u0, u1) of the cumulative-update cycle [Eq. (6)] of chains [0, n), restricted to the
+// phases in the mask: kPhasePre (the update's draws, the saved field, F(x) of E_eff), kPhaseSweeps
+// (the E_eff Markov chain: nsweeps checkerboard sweeps with the Wolff updates between their two
+// colours) and kPhasePost (F(x') of E_eff, ln w with G, the acceptance and S). Chains are
+// independent: a batch is split into sub-batches (as for slmc_logdet), each running its updates on
+// its own forked stream, so the sweeps of one sub-batch overlap the determinants of another. The
+// arithmetic of a chain does not depend on the split or on the phases being run apart.
+int cumulative_phases(slmc_ctx* c, double* x, int n, const double* J, int nsweeps, int u0, int u1, int phases,
+                      double* lnw, double* s_cdw, long long* n_acc, long long* n_sweep_acc, double* obs,
+                      cudaStream_t s) {
+    const size_t NL = (size_t)c->N * c->L;
+    return for_batches(c, n, [&](int f0, int nf) {
+        const bool tc = c->p.precision == SLMC_PREC_TF32X3;
+        int nsub = std::min(c->nsub, nf / kMinSubFields);
+        if (nsub < 2 || tc || !(phases & kPhasePost)) nsub = 1;
+        if (nsub > 1) SLMC_CK(cudaEventRecord(c->sub_fork, s));
+        for (int k = 0; k < nsub; ++k) {
+            const int a = (int)((long long)k * nf / nsub), b = (int)((long long)(k + 1) * nf / nsub), m = b - a;
+            cudaStream_t sk = nsub == 1 ? s : (c->sub_prio ? c->sub_stream_prio[k] : c->sub_stream[k]);
+            if (nsub > 1) SLMC_CK(cudaStreamWaitEvent(sk, c->sub_fork, 0));
+            slmc_ctx view = make_view(c, a);
+            slmc_ctx* v = nsub == 1 ? c : &view;
+            const int g0 = f0 + a;  // first chain of the sub-batch
+            double* xc = x + (size_t)g0 * NL;
+            double* xo = c->x_old + (size_t)a * NL;
+            auto sc = [&](int col) { return scal(c, col) + a; };
+            auto isc = [&](int col) { return iscal(c, col) + a; };
+            for (int u = u0; u < u1; ++u) {
+                c->cur_units = m;
+                if (phases & kPhasePre) {
+                    SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, sk, update_draws(c, m, g0, (uint64_t)u, isc(1), sc(4), sk));
+                    SLMC_CK(cudaMemcpyAsync(xo, xc, m * NL * sizeof(double), cudaMemcpyDeviceToDevice, sk));
+                    SLMC_LAUNCH(SLMC_PROF_EFF, 1, sk, eff_features(c, xc, m, J, nullptr, 0, sc(1), sk));
+                }
+                if (phases & kPhaseSweeps)
+                    for (int sw = 0; sw < nsweeps; ++sw)
+                        for (int h = 0; h < 2; ++h) {
+                            if (h == 1)  // Wolff cluster updates between the two colours of the sweep
+                                for (int k = 0; k < c->nwolff; ++k)
+                                    SLMC_LAUNCH(SLMC_PROF_WOLFF, 1, sk,
+                                                eff_wolff(c, xc, m, g0, J, (uint64_t)u * nsweeps + sw, k, sk, c->dctr,
+                                                          nsweeps));
+                            SLMC_LAUNCH(SLMC_PROF_SWEEP, 1, sk,
+                                        eff_half_sweep(c, xc, m, g0, J, (uint64_t)u * nsweeps + sw, 0, isc(1), h,
+                                                       n_sweep_acc ? n_sweep_acc + g0 : nullptr, sk, c->dctr,
+                                                       nsweeps));
+                        }
+                if (phases & kPhasePost) {
+                    SLMC_LAUNCH(SLMC_PROF_EFF, 1, sk, eff_features(c, xc, m, J, nullptr, 0, sc(2), sk));
+                    SLMC_TRY(logdet_run(c, v, xc, m, sc(0), isc(0), s_cdw ? v->QR : nullptr, sk));
+                    c->cur_units = m;
+                    SLMC_LAUNCH(SLMC_PROF_BOSE, 1, sk, bose_log_weight(c, xc, m, sc(0), sc(3), sk));
+                    SLMC_LAUNCH(SLMC_PROF_ACCEPT, 2, sk,
+                                accept_update(c, m, xc, xo, sc(3), sc(1), sc(2), sc(4), lnw + g0, isc(2),
+                                              n_acc ? n_acc + g0 : nullptr, sk));
+                    if (s_cdw)
+                        SLMC_LAUNCH(SLMC_PROF_CDW, 1, sk,
+                                    cdw_measure(c, v->QR, m, s_cdw + g0, isc(2),
+                                                obs ? obs + (size_t)u * n + g0 : nullptr, sk));
+                }
+            }
+            if (nsub > 1) {
+                SLMC_CK(cudaEventRecord(c->sub_join[k], sk));
+                SLMC_CK(cudaStreamWaitEvent(s, c->sub_join[k], 0));
+            }
+        }
+        return SLMC_OK;
+    });
+}
+
+// Device pointers of a class's per-chain draws (first colour of each chain's sweeps).
+const int* first_colours(slmc_ctx* c) { return iscal(c, 1); }
 }  // namespace slmc
 
 extern "C" {
@@ -522,63 +595,10 @@ int slmc_cumulative_update(slmc_ctx* c, double* x, int n, const double* J, int n
     if (!c || n < 0 || nsweeps < 0 || nupdates < 0 || (n > 0 && (!x || !J || !lnw)) || (obs && !s_cdw))
         return SLMC_ERR_ARG;
     if (!checkerboard_ok(c)) return SLMC_ERR_UNSUPPORTED;
-    const size_t NL = (size_t)c->N * c->L;
     cudaStream_t s = as_stream(stream);
     if (update0 != SLMC_UPDATE_CONTINUE) SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::counter_op(c, update0, false, s));
-    // Chains are independent: a batch is split into sub-batches (as for slmc_logdet), each running all
-    // its updates (sweeps, E_eff, ln w with G, Eq. (6), S) on its own forked stream, so the sweeps of one
-    // sub-batch overlap the determinants of another.
-    SLMC_TRY(for_batches(c, n, [&](int f0, int nf) {
-        const bool tc = c->p.precision == SLMC_PREC_TF32X3;
-        int nsub = std::min(c->nsub, nf / kMinSubFields);
-        if (nsub < 2 || tc) nsub = 1;
-        if (nsub > 1) SLMC_CK(cudaEventRecord(c->sub_fork, s));
-        for (int k = 0; k < nsub; ++k) {
-            const int a = (int)((long long)k * nf / nsub), b = (int)((long long)(k + 1) * nf / nsub), m = b - a;
-            cudaStream_t sk = nsub == 1 ? s : (c->sub_prio ? c->sub_stream_prio[k] : c->sub_stream[k]);
-            if (nsub > 1) SLMC_CK(cudaStreamWaitEvent(sk, c->sub_fork, 0));
-            slmc_ctx view = make_view(c, a);
-            slmc_ctx* v = nsub == 1 ? c : &view;
-            const int g0 = f0 + a;  // first chain of the sub-batch
-            double* xc = x + (size_t)g0 * NL;
-            double* xo = c->x_old + (size_t)a * NL;
-            auto sc = [&](int col) { return scal(c, col) + a; };
-            auto isc = [&](int col) { return iscal(c, col) + a; };
-            for (int u = 0; u < nupdates; ++u) {
-                c->cur_units = m;
-                SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, sk, slmc::update_draws(c, m, g0, (uint64_t)u, isc(1), sc(4), sk));
-                SLMC_CK(cudaMemcpyAsync(xo, xc, m * NL * sizeof(double), cudaMemcpyDeviceToDevice, sk));
-                SLMC_LAUNCH(SLMC_PROF_EFF, 1, sk, slmc::eff_features(c, xc, m, J, nullptr, 0, sc(1), sk));
-                for (int sw = 0; sw < nsweeps; ++sw)
-                    for (int h = 0; h < 2; ++h) {
-                        if (h == 1)  // Wolff cluster updates between the two colours of the sweep
-                            for (int k = 0; k < c->nwolff; ++k)
-                                SLMC_LAUNCH(SLMC_PROF_WOLFF, 1, sk,
-                                            slmc::eff_wolff(c, xc, m, g0, J, (uint64_t)u * nsweeps + sw, k, sk,
-                                                            c->dctr, nsweeps));
-                        SLMC_LAUNCH(SLMC_PROF_SWEEP, 1, sk,
-                                    slmc::eff_half_sweep(c, xc, m, g0, J, (uint64_t)u * nsweeps + sw, 0, isc(1), h,
-                                                         n_sweep_acc ? n_sweep_acc + g0 : nullptr, sk, c->dctr, nsweeps));
-                    }
-                SLMC_LAUNCH(SLMC_PROF_EFF, 1, sk, slmc::eff_features(c, xc, m, J, nullptr, 0, sc(2), sk));
-                SLMC_TRY(logdet_run(c, v, xc, m, sc(0), isc(0), s_cdw ? v->QR : nullptr, sk));
-                c->cur_units = m;
-                SLMC_LAUNCH(SLMC_PROF_BOSE, 1, sk, slmc::bose_log_weight(c, xc, m, sc(0), sc(3), sk));
-                SLMC_LAUNCH(SLMC_PROF_ACCEPT, 2, sk,
-                            slmc::accept_update(c, m, xc, xo, sc(3), sc(1), sc(2), sc(4), lnw + g0, isc(2),
-                                                n_acc ? n_acc + g0 : nullptr, sk));
-                if (s_cdw)
-                    SLMC_LAUNCH(SLMC_PROF_CDW, 1, sk,
-                                slmc::cdw_measure(c, v->QR, m, s_cdw + g0, isc(2),
-                                                  obs ? obs + (size_t)u * n + g0 : nullptr, sk));
-            }
-            if (nsub > 1) {
-                SLMC_CK(cudaEventRecord(c->sub_join[k], sk));
-                SLMC_CK(cudaStreamWaitEvent(s, c->sub_join[k], 0));
-            }
-        }
-        return SLMC_OK;
-    }));
+    SLMC_TRY(slmc::cumulative_phases(c, x, n, J, nsweeps, 0, nupdates, slmc::kPhaseAll, lnw, s_cdw, n_acc,
+                                     n_sweep_acc, obs, s));
     if (nupdates > 0) SLMC_LAUNCH(SLMC_PROF_ACCEPT, 1, s, slmc::counter_op(c, (uint64_t)nupdates, true, s));
     return SLMC_OK;
 }

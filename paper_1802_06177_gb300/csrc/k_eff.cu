@@ -96,8 +96,80 @@ __device__ __forceinline__ double local_energy(const double* J, double a2, doubl
            J[3] * (v2 * v2 * v2 * (1.0 / 6.0) - a2 * v2 * v2 * 0.25) + J[4] * v * nb + J[5] * v * (up + dn);
 }
 
-// One checkerboard half-sweep over all chains. Thread s of chain f owns site i = s / (L/2)
-// and the slice l of the requested colour in the pair (2 (s mod L/2), 2 (s mod L/2) + 1).
+// Loads of the field: plain (cached) in the per-colour kernels, L2-only (ld.global.cg) in the
+// persistent queue kernel, whose CTAs read values that other CTAs of the same launch wrote.
+template <bool kL2>
+__device__ __forceinline__ double ldx(const double* p) {
+    if (kL2) return __ldcg(p);
+    return *p;
+}
+
+// Metropolis update of site pair s of colour c in one chain's field (thread s of the half-sweep
+// owns site i = s / (L/2) and the slice l of colour c in the pair (2 (s mod L/2), 2 (s mod L/2) + 1)).
+// Returns 1 if the move was accepted (and written).
+template <bool kL2>
+__device__ __forceinline__ int site_update(double* xfield, int Lx, int Ly, int L, const double* J, double dtau,
+                                           double a2, double delta, uint32_t key0, uint32_t key1, uint32_t sweep,
+                                           int c, int s, uint32_t chain) {
+    const int half = L / 2;
+    const int i = s / half, lp = s - i * half;
+    const int ix = i % Lx, iy = i / Lx;
+    const int l = 2 * lp + ((ix + iy + c) & 1);
+    const double v = ldx<kL2>(xfield + (size_t)i * L + l);
+    const double up = ldx<kL2>(xfield + (size_t)i * L + (l + 1 == L ? 0 : l + 1));
+    const double dn = ldx<kL2>(xfield + (size_t)i * L + (l == 0 ? L - 1 : l - 1));
+    const int xp = (ix + 1 == Lx ? 0 : ix + 1) + Lx * iy, xm = (ix == 0 ? Lx - 1 : ix - 1) + Lx * iy;
+    const int yp = ix + Lx * (iy + 1 == Ly ? 0 : iy + 1), ym = ix + Lx * (iy == 0 ? Ly - 1 : iy - 1);
+    const double nb = ldx<kL2>(xfield + (size_t)xp * L + l) + ldx<kL2>(xfield + (size_t)xm * L + l) +
+                      ldx<kL2>(xfield + (size_t)yp * L + l) + ldx<kL2>(xfield + (size_t)ym * L + l);
+    const slmc::u32x4 w = slmc::philox4x32_10(slmc::u32x4{(uint32_t)(i * L + l), sweep, chain, 0u}, key0, key1);
+    const double u1 = slmc::uniform53(w.x, w.y);
+    // x' = x + delta (2 u1 - 1), rounded step by step (no contraction) as in the oracle
+    const double xn = __dadd_rn(v, __dmul_rn(delta, __dadd_rn(__dmul_rn(2.0, u1), -1.0)));
+    // Fast decision in FP32: dE = d [2 J_k (s - up - dn) + s (J_p ((x'^2 + x^2)/4 - a^2/2)
+    //   + J_p' ((x'^4 + x'^2 x^2 + x^4)/6 - a^2 (x'^2 + x^2)/4)) + J_nn nb + J_nn' (up + dn)],
+    // d = x' - x, s = x' + x (the exact difference of the local energies, factored). The FP32
+    // verdict is used only when the log-ratio is further from log u than a margin bounding
+    // (i) the FP32 rounding of the bracket (1e-5 of the sum of the magnitudes of its terms,
+    // about 170 units of FP32 rounding), (ii) the rounding of x, x' to FP32, which moves d by
+    // up to 2^-24 (|x| + |x'|), and (iii) the truncation of u to 24 bits (log u is known to
+    // within 2^-24 / u); otherwise the exact FP64 rule of the oracle decides.
+    const float vf = (float)v, xf = (float)xn, upf = (float)up, dnf = (float)dn, nbf = (float)nb;
+    const float d = xf - vf, sm = xf + vf, x2 = xf * xf, v2 = vf * vf, a2f = (float)a2;
+    const float tk = 2.f * (float)J[1] * (sm - upf - dnf);
+    const float tp = sm * (float)J[2] * (0.25f * (x2 + v2) - 0.5f * a2f);
+    const float tpp = sm * (float)J[3] * ((x2 * x2 + x2 * v2 + v2 * v2) * (1.f / 6.f) - 0.25f * a2f * (x2 + v2));
+    const float tn = (float)J[4] * nbf + (float)J[5] * (upf + dnf);
+    const float mag = 2.f * fabsf((float)J[1]) * (fabsf(sm) + fabsf(upf) + fabsf(dnf)) +
+                      fabsf(sm) * (fabsf((float)J[2]) * (x2 + v2 + a2f) +
+                                   fabsf((float)J[3]) * (x2 * x2 + x2 * v2 + v2 * v2 + a2f * (x2 + v2))) +
+                      fabsf((float)J[4] * nbf) + fabsf((float)J[5]) * (fabsf(upf) + fabsf(dnf));
+    const float dlnw32 = -(float)dtau * d * (tk + tp + tpp + tn);
+    const float uf = (float)(w.z >> 8) * 5.9604644775390625e-8f;  // top 24 bits of the acceptance uniform
+    int decided = 0, acc = 0;
+    if (uf > 0.f && isfinite(dlnw32) && isfinite(mag)) {
+        const float lu = logf(uf);
+        const float margin =
+            1e-5f + (float)dtau * mag * (1e-5f * fabsf(d) + 2e-7f * (fabsf(xf) + fabsf(vf))) + 1.2e-7f / uf;
+        if (dlnw32 > lu + margin) {
+            decided = 1;
+            acc = 1;
+        } else if (dlnw32 < lu - margin) {
+            decided = 1;
+            acc = 0;
+        }
+    }
+    if (!decided) {  // exact FP64 rule of the oracle
+        const double u2 = slmc::uniform53(w.z, w.w);
+        const double dE = local_energy(J, a2, xn, up, dn, nb) - local_energy(J, a2, v, up, dn, nb);
+        const double dlnw = -dtau * dE;
+        acc = (dlnw >= 0.0 || u2 < exp(dlnw)) ? 1 : 0;
+    }
+    if (acc) xfield[(size_t)i * L + l] = xn;
+    return acc;
+}
+
+// One checkerboard half-sweep over all chains: thread s of chain f updates site pair s.
 __global__ void __launch_bounds__(kThreads) k_half_sweep(double* __restrict__ x, int Lx, int Ly, int L,
                                                          const double* __restrict__ Jg, double dtau, double a2,
                                                          double delta, uint32_t key0, uint32_t key1, uint32_t sweep_arg,
@@ -117,64 +189,8 @@ __global__ void __launch_bounds__(kThreads) k_half_sweep(double* __restrict__ x,
     int accepted = 0;
     if (s < N * half) {
         const int c = colour_pc ? (colour_pc[f] ^ cxor) : colour;
-        const int i = s / half, lp = s - i * half;
-        const int ix = i % Lx, iy = i / Lx;
-        const int l = 2 * lp + ((ix + iy + c) & 1);
-        double* xfield = x + (size_t)f * N * L;
-        const double v = xfield[(size_t)i * L + l];
-        const double up = xfield[(size_t)i * L + (l + 1 == L ? 0 : l + 1)];
-        const double dn = xfield[(size_t)i * L + (l == 0 ? L - 1 : l - 1)];
-        const int xp = (ix + 1 == Lx ? 0 : ix + 1) + Lx * iy, xm = (ix == 0 ? Lx - 1 : ix - 1) + Lx * iy;
-        const int yp = ix + Lx * (iy + 1 == Ly ? 0 : iy + 1), ym = ix + Lx * (iy == 0 ? Ly - 1 : iy - 1);
-        const double nb = xfield[(size_t)xp * L + l] + xfield[(size_t)xm * L + l] + xfield[(size_t)yp * L + l] +
-                          xfield[(size_t)ym * L + l];
-        const slmc::u32x4 w = slmc::philox4x32_10(slmc::u32x4{(uint32_t)(i * L + l), sweep, (uint32_t)(chain0 + f), 0u}, key0, key1);
-        const double u1 = slmc::uniform53(w.x, w.y);
-        // x' = x + delta (2 u1 - 1), rounded step by step (no contraction) as in the oracle
-        const double xn = __dadd_rn(v, __dmul_rn(delta, __dadd_rn(__dmul_rn(2.0, u1), -1.0)));
-        // Fast decision in FP32: dE = d [2 J_k (s - up - dn) + s (J_p ((x'^2 + x^2)/4 - a^2/2)
-        //   + J_p' ((x'^4 + x'^2 x^2 + x^4)/6 - a^2 (x'^2 + x^2)/4)) + J_nn nb + J_nn' (up + dn)],
-        // d = x' - x, s = x' + x (the exact difference of the local energies, factored). The FP32
-        // verdict is used only when the log-ratio is further from log u than a margin bounding
-        // (i) the FP32 rounding of the bracket (1e-5 of the sum of the magnitudes of its terms,
-        // about 170 units of FP32 rounding), (ii) the rounding of x, x' to FP32, which moves d by
-        // up to 2^-24 (|x| + |x'|), and (iii) the truncation of u to 24 bits (log u is known to
-        // within 2^-24 / u); otherwise the exact FP64 rule of the oracle decides.
-        const float vf = (float)v, xf = (float)xn, upf = (float)up, dnf = (float)dn, nbf = (float)nb;
-        const float d = xf - vf, sm = xf + vf, x2 = xf * xf, v2 = vf * vf, a2f = (float)a2;
-        const float tk = 2.f * (float)J[1] * (sm - upf - dnf);
-        const float tp = sm * (float)J[2] * (0.25f * (x2 + v2) - 0.5f * a2f);
-        const float tpp = sm * (float)J[3] * ((x2 * x2 + x2 * v2 + v2 * v2) * (1.f / 6.f) - 0.25f * a2f * (x2 + v2));
-        const float tn = (float)J[4] * nbf + (float)J[5] * (upf + dnf);
-        const float mag = 2.f * fabsf((float)J[1]) * (fabsf(sm) + fabsf(upf) + fabsf(dnf)) +
-                          fabsf(sm) * (fabsf((float)J[2]) * (x2 + v2 + a2f) +
-                                       fabsf((float)J[3]) * (x2 * x2 + x2 * v2 + v2 * v2 + a2f * (x2 + v2))) +
-                          fabsf((float)J[4] * nbf) + fabsf((float)J[5]) * (fabsf(upf) + fabsf(dnf));
-        const float dlnw32 = -(float)dtau * d * (tk + tp + tpp + tn);
-        const float uf = (float)(w.z >> 8) * 5.9604644775390625e-8f;  // top 24 bits of the acceptance uniform
-        int decided = 0, acc = 0;
-        if (uf > 0.f && isfinite(dlnw32) && isfinite(mag)) {
-            const float lu = logf(uf);
-            const float margin =
-                1e-5f + (float)dtau * mag * (1e-5f * fabsf(d) + 2e-7f * (fabsf(xf) + fabsf(vf))) + 1.2e-7f / uf;
-            if (dlnw32 > lu + margin) {
-                decided = 1;
-                acc = 1;
-            } else if (dlnw32 < lu - margin) {
-                decided = 1;
-                acc = 0;
-            }
-        }
-        if (!decided) {  // exact FP64 rule of the oracle
-            const double u2 = slmc::uniform53(w.z, w.w);
-            const double dE = local_energy(J, a2, xn, up, dn, nb) - local_energy(J, a2, v, up, dn, nb);
-            const double dlnw = -dtau * dE;
-            acc = (dlnw >= 0.0 || u2 < exp(dlnw)) ? 1 : 0;
-        }
-        if (acc) {
-            xfield[(size_t)i * L + l] = xn;
-            accepted = 1;
-        }
+        accepted = site_update<false>(x + (size_t)f * N * L, Lx, Ly, L, J, dtau, a2, delta, key0, key1, sweep, c, s,
+                                      (uint32_t)(chain0 + f));
     }
     const unsigned int ballot = __ballot_sync(0xffffffffu, accepted);
     if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(&s_cnt, __popc(ballot));
@@ -192,21 +208,14 @@ __global__ void __launch_bounds__(kThreads) k_half_sweep(double* __restrict__ x,
 // the activated bonds is found by label propagation in shared memory (marks only go from 0 to 1,
 // so at most N + 1 rounds) and its columns are reflected, x -> -x. Every other term of E_eff is
 // invariant under reflecting whole columns: the move is always accepted.
-__global__ void __launch_bounds__(256) k_wolff(double* __restrict__ x, int Lx, int Ly, int L,
-                                               const double* __restrict__ Jg, double dtau, uint32_t key0,
-                                               uint32_t key1, uint32_t sweep_arg,
-                                               const unsigned long long* __restrict__ dctr, int nsweeps, int nwolff,
-                                               int k, int chain0, unsigned long long* __restrict__ n_sites) {
-    extern __shared__ unsigned char wsm[];
-    const int N = Lx * Ly;
-    unsigned char* act = wsm;        // [2N] activated bond terms
-    unsigned char* in_c = wsm + 2 * N;  // [N] cluster marks
-    __shared__ int s_seed, s_cnt;
-    const int f = blockIdx.x, tid = threadIdx.x;
-    double* __restrict__ xf = x + (size_t)f * N * L;
-    const uint32_t sweep = dctr ? (uint32_t)((*dctr) * (unsigned long long)nsweeps + sweep_arg) : sweep_arg;
-    const uint32_t ctr = sweep * (uint32_t)nwolff + (uint32_t)k;
-    const uint32_t chain = (uint32_t)(chain0 + f);
+// One Wolff cluster update of one chain's field xf by the whole CTA (blockDim.x threads); act and
+// in_c are 2N and N bytes of shared memory; counter ctr, Philox chain index chain.
+template <bool kL2>
+__device__ __forceinline__ void wolff_chain(double* xf, int Lx, int Ly, int L, const double* __restrict__ Jg,
+                                            double dtau, uint32_t key0, uint32_t key1, uint32_t ctr, uint32_t chain,
+                                            unsigned char* act, unsigned char* in_c, int* s_seed, int* s_cnt,
+                                            unsigned long long* __restrict__ n_sites) {
+    const int N = Lx * Ly, tid = threadIdx.x;
     const double cfac = __dmul_rn(__dmul_rn(2.0, dtau), Jg[4]);
     for (int b = tid; b < 2 * N; b += blockDim.x) {
         const int i = b >> 1, ix = i % Lx, iy = i / Lx;
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(256) k_wolff(double* __restrict__ x, int Lx, i
         const double* xi = xf + (size_t)i * L;
         const double* xj = xf + (size_t)j * L;
         double sb = 0.0;
-        for (int l = 0; l < L; ++l) sb = __dadd_rn(sb, __dmul_rn(xi[l], xj[l]));
+        for (int l = 0; l < L; ++l) sb = __dadd_rn(sb, __dmul_rn(ldx<kL2>(xi + l), ldx<kL2>(xj + l)));
         const double t = __dmul_rn(cfac, sb);
         unsigned char a = 0;
         if (t < 0.0) {
@@ -226,11 +235,11 @@ __global__ void __launch_bounds__(256) k_wolff(double* __restrict__ x, int Lx, i
     if (tid == 0) {
         const slmc::u32x4 w = slmc::philox4x32_10(slmc::u32x4{(uint32_t)(2 * N), ctr, chain, 2u}, key0, key1);
         const int s0 = (int)(slmc::uniform53(w.x, w.y) * (double)N);
-        s_seed = s0 < N - 1 ? s0 : N - 1;
-        s_cnt = 0;
+        *s_seed = s0 < N - 1 ? s0 : N - 1;
+        *s_cnt = 0;
     }
     __syncthreads();
-    for (int i = tid; i < N; i += blockDim.x) in_c[i] = (i == s_seed);
+    for (int i = tid; i < N; i += blockDim.x) in_c[i] = (i == *s_seed);
     __syncthreads();
     for (int round = 0; round <= N; ++round) {
         int changed = 0;
@@ -249,11 +258,118 @@ __global__ void __launch_bounds__(256) k_wolff(double* __restrict__ x, int Lx, i
     int cnt = 0;
     for (int i = tid; i < N; i += blockDim.x) cnt += in_c[i];
     for (size_t idx = tid; idx < (size_t)N * L; idx += blockDim.x)
-        if (in_c[idx / L]) xf[idx] = -xf[idx];
+        if (in_c[idx / L]) xf[idx] = -ldx<kL2>(xf + idx);
     if (n_sites) {
-        atomicAdd(&s_cnt, cnt);
+        atomicAdd(s_cnt, cnt);
         __syncthreads();
-        if (tid == 0) atomicAdd(n_sites, (unsigned long long)s_cnt);
+        if (tid == 0) atomicAdd(n_sites, (unsigned long long)*s_cnt);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_wolff(double* __restrict__ x, int Lx, int Ly, int L,
+                                               const double* __restrict__ Jg, double dtau, uint32_t key0,
+                                               uint32_t key1, uint32_t sweep_arg,
+                                               const unsigned long long* __restrict__ dctr, int nsweeps, int nwolff,
+                                               int k, int chain0, unsigned long long* __restrict__ n_sites) {
+    extern __shared__ unsigned char wsm[];
+    const int N = Lx * Ly;
+    __shared__ int s_seed, s_cnt;
+    const int f = blockIdx.x;
+    const uint32_t sweep = dctr ? (uint32_t)((*dctr) * (unsigned long long)nsweeps + sweep_arg) : sweep_arg;
+    const uint32_t ctr = sweep * (uint32_t)nwolff + (uint32_t)k;
+    wolff_chain<false>(x + (size_t)f * N * L, Lx, Ly, L, Jg, dtau, key0, key1, ctr, (uint32_t)(chain0 + f), wsm,
+                       wsm + 2 * N, &s_seed, &s_cnt, n_sites);
+}
+
+// Persistent E_eff sweep queue: the half-sweep slabs and Wolff updates of every chain of several
+// lattice classes, pulled in queue order by the CTAs of one launch. The queue lists, phase after
+// phase (colour 0, the Wolff updates, colour 1 of each sweep), the items of every chain in order of
+// decreasing N L (longest first), so every item depends only on earlier ones: item q of chain g
+// waits until g's completion counter reaches its count of g's earlier items. A CTA takes an item
+// only while it runs, so all items it waits on are held by running CTAs, and the launch cannot
+// deadlock whatever the grid size. Values written by other CTAs of the launch are read through L2
+// (__ldcg); a CTA publishes an item after a barrier and a device-scope fence. The arithmetic of a
+// site update or a Wolff update is the one of k_half_sweep / k_wolff (shared device functions), so
+// the chains are bit-identical to the kernel-per-half-sweep path.
+//
+// Every wait is bounded: after wait_cycles the CTA sets SLMC_EBIT_TIMEOUT in the error word of
+// every class and the abort word ctl[1]; every CTA stops taking items once it sees the abort.
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sweep_queue(const slmc::QueueClass* __restrict__ cls, int ncls,
+                                                          const int4* __restrict__ items, int nitems,
+                                                          unsigned int* __restrict__ done, unsigned int* __restrict__ ctl,
+                                                          uint32_t u, long long wait_cycles) {
+    extern __shared__ unsigned char qsm[];
+    __shared__ double J[6];
+    __shared__ int s_item, s_cnt, s_seed, s_wcnt;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int q = -1;
+            if (ld_acquire_u32(ctl + 1) == 0u) q = (int)atomicAdd(ctl, 1u);
+            if (q >= nitems) q = -1;
+            if (q >= 0) {
+                const int4 it = items[q];
+                const slmc::QueueClass& C = cls[it.x >> 24];
+                const unsigned int* cnt = done + C.done0 + (it.x & 0xffffff);
+                const long long t0 = clock64();
+                while (ld_acquire_u32(cnt) < (unsigned int)it.w) {
+                    if (ld_acquire_u32(ctl + 1) != 0u) {
+                        q = -1;
+                        break;
+                    }
+                    if (clock64() - t0 > wait_cycles) {
+                        for (int k = 0; k < ncls; ++k) atomicOr(cls[k].err, SLMC_EBIT_TIMEOUT);
+                        atomicExch(ctl + 1, 1u);
+                        q = -1;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            s_item = q;
+            s_cnt = 0;
+        }
+        __syncthreads();
+        const int q = s_item;
+        if (q < 0) break;
+        const int4 it = items[q];
+        const slmc::QueueClass& C = cls[it.x >> 24];
+        const int f = it.x & 0xffffff;
+        if (threadIdx.x < 6) J[threadIdx.x] = C.J[threadIdx.x];
+        __syncthreads();
+        const int N = C.Lx * C.Ly;
+        double* xf = C.x + (size_t)f * N * C.L;
+        const int sw = it.y >> 8, sub = it.y & 0x7f;
+        const uint32_t chain = (uint32_t)f;
+        const uint32_t sweep = (uint32_t)((*C.dctr) * (unsigned long long)C.nsweeps +
+                                          (unsigned long long)u * C.nsweeps + sw);
+        if (it.y & 0x80) {
+            const uint32_t ctr = sweep * (uint32_t)C.nwolff + (uint32_t)sub;
+            wolff_chain<true>(xf, C.Lx, C.Ly, C.L, J, C.dtau, C.key0, C.key1, ctr, chain, qsm, qsm + 2 * N, &s_seed,
+                              &s_wcnt, C.wolff_sites);
+        } else {
+            const int sites = N * (C.L / 2);
+            const int c = C.first_colour[f] ^ sub;
+            int accepted = 0;
+            for (int j = 0; j < slmc::kQueueSlab / kThreads; ++j) {
+                const int st = it.z * slmc::kQueueSlab + j * kThreads + threadIdx.x;
+                if (st < sites)
+                    accepted += site_update<true>(xf, C.Lx, C.Ly, C.L, J, C.dtau, C.a2, C.delta, C.key0, C.key1,
+                                                  sweep, c, st, chain);
+            }
+            if (accepted) atomicAdd(&s_cnt, accepted);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (!(it.y & 0x80) && C.n_acc && s_cnt) atomicAdd(C.n_acc + f, (unsigned long long)s_cnt);
+            __threadfence();
+            atomicAdd(done + C.done0 + f, 1u);
+        }
     }
 }
 
@@ -493,6 +609,21 @@ cudaError_t eff_wolff(slmc_ctx* c, double* x, int nf, int chain0, const double* 
     k_wolff<<<nf, 256, 3 * c->N, s>>>(x, c->p.Lx, c->p.Ly, c->L, J, c->p.dtau, (uint32_t)(c->p.seed & 0xffffffffu),
                                       (uint32_t)(c->p.seed >> 32), (uint32_t)sweep, dctr, nsweeps, c->nwolff, k,
                                       chain0, c->wolff_sites);
+    return cudaGetLastError();
+}
+
+int sweep_queue_grid() {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_queue, kThreads, 3 * 1024) != cudaSuccess)
+        return 0;
+    return sms * (per_sm < 1 ? 1 : per_sm);
+}
+
+cudaError_t sweep_queue(const QueueClass* classes, int ncls, const int4* items, int nitems, unsigned int* done,
+                        unsigned int* ctl, int max_N, uint32_t u, long long wait_cycles, int grid, cudaStream_t s) {
+    k_sweep_queue<<<grid, kThreads, 3 * max_N, s>>>(classes, ncls, items, nitems, done, ctl, u, wait_cycles);
     return cudaGetLastError();
 }
 

@@ -256,4 +256,34 @@ cudaError_t fit_merge(slmc_ctx* c, const double* states, int nparts, cudaStream_
 cudaError_t fit_finish(slmc_ctx* c, int nconf, double* J_out, double* resid, cudaStream_t s);
 int validate_params(const slmc_params* p);
 int logdet_fields(slmc_ctx* c, const double* x, int nf, double* lndet, int* sign, cudaStream_t s);
+
+// Phases of one cumulative update (slmc_cumulative_update runs all three, update by update).
+constexpr int kPhasePre = 1, kPhaseSweeps = 2, kPhasePost = 4, kPhaseAll = 7;
+int cumulative_phases(slmc_ctx* c, double* x, int n, const double* J, int nsweeps, int u0, int u1, int phases,
+                      double* lnw, double* s_cdw, long long* n_acc, long long* n_sweep_acc, double* obs,
+                      cudaStream_t s);
+const int* first_colours(slmc_ctx* c);
+
+// Persistent E_eff sweep queue over the chains of several lattice classes. One lattice class:
+struct QueueClass {
+    double* x;                           // chains [nchains][N][L]
+    const double* J;                     // couplings of E_eff (6)
+    const int* first_colour;             // per chain: colour of the first half-sweep of this update
+    unsigned long long* n_acc;           // per chain accepted site moves, or null
+    unsigned long long* wolff_sites;     // class total of flipped sites, or null
+    const unsigned long long* dctr;      // device update counter of the class
+    unsigned int* err;                   // error word of the class's context
+    int Lx, Ly, L, nsweeps, nwolff;
+    int done0;                           // index of chain 0's completion counter
+    double dtau, a2, delta;
+    uint32_t key0, key1;
+};
+// An item of the queue (int4): x = class << 24 | chain, y = sweep << 8 | kind << 7 | (colour step
+// h or Wolff index k), z = slab of kQueueSlab sites of the half-sweep, w = number of the chain's
+// earlier items of this update that must be complete before it starts.
+constexpr int kQueueSlab = 1024;
+constexpr int kQueueWolff = 1;
+int sweep_queue_grid();  // CTAs of the persistent launch on the current device
+cudaError_t sweep_queue(const QueueClass* classes, int ncls, const int4* items, int nitems, unsigned int* done,
+                        unsigned int* ctl, int max_N, uint32_t u, long long wait_cycles, int grid, cudaStream_t s);
 }  // namespace slmc

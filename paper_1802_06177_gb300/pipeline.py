@@ -66,7 +66,12 @@ def binned_error(series, nbins=10):
 def initial_fields(init, chains, Lx, L, alpha, seed):
     """Starting fields: iid N(0, 1) ("gaussian"), or the checkerboard CDW state at the minima
     of the double well, alpha (-1)^(ix+iy) + N(0, 0.3^2) ("cdw": the ordered state the model
-    develops below T_c, so that chains near the transition need not order first)."""
+    develops below T_c, so that chains near the transition need not order first), or a given
+    tensor [chains, N, L] (a warm start from another run's final fields, copied)."""
+    if torch.is_tensor(init):
+        if tuple(init.shape) != (chains, Lx * Lx, L):
+            raise ValueError("initial fields of shape %s, expected %s" % (tuple(init.shape), (chains, Lx * Lx, L)))
+        return init.detach().to(torch.float64).cpu().clone()
     if init == "cdw":
         return torch.from_numpy(inputs.cdw_fields(chains, Lx, Lx, L, amp=alpha, noise=0.3, seed=seed))
     return torch.from_numpy(inputs.gaussian_fields(chains, Lx, Lx, L, sigma=1.0, seed=seed))
@@ -139,10 +144,12 @@ def run_dqmc(Lx, L, n_s=8, chains=32, sweeps=500, precision="fp64", dtau=0.1, la
 
 def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision="fp32", dtau=0.1, lam=1.0,
         omega0=1.0, sweep_delta=0.3, seed=0x1802061774, rounds=2, device="cuda", rank=0, world=1, wolff=0,
-        train_source="self", dqmc_therm=50, dqmc_gap=5, init="gaussian", J0=None, want_series=False):
+        train_source="self", dqmc_therm=50, dqmc_gap=5, init="gaussian", J0=None, want_series=False,
+        return_fields=False):
     """One SLMC run: self-learning (or DQMC) training of E_eff, then `updates` cumulative updates
     of every chain measuring S(pi, pi) after each (want_series: also the per-update, per-chain
-    S(pi, pi), the acceptance counts and the couplings of every training round)."""
+    S(pi, pi), the acceptance counts and the couplings of every training round; return_fields:
+    also the chains' final fields as a device tensor under "x_final", e.g. to warm-start DQMC)."""
     dev = torch.device(device)
     seed = seed + rank
     ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
@@ -233,6 +240,8 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
     if want_series:
         res["S_series"] = obs.cpu().numpy().tolist()
         res["accepted"] = n_acc.cpu().numpy().tolist()
+    if return_fields:
+        res["x_final"] = x.clone()
     ctx.close()
     return res
 

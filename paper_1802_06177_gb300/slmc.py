@@ -37,6 +37,7 @@ EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", 
            "slmc_profile_read", "slmc_logdet_noalloc", "slmc_logdet_noalloc_scratch_bytes", "slmc_set_update_counter",
            "slmc_get_update_counter", "slmc_set_tuning", "slmc_batch_create", "slmc_batch_destroy",
            "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune",
+           "slmc_batch_set_sweep_queue", "slmc_batch_inject_stall",
            "slmc_fit_eff_state", "slmc_fit_eff_merge", "slmc_profile_read_detail",
            "slmc_set_sub_batches", "slmc_set_slice_groups",
            "slmc_set_sub_batch_priorities", "slmc_set_qr_cluster", "slmc_set_wolff", "slmc_get_wolff_sites",
@@ -95,6 +96,8 @@ def load_library(path=LIB_PATH):
         "slmc_batch_bind": ([P, I, P, P, P, P, P, P], I),
         "slmc_batch_capture": ([P, I, I, V], I),
         "slmc_batch_launch": ([P, I, V], I),
+        "slmc_batch_set_sweep_queue": ([P, I], I),
+        "slmc_batch_inject_stall": ([P, ctypes.c_longlong], I),
         "slmc_autotune": ([ctypes.POINTER(Params), I, D, ctypes.POINTER(TuneResult)], I),
         "slmc_fit_eff_state": ([P, P, P, I, P, V], I),
         "slmc_fit_eff_merge": ([P, P, I, P, P, V], I),
@@ -428,6 +431,20 @@ class Batch:
         st = self.lib.slmc_batch_launch(self._b, nrounds, self.stream.cuda_stream)
         if st != 0:
             raise SlmcError("slmc_batch_launch", st)
+
+    def set_sweep_queue(self, on):
+        """slmc_batch_set_sweep_queue: the E_eff sweeps of every class in one persistent launch
+        (on, the default) or as each class's kernel-per-half-sweep sequence; next capture."""
+        st = self.lib.slmc_batch_set_sweep_queue(self._b, 1 if on else 0)
+        if st != 0:
+            raise SlmcError("slmc_batch_set_sweep_queue", st)
+
+    def inject_stall(self, wait_cycles):
+        """slmc_batch_inject_stall: test hook; the next capture's first queue item waits for a
+        count nothing reaches and gives up after wait_cycles, setting SLMC_ERR_TIMEOUT."""
+        st = self.lib.slmc_batch_inject_stall(self._b, int(wait_cycles))
+        if st != 0:
+            raise SlmcError("slmc_batch_inject_stall", st)
 
     def close(self):
         if self._b:

@@ -18,7 +18,14 @@ def chains(cl, seed):
     return cuda(inputs.gaussian_fields(cl["nchains"], cl["Lx"], cl["Lx"], cl["L"], sigma=0.5, seed=seed))
 
 
-def test_graph_rounds_equal_direct_calls():
+WOLFF = [1, 0, 2]  # Wolff updates per sweep of each class (uneven: queue phases a class skips)
+
+
+@pytest.mark.parametrize("queue,wolff", [(True, False), (True, True), (False, True)])
+def test_graph_rounds_equal_direct_calls(queue, wolff):
+    """Rounds of the captured graph -- with the E_eff sweeps of all classes in the persistent
+    queue launch, or as per-class kernel sequences -- reproduce successive direct calls bit for bit
+    (fields, ln w, S, acceptance counts of the cumulative and of the sweep moves, Wolff sites)."""
     require_gpu()
     from paper_1802_06177_gb300.slmc import UPDATE_CONTINUE, Batch
     rounds = 4
@@ -27,39 +34,122 @@ def test_graph_rounds_equal_direct_calls():
     direct = []
     for q, cl in enumerate(CLASSES):
         ctx = make_ctx(cl["Lx"], cl["L"], cl["n_s"], max_fields=cl["nchains"], seed=SEED, sweep_delta=DELTA)
+        if wolff:
+            ctx.set_wolff(WOLFF[q])
         x = chains(cl, 10 + q)
         lnw, s = ctx.chain_init(x)
         n_acc = torch.zeros(cl["nchains"], dtype=torch.int64, device="cuda")
+        n_sw = torch.zeros(cl["nchains"], dtype=torch.int64, device="cuda")
         ctx.set_update_counter(0)
         for r in range(rounds):
-            ctx.cumulative_update(x, Jt, NSW, 1, UPDATE_CONTINUE, lnw, s, n_acc)
+            ctx.cumulative_update(x, Jt, NSW, 1, UPDATE_CONTINUE, lnw, s, n_acc, n_sw)
         torch.cuda.synchronize()
         direct.append((x.cpu().numpy(), lnw.cpu().numpy(), s.cpu().numpy(), n_acc.cpu().numpy(),
-                       ctx.get_update_counter()))
+                       n_sw.cpu().numpy(), ctx.get_update_counter(), ctx.wolff_sites()))
     # the same through one graph
     b = Batch([dict(cl, seed=SEED, sweep_delta=DELTA, precision="fp64") for cl in CLASSES])
+    b.set_sweep_queue(queue)
     state = []
     for q, cl in enumerate(CLASSES):
         ctx = b.context(q)
+        if wolff:
+            ctx.set_wolff(WOLFF[q])
         x = chains(cl, 10 + q)
         with torch.cuda.stream(b.stream):
             lnw, s = ctx.chain_init(x)
             ctx.set_update_counter(0)
         n_acc = torch.zeros(cl["nchains"], dtype=torch.int64, device="cuda")
-        b.bind(q, x, Jt, lnw, s, n_acc)
-        state.append((x, lnw, s, n_acc, ctx))
+        n_sw = torch.zeros(cl["nchains"], dtype=torch.int64, device="cuda")
+        b.bind(q, x, Jt, lnw, s, n_acc, n_sw)
+        state.append((x, lnw, s, n_acc, n_sw, ctx))
     torch.cuda.synchronize()
     b.capture(NSW, 1)
     b.launch(rounds)
     b.stream.synchronize()
-    for q, (x, lnw, s, n_acc, ctx) in enumerate(state):
-        dx, dl, ds, dn, dc = direct[q]
+    for q, (x, lnw, s, n_acc, n_sw, ctx) in enumerate(state):
+        dx, dl, ds, dn, dsw, dc, dw = direct[q]
         assert np.array_equal(x.cpu().numpy(), dx)
         assert np.array_equal(lnw.cpu().numpy(), dl)
         assert np.array_equal(s.cpu().numpy(), ds)
         assert np.array_equal(n_acc.cpu().numpy(), dn)
+        assert np.array_equal(n_sw.cpu().numpy(), dsw) and dsw.min() > 0
         with torch.cuda.stream(b.stream):
+            ctx.get_error()
             assert ctx.get_update_counter() == dc == rounds
+            assert ctx.wolff_sites() == dw
+            assert (dw > 0) == (wolff and WOLFF[q] > 0)
+    b.close()
+
+
+def test_queue_rounds_with_several_updates_per_round():
+    """nupdates > 1 per captured round: the queue launch of update u of the round continues the
+    sweep counter as the u-th of successive direct updates."""
+    require_gpu()
+    from paper_1802_06177_gb300.slmc import UPDATE_CONTINUE, Batch
+    Jt = torch.tensor(J, dtype=torch.float64, device="cuda")
+    cls = CLASSES[:2]
+    ref = []
+    for q, cl in enumerate(cls):
+        ctx = make_ctx(cl["Lx"], cl["L"], cl["n_s"], max_fields=cl["nchains"], seed=SEED, sweep_delta=DELTA)
+        x = chains(cl, 40 + q)
+        lnw, s = ctx.chain_init(x)
+        ctx.set_update_counter(0)
+        ctx.cumulative_update(x, Jt, NSW, 6, UPDATE_CONTINUE, lnw, s)
+        torch.cuda.synchronize()
+        ref.append((x.cpu().numpy(), lnw.cpu().numpy()))
+    b = Batch([dict(cl, seed=SEED, sweep_delta=DELTA, precision="fp64") for cl in cls])
+    state = []
+    for q, cl in enumerate(cls):
+        ctx = b.context(q)
+        x = chains(cl, 40 + q)
+        with torch.cuda.stream(b.stream):
+            lnw, s = ctx.chain_init(x)
+            ctx.set_update_counter(0)
+        b.bind(q, x, Jt, lnw, s)
+        state.append((x, lnw))
+    torch.cuda.synchronize()
+    b.capture(NSW, 3)
+    b.launch(2)
+    b.stream.synchronize()
+    for (x, lnw), (rx, rl) in zip(state, ref):
+        assert np.array_equal(x.cpu().numpy(), rx)
+        assert np.array_equal(lnw.cpu().numpy(), rl)
+    b.close()
+
+
+def test_queue_wait_runs_out_and_reports_timeout():
+    """A queue item made to wait for a completion count that nothing reaches gives up after the
+    injected limit (about 1 ms), flags SLMC_ERR_TIMEOUT in every class's context and stops the
+    queue; the device stays usable and a re-captured normal round runs clean."""
+    require_gpu()
+    from paper_1802_06177_gb300.slmc import Batch, SlmcError
+    Jt = torch.tensor(J, dtype=torch.float64, device="cuda")
+    b = Batch([dict(cl, seed=SEED, sweep_delta=DELTA, precision="fp64") for cl in CLASSES])
+    state = []
+    for q, cl in enumerate(CLASSES):
+        ctx = b.context(q)
+        x = chains(cl, 20 + q)
+        with torch.cuda.stream(b.stream):
+            lnw, s = ctx.chain_init(x)
+        b.bind(q, x, Jt, lnw, s)
+        state.append(ctx)
+    torch.cuda.synchronize()
+    b.inject_stall(2_000_000)
+    b.capture(NSW, 1)
+    b.launch(1)
+    b.stream.synchronize()
+    for ctx in state:
+        with torch.cuda.stream(b.stream):
+            with pytest.raises(SlmcError) as e:
+                ctx.get_error()
+        assert e.value.status == 4  # SLMC_ERR_TIMEOUT
+    b.inject_stall(0)
+    b.capture(NSW, 1)
+    b.launch(2)
+    b.stream.synchronize()
+    for ctx in state:
+        with torch.cuda.stream(b.stream):
+            ctx.get_error()
     b.close()
 
 
