@@ -293,6 +293,24 @@ SLMC_API int slmc_set_dense_slices(slmc_ctx* ctx, int dense);
  * The DQMC updates always use path 1. Errors: SLMC_ERR_ARG for other values. */
 SLMC_API int slmc_set_tupdate_path(slmc_ctx* ctx, int path);
 
+/* How the pre-pivoted blocked QR (qr_mode SLMC_QR_PREPIVOT) applies each panel's block of BP
+ * Householder reflectors to the trailing columns, C <- C - V S^T V^T C (compact WY form), in every
+ * precision mode:
+ *   path = 0 (default where available, N <= 896): the panels are factored in FP64 as before and
+ *            the two products of each trailing update, W = V^T C and C - V W' (W' = S^T W), run on
+ *            the tensor cores, FP64-accurate: C, V and W' are cut into seven 7-bit fixed-point
+ *            BF16 slices (a power of two per column of C, per reflector, per row of V, per column
+ *            of W'), the slice products with a + b <= 6 are summed per level in FP32 accumulators
+ *            that hold every partial sum exactly by construction (at most 448 rows per
+ *            accumulator), and each entry is rounded once to FP64. Each product entry then differs
+ *            from the exact product of the operands by below 2^-44 K max|a_row| max|b_column| (K
+ *            the inner dimension): normwise the size of the FP64 loop's own rounding. 4 launches
+ *            per panel on the caller's stream.
+ *   path = 1: the one-kernel FP64 QR (trailing updates with FP64 FMAs).
+ * The DQMC updates and qr_mode SLMC_QR_PIVOTED are unaffected. Errors: SLMC_ERR_ARG for other
+ * values, SLMC_ERR_UNSUPPORTED for path 0 when N > 896. */
+SLMC_API int slmc_set_qr_path(slmc_ctx* ctx, int path);
+
 /* Thread layout of the FP32 slice kernel: 1: one column group of 256 row threads; 2: two such
  * groups (512 threads); 4 (N <= 256): four column groups of 64 row threads, each thread up to
  * 4 rows x 8 columns. 0 (default) selects 4 for N <= 256 and 1 above. The 256-thread layouts (about 104 KB of shared memory

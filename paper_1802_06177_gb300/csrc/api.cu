@@ -145,7 +145,10 @@ int logdet_run(slmc_ctx* c, slmc_ctx* v, const double* x, int nf, double* lndet,
             if (v->p.precision != SLMC_PREC_FP64 && l0 + nsl < v->L)
                 SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::u_to_f32(v, nf, s));
         } else {
-            SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_blocked(v, nf, s));
+            if (slmc::qrt_active(v))
+                SLMC_LAUNCH(SLMC_PROF_QR, slmc::qr_launches(v), s, slmc::qr_tensor(v, nf, s));
+            else
+                SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_blocked(v, nf, s));
             // Q enters the next reduced-precision slice group (rounded to FP32 there anyway) except
             // after the last group, where it enters the FP64 final step.
             const bool q32 = v->p.precision != SLMC_PREC_FP64 && l0 + nsl < v->L;
@@ -192,6 +195,27 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
     v.tt_path = c->tt_path;
     v.tt_mapA = c->tt_mapA;
     v.tt_mapB = c->tt_mapB;
+    v.qt_buf = c->qt_buf;
+    v.qt_ibuf = c->qt_ibuf;
+    v.qt_C = c->qt_C;
+    v.qt_V1 = c->qt_V1;
+    v.qt_V2 = c->qt_V2;
+    v.qt_W = c->qt_W;
+    v.qt_eC = c->qt_eC;
+    v.qt_eV1 = c->qt_eV1;
+    v.qt_eV2 = c->qt_eV2;
+    v.qt_eW = c->qt_eW;
+    v.qt_ntriv = c->qt_ntriv;
+    v.qt_lnDn = c->qt_lnDn;
+    v.qt_kpad = c->qt_kpad;
+    v.qt_mpad = c->qt_mpad;
+    v.qt_wpad = c->qt_wpad;
+    v.qr_path = c->qr_path;
+    v.qt_mapC = c->qt_mapC;
+    v.qt_mapV1_16 = c->qt_mapV1_16;
+    v.qt_mapV1_32 = c->qt_mapV1_32;
+    v.qt_mapV2 = c->qt_mapV2;
+    v.qt_mapW = c->qt_mapW;
     v.fbase = c->fbase + f0;
     v.sc32 = c->sc32 ? c->sc32 + F0 * c->L * N : nullptr;
     v.Y = c->Y + F0 * NN;
@@ -258,7 +282,7 @@ void free_ctx(slmc_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_rec) cudaEventDestroy(e);
     if (c->prof_base) cudaEventDestroy(c->prof_base);
-    void* bufs[] = {c->E64, c->Einv64, c->kron, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->tcx_F, c->tcx_eF, c->tt_A, c->tt_B, c->tt_eA, c->tt_eB, c->tt_flag, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
+    void* bufs[] = {c->E64, c->Einv64, c->kron, c->F32, c->lo_kidx, c->lo_val, c->sc32, c->tcx_F, c->tcx_eF, c->tt_A, c->tt_B, c->tt_eA, c->tt_eB, c->tt_flag, c->qt_buf, c->qt_ibuf, c->qt_lnDn, c->Y, c->QR, c->U, c->U32, c->Ta, c->Tb, c->lnD, c->tau,
                     c->perm, c->piv, c->sgnU, c->Sws, c->x_old, c->scal, c->iscal, c->feat, c->fitR, c->err, c->dctr,
                     c->wolff_sites, c->dq_stack,
                     c->tc_F, c->tc_p[0], c->tc_p[1], c->tc_y32[0], c->tc_y32[1]};
@@ -413,6 +437,13 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
         alloc(&c->tt_eB, F * npad * sizeof(int));
         alloc(&c->tt_flag, F * (mpad / 128) * sizeof(int));
     }
+    if (slmc::qrt_supported((int)N)) {  // QR with tensor-core trailing updates
+        size_t nb16 = 0, nint = 0;
+        slmc::qrt_sizes((int)N, (int)F, &nb16, &nint);
+        alloc(&c->qt_buf, nb16 * 2);
+        alloc(reinterpret_cast<void**>(&c->qt_ibuf), nint * sizeof(int));
+        alloc(reinterpret_cast<void**>(&c->qt_lnDn), F * N * sizeof(double));
+    }
     alloc(&c->Y, F * NN * sizeof(double));
     alloc(&c->QR, F * NN * sizeof(double));
     alloc(&c->U, F * NN * sizeof(double));
@@ -476,7 +507,7 @@ int slmc_init(const slmc_params* p, int max_fields, slmc_ctx** out) {
     }
     if (cudaMemset(c->err, 0, sizeof(unsigned int)) != cudaSuccess ||
         slmc::build_hopping_exp(c, nullptr) != cudaSuccess || (tc && slmc::tc_init(c, nullptr) != cudaSuccess) ||
-        slmc::tt_init(c) != cudaSuccess ||
+        slmc::tt_init(c) != cudaSuccess || (c->qt_buf && slmc::qrt_init(c, c->qt_buf, c->qt_ibuf) != cudaSuccess) ||
         cudaDeviceSynchronize() != cudaSuccess) {
         free_ctx(c);
         return SLMC_ERR_CUDA;
@@ -764,6 +795,13 @@ int slmc_set_tupdate_path(slmc_ctx* c, int path) {
     if (!c || path < 0 || path > 2) return SLMC_ERR_ARG;
     if (path != 1 && !c->tt_A) return SLMC_ERR_UNSUPPORTED;
     c->tt_path = path;
+    return SLMC_OK;
+}
+
+int slmc_set_qr_path(slmc_ctx* c, int path) {
+    if (!c || path < 0 || path > 1) return SLMC_ERR_ARG;
+    if (path == 0 && !c->qt_buf) return SLMC_ERR_UNSUPPORTED;
+    c->qr_path = path;
     return SLMC_OK;
 }
 

@@ -1,0 +1,625 @@
+// Blocked Householder QR of the UDT stabilisation with its trailing updates on the tensor cores,
+// FP64-accurate.
+//
+// The pre-pivoted blocked QR (see k_qrb.cu) spends about half of its FP64 issue slots on the
+// trailing updates C <- (I - V S^T V^T) C = C - V W', W' = S^T W, W = V^T C, after each panel of BP
+// reflectors. Here the panels are factored as before (FP64, one CTA per field, k_qrt_panel), and the
+// two products of each trailing update run on the tensor cores in exact fixed-point BF16 slices
+// (the same Ozaki-style splitting as the T update): every operand row or column is cut into seven
+// 7-bit digits (slice7.cuh) against its own power of two, the products of digit slices a, b with
+// a + b <= 6 are summed per level a + b in FP32 accumulators in tensor memory -- exactly, because a
+// level's sum of absolute terms stays below 2^24 by construction (at most 36864 per K index, and
+// the K range of one accumulator is at most 448) -- and the epilogue combines the levels in two
+// 64-bit integers and rounds once to FP64. Each product entry is then the correctly rounded value
+// of the sliced operands' product; the slicing (rounding at 2^-48 of each row's / column's largest
+// entry) and the dropped levels 7..12 leave an error below 2^-44 K max_k|a_ik| max_k|b_kj| per
+// entry: normwise the size of the FP64 loop's own rounding, which is what the backward stability of
+// the Householder update needs (errors relative to each column of C, each reflector, each row of
+// W').
+//
+// Per panel t (p = t BP), on the caller's stream:
+//   k_qrt_panel<BP>  factor the panel (shared panel_step); write its outputs; slice V twice: per
+//                    reflector over the rows (B operand of W^T = C^T V) and per row over the
+//                    reflectors (A operand of V W');
+//   k_qrt_slice_C    slice the trailing columns of C (rows p..N-1), one exponent per column;
+//   k_qrt_gemm1<BP>  W^T = C^T V on the tensor cores (M = trailing columns, N = BP, K = rows), then
+//                    W'^T = W^T S and its slices, one exponent per trailing column;
+//   k_qrt_gemm2<BP>  C -= V W' on the tensor cores (M = rows, N = trailing columns, K = BP), the
+//                    FP64 read-modify-write of C in the epilogue.
+// Outputs are those of k_qrb (packed QR, tau, perm, new ln D, sgnU, the panels' S). All waits are
+// clock-bounded and set SLMC_EBIT_TIMEOUT; a CTA that gives up drains its copies and frees its
+// tensor memory.
+#include <algorithm>
+
+#include "qr_panel.cuh"
+#include "slice7.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+using namespace slmc::tc;
+using slmc::s7::abs_bits;
+using slmc::s7::exponent_of_bits;
+using slmc::s7::kS;
+using slmc::s7::pow2d;
+using slmc::s7::slice7;
+using slmc::s7::warp_max_bits;
+
+constexpr int kLv = 7;                       // levels a + b = 0..6
+constexpr int kQT = 320;                     // GEMM threads: 8 epilogue warps, TMA warp, MMA warp
+constexpr uint32_t kTileA = 128 * 128;       // 128 rows x 64 BF16 (one 128-byte swizzle row each)
+constexpr int kSegChunks = 7;                // K chunks (64 rows) per accumulator set of W^T = C^T V
+constexpr int kMaxN = 2 * kSegChunks * 64;   // 896: two accumulator sets
+constexpr int kVRows = 32;                   // rows of the V1 slice buffer per field (BP <= 32)
+// 2^-54: the digits' units 2^(e - 6) per operand and the level weights 2^(-7 level), 2^-42 at level 6
+constexpr int kUnitShift = 2 * 6 + 7 * (kLv - 1);
+
+// Level sums (FP32 integers) of one accumulator entry -> hi 2^28 + lo as 64-bit integers.
+__device__ __forceinline__ void levels_to_int(const uint32_t (&v)[kLv], long long& hi, long long& lo) {
+    hi = (long long)__float2int_rn(__uint_as_float(v[0]));
+#pragma unroll
+    for (int lv = 1; lv < 3; ++lv) hi = hi * 128 + (long long)__float2int_rn(__uint_as_float(v[lv]));
+    lo = (long long)__float2int_rn(__uint_as_float(v[3]));
+#pragma unroll
+    for (int lv = 4; lv < kLv; ++lv) lo = lo * 128 + (long long)__float2int_rn(__uint_as_float(v[lv]));
+}
+
+// ---- panel ----------------------------------------------------------------------------------
+template <int BP>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_qrt_panel(double* __restrict__ Yall, double* __restrict__ lnD_all, double* __restrict__ QRall,
+                double* __restrict__ tau_all, int* __restrict__ perm_all, int* __restrict__ sgnU,
+                double* __restrict__ Sall, unsigned int* __restrict__ err, int N, int t, double* __restrict__ lnDn_ws,
+                int* __restrict__ ntriv_ws, __nv_bfloat16* __restrict__ V1, int* __restrict__ eV1,
+                __nv_bfloat16* __restrict__ V2, int* __restrict__ eV2, int kpad, int mpad, size_t plane1,
+                size_t plane2, int fbase) {
+    constexpr int BPS = BP + 1;
+    const int f = blockIdx.x, gf = fbase + f;
+    const size_t NN = (size_t)N * N;
+    double* __restrict__ Y = Yall + f * NN;
+    double* __restrict__ QR = QRall + f * NN;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* Vp = reinterpret_cast<double*>(smraw);
+    double* Ssm = Vp + (size_t)N * BPS;
+    double* Wsm = Ssm + BP * BP;
+    double* s_key = Wsm + kWarps * BP * kCT;
+    double* s_lnd = s_key + N;
+    double* s_lnDn = s_lnd + N;
+    double* s_g = s_lnDn + N;
+    double* s_tau = s_g + N;
+    double* s_beta = s_tau + BP;
+    int* s_perm = reinterpret_cast<int*>(s_beta + BP);
+    __shared__ double s_mx;
+    __shared__ int s_ntriv, s_wide;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int p = t * BP, nb = min(BP, N - p), npanels = (N + BP - 1) / BP;
+
+    for (int j = tid; j < N; j += kThreads) s_lnd[j] = lnD_all[(size_t)f * N + j];
+    if (tid == 0) {
+        s_ntriv = 0;
+        s_wide = 0;
+    }
+    __syncthreads();
+    if (t == 0) {  // scaled column norms and the pre-pivoting order, as in k_qrb
+        if (warp == 0) {
+            double mx = -DBL_MAX;
+            for (int j = lane; j < N; j += 32) mx = fmax(mx, s_lnd[j]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) s_mx = mx;
+        }
+        __syncthreads();
+        for (int j = warp; j < N; j += kWarps) {
+            double a = 0.0;
+            for (int i = lane; i < N; i += 32) {
+                const double y = Y[(size_t)j * N + i];
+                a = fma(y, y, a);
+            }
+            a = slmc::warp_allsum(a);
+            if (lane == 0) {
+                const double key = a * exp(2.0 * (s_lnd[j] - s_mx));
+                s_key[j] = (key >= 0.0) ? key : -1.0;
+            }
+        }
+        __syncthreads();
+        for (int j = tid; j < N; j += kThreads) {
+            const double kj = s_key[j];
+            int r = 0;
+            for (int i = 0; i < N; ++i) {
+                const double ki = s_key[i];
+                r += (ki > kj) || (ki == kj && i < j);
+            }
+            s_perm[r] = j;
+        }
+        __syncthreads();
+        for (int j = tid; j < N; j += kThreads) perm_all[(size_t)f * N + j] = s_perm[j];
+    } else {
+        for (int j = tid; j < N; j += kThreads) s_perm[j] = perm_all[(size_t)f * N + j];
+        for (int i = tid; i < p; i += kThreads) {
+            const double l = lnDn_ws[(size_t)gf * N + i];
+            s_lnDn[i] = l;
+            s_g[i] = exp(-l);
+            if (fabs(l) > 600.0) s_wide = 1;
+        }
+    }
+    for (int k = tid; k < N; k += kThreads)
+        if (fabs(s_lnd[k]) > 600.0) s_wide = 1;
+    __syncthreads();
+
+    panel_step<BP>(Y, QR, tau_all + (size_t)f * N, Sall + (size_t)f * N * BP, Vp, Ssm, Wsm, s_lnd, s_lnDn, s_g, s_tau,
+                   s_beta, s_perm, &s_ntriv, &s_wide, N, p, nb);
+    __syncthreads();
+    if (tid < nb) lnDn_ws[(size_t)gf * N + p + tid] = s_lnDn[p + tid];
+    const int ntriv = (t == 0 ? 0 : ntriv_ws[gf]) + s_ntriv;
+    if (t == npanels - 1) {  // every scale is known: publish ln D', the sign of det U
+        bool bad = false;
+        for (int k = tid; k < N; k += kThreads) {
+            lnD_all[(size_t)f * N + k] = s_lnDn[k];
+            bad |= !isfinite(s_lnDn[k]);
+        }
+        if (tid == 0) sgnU[f] = (ntriv & 1) ? -1 : 1;
+        if (bad) atomicOr(err, SLMC_EBIT_NONFINITE);
+        return;
+    }
+    if (tid == 0) ntriv_ws[gf] = ntriv;
+    // V1: reflector m over rows p..N-1 (K-major, K chunks from the one holding row p)
+    const int kstart = (p / 64) * 64;
+    for (int m = warp; m < BP; m += kWarps) {
+        long long mx = 0;
+        for (int r = p + lane; r < N; r += 32) mx = max(mx, abs_bits(Vp[r * BPS + m]));
+        const int e = exponent_of_bits(warp_max_bits(mx));
+        if (lane == 0) eV1[(size_t)gf * kVRows + m] = e;
+        __nv_bfloat16* dst = V1 + ((size_t)gf * kVRows + m) * kpad;
+        for (int k = kstart + lane; k < kpad; k += 32) {
+            __nv_bfloat16 q[kS];
+            slice7((k >= p && k < N) ? Vp[k * BPS + m] : 0.0, e, q);
+#pragma unroll
+            for (int s = 0; s < kS; ++s) dst[(size_t)s * plane1 + k] = q[s];
+        }
+    }
+    // V2: row r over the reflectors (K = the BP reflectors, padded to 64 with zeros set at init),
+    // rows of the first row tile that holds row p onward
+    for (int r = (p / 128) * 128 + warp; r < mpad; r += kWarps) {
+        const double v = (r >= p && r < N && lane < BP) ? Vp[r * BPS + lane] : 0.0;
+        const int e = exponent_of_bits(warp_max_bits(abs_bits(v)));
+        if (lane == 0) eV2[(size_t)gf * mpad + r] = e;
+        if (lane < BP) {
+            __nv_bfloat16 q[kS];
+            slice7(v, e, q);
+#pragma unroll
+            for (int s = 0; s < kS; ++s) V2[(size_t)s * plane2 + ((size_t)gf * mpad + r) * 64 + lane] = q[s];
+        }
+    }
+}
+
+// ---- slices of the trailing columns ---------------------------------------------------------
+// Warp w of block x slices trailing column jj = 8 x + w (logical column j0 + jj) over rows p..N-1.
+__global__ void __launch_bounds__(256) k_qrt_slice_C(const double* __restrict__ Yall, const int* __restrict__ perm_all,
+                                                     __nv_bfloat16* __restrict__ Cs, int* __restrict__ eC, int N,
+                                                     int p, int j0, int kpad, int jpad, size_t plane, int fbase) {
+    const int f = blockIdx.y, gf = fbase + f, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int jj = blockIdx.x * 8 + warp, j = j0 + jj;
+    if (j >= N) return;
+    const double* col = Yall + (size_t)f * N * N + (size_t)perm_all[(size_t)f * N + j] * N;
+    long long mx = 0;
+    for (int r = p + lane; r < N; r += 32) mx = max(mx, abs_bits(col[r]));
+    const int e = exponent_of_bits(warp_max_bits(mx));
+    if (lane == 0) eC[(size_t)gf * jpad + jj] = e;
+    __nv_bfloat16* dst = Cs + ((size_t)gf * jpad + jj) * kpad;
+    for (int k = (p / 64) * 64 + lane; k < kpad; k += 32) {
+        __nv_bfloat16 q[kS];
+        slice7((k >= p && k < N) ? col[k] : 0.0, e, q);
+#pragma unroll
+        for (int s = 0; s < kS; ++s) dst[(size_t)s * plane + k] = q[s];
+    }
+}
+
+// ---- W^T = C^T V, then W'^T = W^T S and its slices ------------------------------------------
+// CTA = 128 trailing columns of one field. TMA streams per 64-row K chunk the seven C slices
+// through a 7-tile ring and the seven V slices double-buffered; products (a, b), a + b <= 6, go to
+// the accumulator of level a + b of the chunk's segment (seven chunks per segment).
+template <int BP>
+__global__ void __launch_bounds__(kQT, 1)
+    k_qrt_gemm1(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmV,
+                const int* __restrict__ eC, const int* __restrict__ eV1, const double* __restrict__ Sall,
+                __nv_bfloat16* __restrict__ Ws, int* __restrict__ eW, int N, int p, int n_t, int kpad, int jpad,
+                int wpad, size_t planeW, int fbase, unsigned int* __restrict__ err) {
+    constexpr uint32_t kTileB = BP * 128;
+    constexpr uint32_t kChunkB = kS * kTileB;
+    constexpr uint32_t kIdesc = idesc_f32acc(1, 128, BP);
+    constexpr int WS = BP + 1;
+    const int mt = blockIdx.x, f = blockIdx.y, gf = fbase + f;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kc0 = p / 64, nkc = kpad / 64 - kc0;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar_full[kS], bar_empty[kS], bar_bfull[2], bar_bempty[2], bar_acc, bar_done;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_sh;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t bbuf = base, aring = base + 2 * kChunkB;
+    // after the MMAs: stage of W [128][WS], W' [128][WS] and S [BP][BP] in the ring
+    double* stW = reinterpret_cast<double*>(smem_raw + (aring - raw));
+    double* stWp = stW + 128 * WS;
+    double* Ssh = stWp + 128 * WS;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kS; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&bar_bfull[b]), 1);
+            mbar_init(smem_u32(&bar_bempty[b]), 1);
+        }
+        mbar_init(smem_u32(&bar_acc), 1);
+        mbar_init(smem_u32(&bar_done), 1);
+        abort_sh = 0;
+        fence_barrier_init();
+    }
+    if (warp == 9) {
+        tmem_alloc(smem_u32(&tmem_base_sh), 512);
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 8) {
+        if (lane == 0) {
+            int issued_a = 0, issued_b = 0;
+            for (int u = 0; u < nkc && !abort_sh; ++u) {
+                const int kc = kc0 + u, bs = u & 1;
+                if (u >= 2 && !mbar_wait(smem_u32(&bar_bempty[bs]), ((u >> 1) - 1) & 1, err)) {
+                    abort_sh = 1;
+                    break;
+                }
+                const uint32_t bb = smem_u32(&bar_bfull[bs]);
+                mbar_expect_tx(bb, kChunkB);
+                for (int b = 0; b < kS; ++b) tma_load_3d(bbuf + bs * kChunkB + b * kTileB, &tmV, kc * 64, gf * kVRows, b, bb);
+                issued_b = u + 1;
+                for (int a = 0; a < kS; ++a) {
+                    const int q = u * kS + a;
+                    if (q >= kS && !mbar_wait(smem_u32(&bar_empty[a]), ((q / kS) - 1) & 1, err)) {
+                        abort_sh = 1;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&bar_full[a]);
+                    mbar_expect_tx(fb, kTileA);
+                    tma_load_3d(aring + a * kTileA, &tmC, kc * 64, gf * jpad + mt * 128, a, fb);
+                    issued_a = q + 1;
+                }
+            }
+            for (int q = issued_a - 1; q >= 0 && q >= issued_a - kS; --q)
+                mbar_wait(smem_u32(&bar_full[q % kS]), (q / kS) & 1, err);
+            for (int u = issued_b - 1; u >= 0 && u >= issued_b - 2; --u)
+                mbar_wait(smem_u32(&bar_bfull[u & 1]), (u >> 1) & 1, err);
+        }
+    } else if (warp == 9) {
+        if (lane == 0) {
+            bool ok = true;
+            uint32_t written = 0;
+            for (int u = 0; u < nkc && ok; ++u) {
+                const int bs = u & 1, seg = u / kSegChunks;
+                if (!mbar_wait(smem_u32(&bar_bfull[bs]), (u >> 1) & 1, err) || abort_sh) {
+                    ok = false;
+                    break;
+                }
+                for (int a = 0; a < kS && ok; ++a) {
+                    const int q = u * kS + a;
+                    if (!mbar_wait(smem_u32(&bar_full[a]), (q / kS) & 1, err) || abort_sh) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t ad = smem_desc_sw128(aring + a * kTileA + ks * 32);
+#pragma unroll
+                        for (int b = 0; b < kS; ++b) {
+                            if (a + b >= kLv) continue;
+                            const int acc = seg * kLv + a + b;
+                            const uint64_t bd = smem_desc_sw128(bbuf + bs * kChunkB + b * kTileB + ks * 32);
+                            mma_bf16(tmem + (uint32_t)(acc * BP), ad, bd, kIdesc, (written >> acc) & 1u);
+                            written |= 1u << acc;
+                        }
+                    }
+                    mma_commit(smem_u32(&bar_empty[a]));
+                }
+                if (ok) mma_commit(smem_u32(&bar_bempty[bs]));
+            }
+            if (ok) mma_commit(smem_u32(&bar_acc));
+            else abort_sh = 1;
+            mma_commit(smem_u32(&bar_done));
+            mbar_wait(smem_u32(&bar_done), 0, err);
+        }
+    } else {
+        // ---- epilogue: warp w drains rows 32 (w % 4).. for reflectors (w / 4) BP/2 .. ----
+        constexpr int HC = BP / 2;
+        const int q4 = warp & 3, h = warp >> 2, r = 32 * q4 + lane, jj = mt * 128 + r;
+        const int nseg = (nkc + kSegChunks - 1) / kSegChunks;
+        const bool bad = !mbar_wait(smem_u32(&bar_acc), 0, err) || abort_sh;
+        if (!named_sync_or(1, 256, bad)) {
+            tc_fence_after();
+            const int ec = jj < n_t ? eC[(size_t)gf * jpad + jj] : 0;
+#pragma unroll
+            for (int c0 = 0; c0 < HC; c0 += 8) {
+                long long hi[8], lo[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) hi[c] = lo[c] = 0;
+                for (int sg = 0; sg < nseg; ++sg) {
+                    uint32_t v[kLv][8];
+                    const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(sg * kLv * BP + h * HC + c0);
+#pragma unroll
+                    for (int lv = 0; lv < kLv; ++lv) tmem_ld8(tl + (uint32_t)(lv * BP), v[lv]);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        uint32_t w[kLv];
+#pragma unroll
+                        for (int lv = 0; lv < kLv; ++lv) w[lv] = v[lv][c];
+                        long long a, b;
+                        levels_to_int(w, a, b);
+                        hi[c] += a;
+                        lo[c] += b;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int m = h * HC + c0 + c;
+                    stW[r * WS + m] = fma(__ll2double_rn(hi[c]), 268435456.0, __ll2double_rn(lo[c])) *
+                                      pow2d(ec + eV1[(size_t)gf * kVRows + m] - kUnitShift);
+                }
+            }
+            for (int idx = threadIdx.x; idx < BP * BP; idx += 256) Ssh[idx] = Sall[((size_t)f * N + p) * BP + idx];
+        }
+        named_sync(1, 256);
+        if (!bad) {
+            // W'[m] = sum_{q <= m} S[q][m] W[q]  (S upper triangular); thread (row, half)
+            const int rr = threadIdx.x & 127, hh = threadIdx.x >> 7;
+            for (int m = hh * HC; m < hh * HC + HC; ++m) {
+                double a = 0.0;
+                for (int q = 0; q <= m; ++q) a = fma(Ssh[q * BP + m], stW[rr * WS + q], a);
+                stWp[rr * WS + m] = a;
+            }
+        }
+        named_sync(1, 256);
+        if (!bad && threadIdx.x < 128) {
+            const int rr = threadIdx.x, j2 = mt * 128 + rr;
+            if (j2 < n_t) {
+                long long mx = 0;
+                for (int m = 0; m < BP; ++m) mx = max(mx, abs_bits(stWp[rr * WS + m]));
+                const int e = exponent_of_bits(mx);
+                eW[(size_t)gf * wpad + j2] = e;
+                __nv_bfloat16* dst = Ws + ((size_t)gf * wpad + j2) * 64;
+                for (int m = 0; m < BP; ++m) {
+                    __nv_bfloat16 q[kS];
+                    slice7(stWp[rr * WS + m], e, q);
+#pragma unroll
+                    for (int s = 0; s < kS; ++s) dst[(size_t)s * planeW + m] = q[s];
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 9) tmem_dealloc(tmem, 512);
+}
+
+// ---- C -= V W' -----------------------------------------------------------------------------
+// CTA = 128 rows (row tile p/128 + blockIdx.y) x 64 trailing columns of one field; one K chunk
+// (BP reflectors) of seven V slices and seven W' slices.
+template <int BP>
+__global__ void __launch_bounds__(kQT, 1)
+    k_qrt_gemm2(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmW,
+                const int* __restrict__ eV2, const int* __restrict__ eW, const int* __restrict__ perm_all,
+                double* __restrict__ Yall, int N, int p, int j0, int n_t, int mpad, int wpad, int fbase,
+                unsigned int* __restrict__ err) {
+    constexpr uint32_t kTileW = 64 * 128;
+    constexpr uint32_t kIdesc = idesc_f32acc(1, 128, 64);
+    const int nt = blockIdx.x, mt = p / 128 + blockIdx.y, f = blockIdx.z, gf = fbase + f;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar_full, bar_acc, bar_done;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_sh;
+    __shared__ int eW_sh[64];
+    __shared__ int col_sh[64];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t abuf = base, bbuf = base + kS * kTileA;
+
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar_full), 1);
+        mbar_init(smem_u32(&bar_acc), 1);
+        mbar_init(smem_u32(&bar_done), 1);
+        abort_sh = 0;
+        fence_barrier_init();
+    }
+    if (threadIdx.x < 64) {
+        const int jj = nt * 64 + threadIdx.x;
+        eW_sh[threadIdx.x] = jj < n_t ? eW[(size_t)gf * wpad + jj] : 0;
+        col_sh[threadIdx.x] = jj < n_t ? perm_all[(size_t)f * N + j0 + jj] : 0;
+    }
+    if (warp == 9) {
+        tmem_alloc(smem_u32(&tmem_base_sh), 512);
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 8) {
+        if (lane == 0) {
+            const uint32_t fb = smem_u32(&bar_full);
+            mbar_expect_tx(fb, kS * (kTileA + kTileW));
+            for (int a = 0; a < kS; ++a) tma_load_3d(abuf + a * kTileA, &tmV, 0, gf * mpad + mt * 128, a, fb);
+            for (int b = 0; b < kS; ++b) tma_load_3d(bbuf + b * kTileW, &tmW, 0, gf * wpad + nt * 64, b, fb);
+            mbar_wait(fb, 0, err);  // (bounded) the copies have landed before the CTA can exit
+        }
+    } else if (warp == 9) {
+        if (lane == 0) {
+            if (mbar_wait(smem_u32(&bar_full), 0, err)) {
+                tc_fence_after();
+                uint32_t written = 0;
+#pragma unroll
+                for (int ks = 0; ks < BP / 16; ++ks)
+#pragma unroll
+                    for (int a = 0; a < kS; ++a) {
+                        const uint64_t ad = smem_desc_sw128(abuf + a * kTileA + ks * 32);
+#pragma unroll
+                        for (int b = 0; b < kS; ++b) {
+                            if (a + b >= kLv) continue;
+                            const int lv = a + b;
+                            const uint64_t bd = smem_desc_sw128(bbuf + b * kTileW + ks * 32);
+                            mma_bf16(tmem + (uint32_t)(lv * 64), ad, bd, kIdesc, (written >> lv) & 1u);
+                            written |= 1u << lv;
+                        }
+                    }
+                mma_commit(smem_u32(&bar_acc));
+            } else {
+                abort_sh = 1;
+            }
+            mma_commit(smem_u32(&bar_done));
+            mbar_wait(smem_u32(&bar_done), 0, err);
+        }
+    } else {
+        // ---- epilogue: warp w: rows 32 (w % 4).. of the tile, columns 32 (w / 4)..; C -= V W' ----
+        const int q4 = warp & 3, h = warp >> 2, r = mt * 128 + 32 * q4 + lane;
+        const bool bad = !mbar_wait(smem_u32(&bar_acc), 0, err) || abort_sh;
+        if (!named_sync_or(1, 256, bad)) {
+            tc_fence_after();
+            const bool row_ok = r >= p && r < N;
+            const int ev = row_ok ? eV2[(size_t)gf * mpad + r] : 0;
+            double* Yf = Yall + (size_t)f * N * N;
+#pragma unroll
+            for (int c0 = 0; c0 < 32; c0 += 8) {
+                uint32_t v[kLv][8];
+                const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(32 * h + c0);
+#pragma unroll
+                for (int lv = 0; lv < kLv; ++lv) tmem_ld8(tl + (uint32_t)(lv * 64), v[lv]);
+                tmem_ld_wait();
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int cc = 32 * h + c0 + c, jj = nt * 64 + cc;
+                    if (!row_ok || jj >= n_t) continue;
+                    uint32_t w[kLv];
+#pragma unroll
+                    for (int lv = 0; lv < kLv; ++lv) w[lv] = v[lv][c];
+                    long long hi, lo;
+                    levels_to_int(w, hi, lo);
+                    const double t = fma(__ll2double_rn(hi), 268435456.0, __ll2double_rn(lo)) *
+                                     pow2d(ev + eW_sh[cc] - kUnitShift);
+                    double* y = Yf + (size_t)col_sh[cc] * N + r;
+                    *y = *y - t;
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 9) tmem_dealloc(tmem, 512);
+}
+
+size_t gemm1_smem(int BP) { return 1024 + 2 * (size_t)kS * BP * 128 + (size_t)kS * kTileA; }
+size_t gemm2_smem() { return 1024 + (size_t)kS * (kTileA + 64 * 128); }
+
+template <int BP>
+cudaError_t launch_qrt(slmc_ctx* c, int nf, cudaStream_t s) {
+    const int N = c->N, npanels = (N + BP - 1) / BP, kpad = c->qt_kpad, mpad = c->qt_mpad, wpad = c->qt_wpad;
+    const int jpad = mpad;
+    const size_t F = c->max_fields;
+    const size_t plane1 = F * kVRows * kpad, plane2 = F * mpad * 64, planeC = F * jpad * kpad, planeW = F * wpad * 64;
+    __nv_bfloat16* V1 = reinterpret_cast<__nv_bfloat16*>(c->qt_V1);
+    __nv_bfloat16* V2 = reinterpret_cast<__nv_bfloat16*>(c->qt_V2);
+    __nv_bfloat16* Cs = reinterpret_cast<__nv_bfloat16*>(c->qt_C);
+    __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(c->qt_W);
+    const size_t smP = QrSmem<BP>::bytes(N), sm1 = gemm1_smem(BP), sm2 = gemm2_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_qrt_panel<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smP);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_qrt_gemm1<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_qrt_gemm2<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    if (e != cudaSuccess) return e;
+    const CUtensorMap& mapV1 = BP == 32 ? c->qt_mapV1_32 : c->qt_mapV1_16;
+    for (int t = 0; t < npanels; ++t) {
+        const int p = t * BP;
+        k_qrt_panel<BP><<<nf, kThreads, smP, s>>>(c->Y, c->lnD, c->QR, c->tau, c->perm, c->sgnU, c->Sws, c->err, N, t,
+                                                  c->qt_lnDn, c->qt_ntriv, V1, c->qt_eV1, V2, c->qt_eV2, kpad, mpad,
+                                                  plane1, plane2, c->fbase);
+        if (t + 1 == npanels) break;
+        const int j0 = p + BP, n_t = N - j0;
+        k_qrt_slice_C<<<dim3((n_t + 7) / 8, nf), 256, 0, s>>>(c->Y, c->perm, Cs, c->qt_eC, N, p, j0, kpad, jpad, planeC,
+                                                              c->fbase);
+        k_qrt_gemm1<BP><<<dim3((n_t + 127) / 128, nf), kQT, sm1, s>>>(c->qt_mapC, mapV1, c->qt_eC, c->qt_eV1, c->Sws,
+                                                                      Ws, c->qt_eW, N, p, n_t, kpad, jpad, wpad, planeW,
+                                                                      c->fbase, c->err);
+        k_qrt_gemm2<BP><<<dim3((n_t + 63) / 64, mpad / 128 - p / 128, nf), kQT, sm2, s>>>(
+            c->qt_mapV2, c->qt_mapW, c->qt_eV2, c->qt_eW, c->perm, c->Y, N, p, j0, n_t, mpad, wpad, c->fbase, c->err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace slmc {
+
+bool qrt_supported(int N) { return N >= 2 && N <= kMaxN; }
+
+// Sizes of the slice buffers (BF16 elements) and exponent arrays of a context with F fields.
+void qrt_sizes(int N, int F, size_t* bf16_elems, size_t* int_elems) {
+    const size_t kpad = (N + 63) / 64 * 64, mpad = (N + 127) / 128 * 128, wpad = kpad;
+    *bf16_elems = (size_t)kS * F * (mpad * kpad + kVRows * kpad + mpad * 64 + wpad * 64);
+    *int_elems = (size_t)F * (mpad + kVRows + mpad + wpad + 1);
+}
+
+// Carves the buffers allocated by slmc_init, zeroes them (the padding is never written again) and
+// encodes the TMA descriptors.
+cudaError_t qrt_init(slmc_ctx* c, void* bf16_base, int* int_base) {
+    const int N = c->N;
+    const size_t F = c->max_fields;
+    c->qt_kpad = (N + 63) / 64 * 64;
+    c->qt_mpad = (N + 127) / 128 * 128;
+    c->qt_wpad = c->qt_kpad;
+    const size_t kpad = c->qt_kpad, mpad = c->qt_mpad, wpad = c->qt_wpad;
+    __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(bf16_base);
+    c->qt_C = b;
+    b += (size_t)kS * F * mpad * kpad;
+    c->qt_V1 = b;
+    b += (size_t)kS * F * kVRows * kpad;
+    c->qt_V2 = b;
+    b += (size_t)kS * F * mpad * 64;
+    c->qt_W = b;
+    b += (size_t)kS * F * wpad * 64;
+    c->qt_eC = int_base;
+    c->qt_eV1 = c->qt_eC + F * mpad;
+    c->qt_eV2 = c->qt_eV1 + F * kVRows;
+    c->qt_eW = c->qt_eV2 + F * mpad;
+    c->qt_ntriv = c->qt_eW + F * wpad;
+    size_t nb16 = 0, nint = 0;
+    qrt_sizes(N, (int)F, &nb16, &nint);
+    cudaError_t e = cudaMemset(bf16_base, 0, nb16 * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMemset(int_base, 0, nint * sizeof(int));
+    if (e != cudaSuccess) return e;
+    if (!make_map_sw128(&c->qt_mapC, c->qt_C, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, kpad, F * mpad, kS, 128) ||
+        !make_map_sw128(&c->qt_mapV1_32, c->qt_V1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, kpad, F * kVRows, kS, 32) ||
+        !make_map_sw128(&c->qt_mapV1_16, c->qt_V1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, kpad, F * kVRows, kS, 16) ||
+        !make_map_sw128(&c->qt_mapV2, c->qt_V2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 64, F * mpad, kS, 128) ||
+        !make_map_sw128(&c->qt_mapW, c->qt_W, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 64, F * wpad, kS, 64))
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+bool qrt_active(const slmc_ctx* c) { return c->qt_C && c->qr_path == 0 && qrt_supported(c->N); }
+
+int qr_launches(const slmc_ctx* c) {
+    if (!qrt_active(c)) return 1;
+    const int BP = qr_panel_width(c), np = (c->N + BP - 1) / BP;
+    return np + 3 * (np - 1);
+}
+
+cudaError_t qr_tensor(slmc_ctx* c, int nf, cudaStream_t s) {
+    return qr_panel_width(c) == 32 ? launch_qrt<32>(c, nf, s) : launch_qrt<16>(c, nf, s);
+}
+
+}  // namespace slmc

@@ -27,14 +27,20 @@
 // tensor-core kernels.
 #include <cuda_bf16.h>
 
+#include "slice7.cuh"
 #include "tc_ptx.cuh"
 
 namespace {
 
 using namespace slmc::tc;
+using slmc::s7::abs_bits;
+using slmc::s7::exponent_of_bits;
+using slmc::s7::kS;
+using slmc::s7::pow2d;
+using slmc::s7::slice7;
+using slmc::s7::warp_max_bits;
 
 constexpr int kW = 7;
-constexpr int kS = 7;        // slices of each operand
 constexpr int kLevels = 7;   // a + b = 0..6
 constexpr int kNT = 64;      // columns per CTA
 constexpr int kThreads = 320;
@@ -43,45 +49,6 @@ constexpr uint32_t kBTile = kNT * 128;  // 64 rows (columns of T) x 64 BF16
 constexpr uint32_t kBChunk = kS * kBTile;
 constexpr uint32_t kTmemCols = 512;     // 7 x 64 = 448 used
 constexpr uint32_t kIdesc = idesc_f32acc(1, 128, kNT);
-
-__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
-
-// |v| as an ordered integer (the bit pattern without the sign), and its warp maximum.
-__device__ __forceinline__ long long abs_bits(double v) { return __double_as_longlong(v) & 0x7fffffffffffffffll; }
-
-__device__ __forceinline__ long long warp_max_bits(long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Power of two of the largest |v| from its bit pattern (0 for a zero row or column).
-__device__ __forceinline__ int exponent_of_bits(long long m) {
-    return m == 0 ? 0 : (int)((m >> 52) & 0x7ff) - 1023;
-}
-
-// The seven slices of v in units of 2^(e - 6 - 42), with integer arithmetic only (the FP64 pipe
-// is the scarce unit): v is rounded once to n = round(v 2^(48 - e)) (|n| <= 2^49, half away from
-// zero) and n is written in balanced base-128 digits d_6..d_1 in [-64, 63] and d_0 = the rest,
-// |d_0| <= 128, so v ~ 2^(e - 6) sum_s d_s 2^(-7 s). Each digit is exact in BF16.
-__device__ __forceinline__ void slice7(double v, int e, __nv_bfloat16 (&q)[kS]) {
-    const long long bits = __double_as_longlong(v);
-    const int ex = (int)((bits >> 52) & 0x7ff);
-    long long n = 0;
-    const int r = 1027 + e - ex;  // right shift of the 53-bit significand; >= 4 whenever |v| < 2^(e + 1)
-    if (ex != 0 && r < 63) {
-        const long long m = (bits & 0xfffffffffffffll) | 0x10000000000000ll;
-        n = r > 0 ? (m + (1ll << (r - 1))) >> r : m;
-        if (bits < 0) n = -n;
-    }
-#pragma unroll
-    for (int s = kS - 1; s >= 1; --s) {
-        const int d = (int)((n + 64) & 127) - 64;
-        n = (n - d) >> 7;
-        q[s] = __ushort_as_bfloat16((unsigned short)(__float_as_uint((float)d) >> 16));
-    }
-    q[0] = __ushort_as_bfloat16((unsigned short)(__float_as_uint((float)n) >> 16));
-}
 
 __device__ __forceinline__ int warp_sum_int(int v) {
 #pragma unroll

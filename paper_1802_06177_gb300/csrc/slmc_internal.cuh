@@ -85,6 +85,25 @@ struct slmc_ctx {
     int* tt_flag;
     int tt_mpad, tt_npad, tt_path;
     CUtensorMap tt_mapA, tt_mapB;
+    // Blocked QR with its trailing updates on the tensor cores (k_qrt.cu): one allocation (qt_buf) of
+    // BF16 slices of the trailing columns C [7][fields * qt_mpad][qt_kpad], of the panel reflectors
+    // for W = V^T C [7][fields * 32][qt_kpad] and for V W' [7][fields * qt_mpad][64], of W'
+    // [7][fields * qt_wpad][64]; one of int exponents (qt_ibuf) and a [fields][N] array of the
+    // panels' new scales. qr_path: 0 tensor-core trailing updates, 1 the one-kernel FP64 QR.
+    void* qt_buf;
+    int* qt_ibuf;
+    void* qt_C;
+    void* qt_V1;
+    void* qt_V2;
+    void* qt_W;
+    int* qt_eC;
+    int* qt_eV1;
+    int* qt_eV2;
+    int* qt_eW;
+    int* qt_ntriv;
+    double* qt_lnDn;
+    int qt_kpad, qt_mpad, qt_wpad, qr_path;
+    CUtensorMap qt_mapC, qt_mapV1_16, qt_mapV1_32, qt_mapV2, qt_mapW;
     int fbase;  // first field of this context's workspace within the owner's (views of sub-batches)
     // Split-TF32 slice path (SLMC_PREC_TF32X3): operand pieces of F and of the running slice
     // product (ping/pong), FP32 copies of it, and their TMA descriptors.
@@ -210,6 +229,13 @@ cudaError_t t_update_tiled(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t t_update(slmc_ctx* c, int nf, cudaStream_t s);
 int t_update_launches(const slmc_ctx* c);
 size_t tt_slices();  // BF16 slices per operand of the tensor-core T update
+// QR with tensor-core trailing updates (k_qrt.cu)
+bool qrt_supported(int N);
+void qrt_sizes(int N, int F, size_t* bf16_elems, size_t* int_elems);
+cudaError_t qrt_init(slmc_ctx* c, void* bf16_base, int* int_base);
+bool qrt_active(const slmc_ctx* c);
+int qr_launches(const slmc_ctx* c);
+cudaError_t qr_tensor(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t tt_init(slmc_ctx* c);
 cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t form_q_blocked(slmc_ctx* c, int nf, bool fp32, cudaStream_t s);

@@ -96,10 +96,11 @@ def dqmc_configurations(ctx, x, therm, gap, count, sweep0=0):
 
 def run_dqmc(Lx, L, n_s=8, chains=32, sweeps=500, precision="fp64", dtau=0.1, lam=1.0, omega0=1.0,
              sweep_delta=0.5, seed=0x1802061774, device="cuda", rank=0, world=1, nblock=0, init="gaussian",
-             want_series=False):
+             want_series=False, return_fields=False):
     """Conventional DQMC chains: S(pi, pi) from G after every sweep, its integrated
     autocorrelation time in sweeps and the time per sweep (want_series: also the per-sweep,
-    per-chain S(pi, pi) and the acceptance counts of this process)."""
+    per-chain S(pi, pi) and the acceptance counts of this process; return_fields: also the final
+    fields as a device tensor under "x_final")."""
     dev = torch.device(device)
     seed = seed + rank
     ctx = Context(Lx, Lx, L, dtau=dtau, lam=lam, omega0=omega0, n_s=n_s, precision=precision,
@@ -138,6 +139,8 @@ def run_dqmc(Lx, L, n_s=8, chains=32, sweeps=500, precision="fp64", dtau=0.1, la
         res["S_series"] = obs.cpu().numpy().tolist()
         res["accepted_local"] = n_loc.cpu().numpy().tolist()
         res["accepted_block"] = n_blk.cpu().numpy().tolist()
+    if return_fields:
+        res["x_final"] = x.clone()
     ctx.close()
     return res
 

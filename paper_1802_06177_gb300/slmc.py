@@ -37,7 +37,7 @@ EXPORTS = ("slmc_status_string", "slmc_init", "slmc_destroy", "slmc_get_error", 
            "slmc_profile_read", "slmc_logdet_noalloc", "slmc_logdet_noalloc_scratch_bytes", "slmc_set_update_counter",
            "slmc_get_update_counter", "slmc_set_tuning", "slmc_batch_create", "slmc_batch_destroy",
            "slmc_batch_context", "slmc_batch_bind", "slmc_batch_capture", "slmc_batch_launch", "slmc_autotune",
-           "slmc_batch_set_sweep_queue", "slmc_batch_inject_stall",
+           "slmc_batch_set_sweep_queue", "slmc_batch_inject_stall", "slmc_set_qr_path",
            "slmc_fit_eff_state", "slmc_fit_eff_merge", "slmc_profile_read_detail",
            "slmc_set_sub_batches", "slmc_set_slice_groups",
            "slmc_set_sub_batch_priorities", "slmc_set_qr_cluster", "slmc_set_wolff", "slmc_get_wolff_sites",
@@ -108,6 +108,7 @@ def load_library(path=LIB_PATH):
         "slmc_set_qr_cluster": ([P, I], I),
         "slmc_set_dense_slices": ([P, I], I),
         "slmc_set_tupdate_path": ([P, I], I),
+        "slmc_set_qr_path": ([P, I], I),
         "slmc_set_wolff": ([P, I], I),
         "slmc_get_wolff_sites": ([P, ctypes.POINTER(ctypes.c_longlong), I, V], I),
         "slmc_dqmc_sweep": ([P, P, I, I, U64, I, P, P, V], I),
@@ -351,6 +352,11 @@ class Context:
         tensor kernel with every tile on its FP64 fallback."""
         self._check("slmc_set_tupdate_path", self.lib.slmc_set_tupdate_path(self._ctx, int(path)))
 
+
+    def set_qr_path(self, path):
+        """slmc_set_qr_path: 0 = QR trailing updates on the tensor cores (FP64-accurate sliced
+        BF16), 1 = the one-kernel FP64 QR."""
+        self._check("slmc_set_qr_path", self.lib.slmc_set_qr_path(self._ctx, path))
     def set_sub_batch_priorities(self, on):
         """Descending stream priorities for the sub-batches (1) or equal priorities (0)."""
         self._check("slmc_set_sub_batch_priorities", self.lib.slmc_set_sub_batch_priorities(self._ctx, 1 if on else 0))

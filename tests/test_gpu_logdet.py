@@ -318,3 +318,34 @@ def test_tupdate_paths(precision, Lx, Ly, L, n_s, nf):
     for G, ld, sg in out[1:]:
         assert np.abs(ld - out[0][1]).max() <= TOL_LNDET_FP64
         assert np.abs(G - out[0][0]).max() <= TOL_G_FP64
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x9"])
+@pytest.mark.parametrize("Lx,Ly,L,n_s,nf", [(4, 4, 40, 10, 6), (6, 4, 37, 8, 3), (10, 10, 30, 7, 3),
+                                            (12, 12, 120, 10, 3), (16, 16, 160, 8, 3), (18, 18, 36, 9, 2),
+                                            (24, 24, 48, 8, 2)])
+def test_qr_paths(precision, Lx, Ly, L, n_s, nf):
+    """The pre-pivoted blocked QR with its trailing updates on the tensor cores (exact 7-bit
+    slices of C, V and W', path 0) and with FP64 FMAs (path 1): each within the bars of the
+    oracle, and in FP64 mode the two within the FP64 bars (1e-8 ln det, 1e-9 G) of each other. The shapes span
+    one to five panels of 32 (16 above N = 256) columns, ragged last panels and row tiles, and two
+    accumulator segments of W = V^T C (N = 576 > 448 rows)."""
+    x = inputs.mixed_fields(nf, Lx, Ly, L, seed=500 + L)
+    ctx = make_ctx(Lx, L, n_s, Ly=Ly, precision=precision, max_fields=nf)
+    out = []
+    for path in (0, 1):
+        ctx.set_qr_path(path)
+        G, ld, sg = ctx.greens(cuda(x))
+        ctx.get_error()
+        out.append((G.cpu().numpy(), ld.cpu().numpy(), sg.cpu().numpy()))
+    l_ref, s_ref, G_ref = oracle_many(HolsteinParams(Lx, Ly, L, n_s=n_s), x)
+    tl, tg = (TOL_LNDET_FP64, TOL_G_FP64) if precision == "fp64" else (TOL_LNDET_MIXED, 1e-6)
+    for G, ld, sg in out:
+        assert np.abs(ld - l_ref).max() <= tl
+        assert np.array_equal(sg, s_ref)
+        assert np.abs(G - G_ref).max() <= tg
+    # FP64 mode: the two paths agree to the FP64 bars. Mixed modes cut Q into reduced-precision
+    # slices, where a rounding-level change of Q moves the result by up to a few 1e-7.
+    xl, xg = (TOL_LNDET_FP64, TOL_G_FP64) if precision == "fp64" else (TOL_LNDET_MIXED / 10, 1e-7)
+    assert np.abs(out[0][1] - out[1][1]).max() <= xl
+    assert np.abs(out[0][0] - out[1][0]).max() <= xg
