@@ -465,7 +465,9 @@ SLMC_API int slmc_autotune(const slmc_params* p, int ntune, double tol, slmc_tun
  * and caches it; make that first call before any stream capture. A device reset
  * (cudaDeviceReset) or a new primary context on that device invalidates the cached address:
  * do not use this entry point on that device afterwards in the same process. The arithmetic
- * is that of slmc_logdet (FP64 slices through the separable factors for sides <= 32). All calls share the array
+ * is that of slmc_logdet with slmc_set_tupdate_path(1) and slmc_set_qr_path(1): the T update and
+ * the QR trailing updates with FP64 FMAs (there is no room for their tensor-core slices); FP64
+ * slices through the separable factors for sides <= 32. All calls share the array
  * and it keeps the last call's contents; each call clears the error word it uses on the
  * stream. Calls that overlap on the GPU race on the array: serialise them. Device-side
  * failures are reported only through the outputs (lndet NaN, sign 0). */

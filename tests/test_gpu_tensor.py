@@ -109,6 +109,10 @@ def test_bf16x9_accumulation_is_exact(Lx, L):
     E = exp_hopping(Lx, Lx, 1.0, 0.0, 0.1)
     x = inputs.mixed_fields(2, Lx, Lx, L, seed=5)
     ctx = make_ctx(Lx, L, L, precision="bf16x9", max_fields=2)
+    # the QR and LU of the model are scipy's FP64 ones: compare with the FP64 QR path (the
+    # tensor-core trailing updates err normwise, which this unstabilised group of L slices,
+    # far worse conditioned than any stabilisation interval, turns into ~1e-8 of ln det)
+    ctx.set_qr_path(1)
     lndet, sign = ctx.logdet(cuda(x))
     torch.cuda.synchronize()
     ctx.get_error()

@@ -56,3 +56,15 @@ def test_cdw_initial_fields_sit_at_the_double_well_minima():
     assert abs(x.std(axis=(0, 2)).mean() - 0.3) < 0.05           # noise 0.3 per site
     g = initial_fields("gaussian", 3, Lx, L, alpha, seed=1).numpy()
     assert abs(g.mean()) < 0.1 and abs(g.std() - 1.0) < 0.1
+
+
+def test_warm_start_fields_are_copied_and_checked():
+    import pytest
+    import torch
+
+    from paper_1802_06177_gb300.pipeline import initial_fields
+    x = torch.randn(3, 16, 8, dtype=torch.float64)
+    y = initial_fields(x, 3, 4, 8, 4.0, 0)
+    assert torch.equal(y, x) and y.data_ptr() != x.data_ptr()
+    with pytest.raises(ValueError):
+        initial_fields(x, 2, 4, 8, 4.0, 0)

@@ -3,8 +3,9 @@ ABI: it serves callers that cannot allocate device memory (graph capture, alloca
 hot loops, hosts owning the memory budget), keeping its workspace in a fixed device array.
 Its results must equal those of the regular slmc_logdet on the same fields, on two calls
 in a row (the array is reused and keeps the previous call's contents). The entry point runs
-the T update of the stabilisation with FP64 FMAs (it has no room for the tensor-core slices),
-so the regular context it is compared with is set to the same path. This file is collected
+the T update and the QR trailing updates of the stabilisation with FP64 FMAs (it has no room
+for the tensor-core slices), so the regular context it is compared with is set to the same
+paths. This file is collected
 last so that a failure here cannot hide the other tests' results."""
 import ctypes
 
@@ -27,6 +28,7 @@ def test_noalloc_matches_logdet_twice(Lx, L, n_s, nf):
     assert lib.slmc_logdet_noalloc_scratch_bytes() == 16 << 20
     ctx = make_ctx(Lx, L, n_s, max_fields=nf)
     ctx.set_tupdate_path(1)
+    ctx.set_qr_path(1)
     p = Params(Lx, Lx, L, 0.1, 1.0, 0.0, 1.0, 1.0, n_s, 0, 0.0, 0)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
@@ -59,6 +61,7 @@ def test_noalloc_fp32_matches_logdet(Lx, L, n_s, nf):
     lib = load_library()
     ctx = make_ctx(Lx, L, n_s, precision="fp32", max_fields=nf)
     ctx.set_tupdate_path(1)
+    ctx.set_qr_path(1)
     p = Params(Lx, Lx, L, 0.1, 1.0, 0.0, 1.0, 1.0, n_s, 1, 0.0, 0)
     x = cuda(inputs.mixed_fields(nf, Lx, Lx, L, seed=7))
     ref_l, ref_s = ctx.logdet(x)
@@ -80,6 +83,7 @@ def test_noalloc_reuse_across_lattices_and_chunks():
     for Lx, L, n_s, nf, prec, tol in ((16, 160, 8, 7, "fp32", 1e-10), (4, 40, 10, 9, "fp64", 1e-12)):
         ctx = make_ctx(Lx, L, n_s, precision=prec, max_fields=nf)
         ctx.set_tupdate_path(1)
+        ctx.set_qr_path(1)
         x = cuda(inputs.mixed_fields(nf, Lx, Lx, L, seed=31 + Lx))
         ref_l, ref_s = ctx.logdet(x)
         lndet, sign = logdet_noalloc(x, Lx, Lx, L, n_s=n_s, precision=prec)
