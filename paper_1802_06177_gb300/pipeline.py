@@ -202,9 +202,13 @@ def run(Lx, L, n_s=8, chains=32, train=2000, updates=500, sweeps=100, precision=
         del xs, ys, X, Y
         if r < rounds - 1:
             del xp
-    # production starts from the last self-generated configurations (inside the training
-    # distribution); the initial Gaussian field is atypical for both weights
-    x = (xp if xp is not None else x).contiguous()
+    # production starts from the DQMC chains when they trained E_eff (configurations of the exact
+    # weight w), else from the last self-generated configurations (inside the training
+    # distribution; the initial Gaussian field is atypical for both weights). Near T_c, chains
+    # started from E_eff-generated configurations keep a lower S(pi, pi) for thousands of steps.
+    if train_source != "dqmc":
+        x = xp if xp is not None else x
+    x = x.contiguous()
     lnw, s = ctx.chain_init(x)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0

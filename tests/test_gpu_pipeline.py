@@ -154,7 +154,8 @@ def _oracle_run(Lx, L, n_s, chains, train, updates, sweeps, dtau, lam, omega0, s
             xs.append(xp.copy())
         J = fit(np.concatenate(xs))
         Js.append(J)
-    x = xp if xp is not None else x
+    if train_source != "dqmc":
+        x = xp if xp is not None else x
     lnw, S_cur = [], []
     for c in range(chains):
         lw, _, _, G = log_weight(p, x[c], E=E)
