@@ -192,14 +192,58 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # algorithmic work per launch call of each kernel class (flops or bytes), per field
 # ---------------------------------------------------------------------------------------
-def class_work(cls, wl, nsl_mean, precision="fp32"):
+QR_PANEL_OVERRIDE = [0]  # --qr-panel
+
+
+def qr_panel_width(N):
+    return QR_PANEL_OVERRIDE[0] or (32 if N <= 256 else 16)
+
+
+def qrt_panel_sizes(N):
+    """(p, m, n_t) of every panel of the pre-pivoted blocked QR: first row, rows m = N - p, trailing
+    columns n_t after the panel."""
+    bp = qr_panel_width(N)
+    return [(p, N - p, max(0, N - p - bp)) for p in range(0, N, bp)]
+
+
+def qr_panel_flops(N):
+    """FP64 flops of the panels of one QR: Householder QR of each m x BP panel (2 m BP^2 - 2/3 BP^3),
+    its Gram matrix V^T V (m BP^2) and compact-WY triangle S (BP^3 / 3)."""
+    bp = qr_panel_width(N)
+    return sum(2.0 * m * bp * bp - 2.0 / 3.0 * bp ** 3 + m * bp * bp + bp ** 3 / 3.0 for _, m, _ in qrt_panel_sizes(N))
+
+
+def qr_trailing_flops(N):
+    """FP64-equivalent flops of the trailing updates of one QR: W = V^T C and C - V W' (2 x 2 m n_t BP)."""
+    bp = qr_panel_width(N)
+    return sum(4.0 * m * nt * bp for _, m, nt in qrt_panel_sizes(N))
+
+
+def qr_trailing_issued(N):
+    """BF16 MMA flops the tensor-core trailing updates of one QR issue: 28 slice products each of
+    W^T = C^T V (128-row tiles of trailing columns x BP x K chunks of 64 from the chunk of row p)
+    and of V W' (128-row tiles from the tile of row p x 64-column tiles x BP)."""
+    bp = qr_panel_width(N)
+    kpad, mpad = -(-N // 64) * 64, -(-N // 128) * 128
+    t = 0.0
+    for p, _, nt in qrt_panel_sizes(N):
+        if nt == 0:
+            continue
+        t += 28 * 2.0 * (128 * -(-nt // 128)) * bp * (kpad - 64 * (p // 64))
+        t += 28 * 2.0 * (mpad - 128 * (p // 128)) * (64 * -(-nt // 64)) * bp
+    return t
+
+
+def class_work(cls, wl, nsl_mean, precision="fp32", qrt=False):
     N, L = wl.N, wl.L
     if cls == "slice" and precision == "fp64":  # separable exp(-dtau K): N^2 (Lx + Ly) FMAs per slice
         return 2.0 * N ** 2 * (2 * wl.Lx) * nsl_mean, "flop"
     if cls == "slice":
         return 2.0 * N ** 3 * nsl_mean, "flop"
-    if cls == "qr":
-        return 4.0 / 3.0 * N ** 3, "flop"
+    if cls == "qr":  # per field and QR: with the tensor-core trailing updates, the FP64 panels alone
+        return (qr_panel_flops(N) if qrt else 4.0 / 3.0 * N ** 3), "flop"
+    if cls == "qrtc":
+        return qr_trailing_flops(N), "flop"
     if cls == "formq":
         return 4.0 / 3.0 * N ** 3, "flop"
     if cls == "tupdate":
@@ -213,7 +257,8 @@ def class_work(cls, wl, nsl_mean, precision="fp32"):
 
 # DRAM traffic per field of the dominant kernel, from the committed ncu summary of that
 # kernel; valid only while the kernel source is the one the counters were taken on.
-TRAFFIC_SOURCES = {"qr": ("profiles/k_qrb_16x16_L160.md", "paper_1802_06177_gb300/csrc/k_qrb.cu")}
+TRAFFIC_SOURCES = {"qr": ("profiles/k_qrt_16x16_L160.md", "paper_1802_06177_gb300/csrc/k_qrt.cu"),
+                   "qrtc": ("profiles/k_qrt_16x16_L160.md", "paper_1802_06177_gb300/csrc/k_qrt.cu")}
 
 
 def kernel_traffic(cls, fields_per_call):
@@ -224,7 +269,7 @@ def kernel_traffic(cls, fields_per_call):
     prof_md, src = (os.path.join(ROOT, q) for q in TRAFFIC_SOURCES[cls])
     if not (os.path.exists(prof_md) and os.path.exists(src)):
         return None
-    m = re.search(r"traffic-per-field: ([0-9.eE+]+) bytes \(source sha256 ([0-9a-f]+)\)", open(prof_md).read())
+    m = re.search(r"traffic-per-field %s: ([0-9.eE+]+) bytes \(source sha256 ([0-9a-f]+)\)" % cls, open(prof_md).read())
     if not m:
         return None
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -359,6 +404,15 @@ def tensor_use(wl, nf, ngroups, precision, prof, peaks):
         out["slice:" + precision] = {"issued_tflops": t, "peak_tflops": peak, "frac_of_peak": t / peak,
                                      "busy_ms": sl[2], "dense_fp32_equivalent_tflops":
                                      2.0 * N ** 3 * nsl_mean * sl[3] / (sl[2] / 1e3) / 1e12, "peak_source": how}
+    qt = prof.get("qrtc")
+    if qt and qt[2] > 0:
+        field_qrs = qt[3] / max(1, len(qrt_panel_sizes(N)) - 1)  # one call per panel but the last
+        issued = qr_trailing_issued(N) * field_qrs
+        t = issued / (qt[2] / 1e3) / 1e12
+        out["qrtc:" + precision] = {"issued_tflops": t, "peak_tflops": bf16, "frac_of_peak": t / bf16,
+                                    "busy_ms": qt[2], "includes": "the slicing of the trailing columns",
+                                    "fp64_equivalent_tflops": qr_trailing_flops(N) * field_qrs / (qt[2] / 1e3) / 1e12,
+                                    "peak_source": src}
     tu = prof.get("tupdate")
     if tu and tu[2] > 0:
         nk = npad // 64
@@ -384,6 +438,7 @@ def run_gpu(args):
     rank, local, world = dist_setup(args)
     wl = WORKLOADS[args.workload]
     nf = args.fields or wl.nfields
+    QR_PANEL_OVERRIDE[0] = args.qr_panel
     pool = None
     nproc = min(16, os.cpu_count() or 1)
     if rank == 0 and not args.no_cpu_baseline:
@@ -408,6 +463,10 @@ def run_gpu(args):
             c.set_qr_cluster(args.qr_cluster)
         if args.dense_slices:
             c.set_dense_slices(1)
+        if args.qr_panel:
+            c.set_tuning(args.qr_panel, 0)
+        if args.qr_path >= 0:
+            c.set_qr_path(args.qr_path)
         return c
 
     def setup(ctx):
@@ -523,7 +582,13 @@ def run_gpu(args):
     # (union of their call intervals) and divide the class's work by it
     dom = max(prof, key=lambda k: prof[k][2])
     dom_ms, dom_calls, dom_busy, dom_units = prof[dom]
-    work, kind = class_work(dom, wl, nsl_mean, args.precision)
+    # with the tensor-core trailing updates a QR is one "qr" call per panel and one "qrtc" call per
+    # panel but the last: count QRs of all fields (field-QRs) and calls per QR
+    qrt = bool(prof.get("qrtc") and prof["qrtc"][1] > 0)
+    npan = len(qrt_panel_sizes(wl.N))
+    per_qr = {"qr": npan, "qrtc": max(1, npan - 1)}.get(dom, 1) if qrt else 1
+    dom_calls, dom_units = dom_calls / per_qr, dom_units / per_qr
+    work, kind = class_work(dom, wl, nsl_mean, args.precision, qrt)
     roof = None
     if work:
         fields_per_call = dom_units / max(dom_calls, 1)
@@ -547,6 +612,11 @@ def run_gpu(args):
             roof = dict(common, bound="alu", pipe="fp64" if fp64_cls else "fp32", achieved=achieved, peak=peak,
                         unit="TFLOP/s", frac=achieved / peak, peak_probed=pk, frac_of_probed=achieved / pk,
                         traffic=traffic, peak_source=src)
+        elif kind == "flop" and dom == "qrtc":
+            t = tensor_use(wl, nf, ngroups, args.precision, prof, peaks).get("qrtc:" + args.precision)
+            if t:
+                roof = dict(common, bound="tensor", achieved=t["issued_tflops"], peak=t["peak_tflops"],
+                            unit="TFLOP/s", frac=t["frac_of_peak"], traffic=None, peak_source=t["peak_source"])
         elif kind == "flop":  # tensor-core classes: issued BF16 flops against the measured BF16 rate
             t = tensor_use(wl, nf, ngroups, args.precision, prof, peaks).get(dom + ":" + args.precision)
             if t:
@@ -596,18 +666,20 @@ def run_gpu(args):
     # every mode; the other groups' Q is FP64 only in FP64 mode), final LU, G, and FP64 slices in
     # FP64 mode; the T update runs on the tensor cores) against the step time
     N3 = float(wl.N) ** 3
-    w64 = ngroups * (4.0 / 3.0) * N3 + (4.0 / 3.0) * N3 * (ngroups if args.precision == "fp64" else 1) \
+    w_qr = qr_panel_flops(wl.N) if qrt else (4.0 / 3.0) * N3  # the panels alone when the trailing updates are TC
+    w64 = ngroups * w_qr + (4.0 / 3.0) * N3 * (ngroups if args.precision == "fp64" else 1) \
         + (2.0 / 3.0 + (2.0 if args.mode == "step" else 0.0)) * N3
     if args.precision == "fp64":  # slices through the separable exp(-dtau K): N^2 (Lx + Ly) FMAs each
         w64 += 2.0 * float(wl.N) ** 2 * (2 * wl.Lx) * wl.L
     ach64 = w64 * nf * world / (ms_step / 1e3) / 1e12 / world
     fp64_step = {"flop_per_eval": w64, "achieved_per_gpu": ach64, "unit": "TFLOP/s",
                  "frac_of_nominal": ach64 / NOMINAL["fp64_tflops"], "frac_of_probed": ach64 / probed["fp64_tflops"],
-                 "excludes": "T update (tensor cores)"}
+                 "excludes": "T update (tensor cores)" + (", QR trailing updates (tensor cores)" if qrt else "")}
     dtype = {"fp64": "f64", "fp32": "f32 slices + f64 stabilisation",
              "tf32x3": "tf32x3 slices (tensor cores) + f64 stabilisation",
              "bf16x9": "bf16x9 exact-sliced slices (tensor cores) + f64 stabilisation"}[args.precision] + \
-        "; T update f64-accurate on the tensor cores (bf16 slices)"
+        "; T update f64-accurate on the tensor cores (bf16 slices)" + \
+        ("; QR trailing updates f64-accurate on the tensor cores (bf16 slices)" if qrt else "")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config_of(wl, args, args.precision),
@@ -861,6 +933,8 @@ def main():
     ap.add_argument("--sub-priorities", type=int, default=-1, help="descending sub-batch stream priorities (1/0)")
     ap.add_argument("--qr-cluster", type=int, default=0, help="CTAs per field of the QR (0 = automatic, 1, 2, 4)")
     ap.add_argument("--dense-slices", action="store_true", help="FP64 mode: dense exp(-dtau K) slice products")
+    ap.add_argument("--qr-panel", type=int, default=0, help="QR panel width 16 or 32 (0 = default)")
+    ap.add_argument("--qr-path", type=int, default=-1, help="0 = QR trailing updates on the tensor cores, 1 = FP64")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "slmc":
         args.warmup = 3

@@ -357,7 +357,7 @@ SLMC_API int slmc_measure_cdw(slmc_ctx* ctx, const double* G, int n, double* S, 
 
 /* Kernel classes reported by slmc_profile_read (index into its arrays). */
 #define SLMC_PROF_SLICE 0     /* slice-group products B ... B U */
-#define SLMC_PROF_QR 1        /* pivoted Householder QR */
+#define SLMC_PROF_QR 1        /* pivoted Householder QR (with SLMC_PROF_QRTC: its panels only) */
 #define SLMC_PROF_FORMQ 2     /* formation of Q */
 #define SLMC_PROF_TUPDATE 3   /* T <- Rt P^T T */
 #define SLMC_PROF_FINAL 4     /* identity init, M assembly, LU and log-det */
@@ -370,7 +370,8 @@ SLMC_API int slmc_measure_cdw(slmc_ctx* ctx, const double* G, int n, double* S, 
 #define SLMC_PROF_CDW 11      /* S(pi,pi) */
 #define SLMC_PROF_WOLFF 12    /* Wolff cluster updates of the effective model */
 #define SLMC_PROF_DQMC 13     /* DQMC local updates (fast ratio, Sherman-Morrison, wrapping) */
-#define SLMC_PROF_NCLASS 14
+#define SLMC_PROF_QRTC 14     /* QR trailing updates on the tensor cores (slmc_set_qr_path 0) */
+#define SLMC_PROF_NCLASS 15
 
 /* Total number of CUDA kernels this context has enqueued since slmc_init (host counter,
  * no synchronisation). */

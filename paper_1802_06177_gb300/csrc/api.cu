@@ -111,7 +111,9 @@ int launch(slmc_ctx* c, int cls, int nkernels, cudaStream_t s, Fn&& fn) {
         c->ev_rec.push_back(e);
         c->ev_cls.push_back(cls);
         c->ev_units.push_back(c->cur_units);
-        if (c->ev_cls.size() >= 4096) return flush_profile(c);  // bounded pool: drains recorded pairs
+        // bounded pool: drains the recorded pairs (a device synchronisation) every 65536 calls,
+        // well beyond a profiled region of a few steps
+        if (c->ev_cls.size() >= 65536) return flush_profile(c);
     }
     return SLMC_OK;
 }
@@ -145,10 +147,15 @@ int logdet_run(slmc_ctx* c, slmc_ctx* v, const double* x, int nf, double* lndet,
             if (v->p.precision != SLMC_PREC_FP64 && l0 + nsl < v->L)
                 SLMC_LAUNCH(SLMC_PROF_FORMQ, 1, s, slmc::u_to_f32(v, nf, s));
         } else {
-            if (slmc::qrt_active(v))
-                SLMC_LAUNCH(SLMC_PROF_QR, slmc::qr_launches(v), s, slmc::qr_tensor(v, nf, s));
-            else
+            if (slmc::qrt_active(v)) {  // panels in FP64, trailing updates on the tensor cores
+                const int np = slmc::qrt_panels(v);
+                for (int t = 0; t < np; ++t) {
+                    SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qrt_panel(v, nf, t, s));
+                    if (t + 1 < np) SLMC_LAUNCH(SLMC_PROF_QRTC, 3, s, slmc::qrt_trailing(v, nf, t, s));
+                }
+            } else {
                 SLMC_LAUNCH(SLMC_PROF_QR, 1, s, slmc::qr_blocked(v, nf, s));
+            }
             // Q enters the next reduced-precision slice group (rounded to FP32 there anyway) except
             // after the last group, where it enters the FP64 final step.
             const bool q32 = v->p.precision != SLMC_PREC_FP64 && l0 + nsl < v->L;

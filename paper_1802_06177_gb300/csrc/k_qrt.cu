@@ -150,18 +150,20 @@ __global__ void __launch_bounds__(kThreads, 2)
                    s_beta, s_perm, &s_ntriv, &s_wide, N, p, nb);
     __syncthreads();
     if (tid < nb) lnDn_ws[(size_t)gf * N + p + tid] = s_lnDn[p + tid];
-    const int ntriv = (t == 0 ? 0 : ntriv_ws[gf]) + s_ntriv;
-    if (t == npanels - 1) {  // every scale is known: publish ln D', the sign of det U
+    if (tid == 0) {  // reflectors with tau != 0 so far (their parity is the sign of det U)
+        const int ntriv = (t == 0 ? 0 : ntriv_ws[gf]) + s_ntriv;
+        if (t == npanels - 1) sgnU[f] = (ntriv & 1) ? -1 : 1;
+        else ntriv_ws[gf] = ntriv;
+    }
+    if (t == npanels - 1) {  // every scale is known: publish ln D'
         bool bad = false;
         for (int k = tid; k < N; k += kThreads) {
             lnD_all[(size_t)f * N + k] = s_lnDn[k];
             bad |= !isfinite(s_lnDn[k]);
         }
-        if (tid == 0) sgnU[f] = (ntriv & 1) ? -1 : 1;
         if (bad) atomicOr(err, SLMC_EBIT_NONFINITE);
         return;
     }
-    if (tid == 0) ntriv_ws[gf] = ntriv;
     // V1: reflector m over rows p..N-1 (K-major, K chunks from the one holding row p)
     const int kstart = (p / 64) * 64;
     for (int m = warp; m < BP; m += kWarps) {
@@ -526,37 +528,60 @@ __global__ void __launch_bounds__(kQT, 1)
 size_t gemm1_smem(int BP) { return 1024 + 2 * (size_t)kS * BP * 128 + (size_t)kS * kTileA; }
 size_t gemm2_smem() { return 1024 + (size_t)kS * (kTileA + 64 * 128); }
 
-template <int BP>
-cudaError_t launch_qrt(slmc_ctx* c, int nf, cudaStream_t s) {
-    const int N = c->N, npanels = (N + BP - 1) / BP, kpad = c->qt_kpad, mpad = c->qt_mpad, wpad = c->qt_wpad;
-    const int jpad = mpad;
+struct QrtArgs {
+    int N, kpad, mpad, wpad, jpad;
+    size_t plane1, plane2, planeC, planeW;
+    __nv_bfloat16 *V1, *V2, *Cs, *Ws;
+};
+
+QrtArgs qrt_args(const slmc_ctx* c) {
+    QrtArgs a;
+    a.N = c->N;
+    a.kpad = c->qt_kpad;
+    a.mpad = c->qt_mpad;
+    a.wpad = c->qt_wpad;
+    a.jpad = c->qt_mpad;
     const size_t F = c->max_fields;
-    const size_t plane1 = F * kVRows * kpad, plane2 = F * mpad * 64, planeC = F * jpad * kpad, planeW = F * wpad * 64;
-    __nv_bfloat16* V1 = reinterpret_cast<__nv_bfloat16*>(c->qt_V1);
-    __nv_bfloat16* V2 = reinterpret_cast<__nv_bfloat16*>(c->qt_V2);
-    __nv_bfloat16* Cs = reinterpret_cast<__nv_bfloat16*>(c->qt_C);
-    __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(c->qt_W);
-    const size_t smP = QrSmem<BP>::bytes(N), sm1 = gemm1_smem(BP), sm2 = gemm2_smem();
+    a.plane1 = F * kVRows * a.kpad;
+    a.plane2 = F * a.mpad * 64;
+    a.planeC = F * a.jpad * a.kpad;
+    a.planeW = F * a.wpad * 64;
+    a.V1 = reinterpret_cast<__nv_bfloat16*>(c->qt_V1);
+    a.V2 = reinterpret_cast<__nv_bfloat16*>(c->qt_V2);
+    a.Cs = reinterpret_cast<__nv_bfloat16*>(c->qt_C);
+    a.Ws = reinterpret_cast<__nv_bfloat16*>(c->qt_W);
+    return a;
+}
+
+template <int BP>
+cudaError_t launch_panel(slmc_ctx* c, int nf, int t, cudaStream_t s) {
+    const QrtArgs a = qrt_args(c);
+    const size_t smP = QrSmem<BP>::bytes(a.N);
     cudaError_t e = cudaFuncSetAttribute(k_qrt_panel<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smP);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_qrt_gemm1<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e != cudaSuccess) return e;
+    k_qrt_panel<BP><<<nf, kThreads, smP, s>>>(c->Y, c->lnD, c->QR, c->tau, c->perm, c->sgnU, c->Sws, c->err, a.N, t,
+                                              c->qt_lnDn, c->qt_ntriv, a.V1, c->qt_eV1, a.V2, c->qt_eV2, a.kpad,
+                                              a.mpad, a.plane1, a.plane2, c->fbase);
+    return cudaGetLastError();
+}
+
+// Trailing update of panel t (t < last panel): slices of C, W'^T = (C^T V) S, C -= V W'.
+template <int BP>
+cudaError_t launch_trailing(slmc_ctx* c, int nf, int t, cudaStream_t s) {
+    const QrtArgs a = qrt_args(c);
+    const size_t sm1 = gemm1_smem(BP), sm2 = gemm2_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_qrt_gemm1<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_qrt_gemm2<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
     if (e != cudaSuccess) return e;
     const CUtensorMap& mapV1 = BP == 32 ? c->qt_mapV1_32 : c->qt_mapV1_16;
-    for (int t = 0; t < npanels; ++t) {
-        const int p = t * BP;
-        k_qrt_panel<BP><<<nf, kThreads, smP, s>>>(c->Y, c->lnD, c->QR, c->tau, c->perm, c->sgnU, c->Sws, c->err, N, t,
-                                                  c->qt_lnDn, c->qt_ntriv, V1, c->qt_eV1, V2, c->qt_eV2, kpad, mpad,
-                                                  plane1, plane2, c->fbase);
-        if (t + 1 == npanels) break;
-        const int j0 = p + BP, n_t = N - j0;
-        k_qrt_slice_C<<<dim3((n_t + 7) / 8, nf), 256, 0, s>>>(c->Y, c->perm, Cs, c->qt_eC, N, p, j0, kpad, jpad, planeC,
-                                                              c->fbase);
-        k_qrt_gemm1<BP><<<dim3((n_t + 127) / 128, nf), kQT, sm1, s>>>(c->qt_mapC, mapV1, c->qt_eC, c->qt_eV1, c->Sws,
-                                                                      Ws, c->qt_eW, N, p, n_t, kpad, jpad, wpad, planeW,
-                                                                      c->fbase, c->err);
-        k_qrt_gemm2<BP><<<dim3((n_t + 63) / 64, mpad / 128 - p / 128, nf), kQT, sm2, s>>>(
-            c->qt_mapV2, c->qt_mapW, c->qt_eV2, c->qt_eW, c->perm, c->Y, N, p, j0, n_t, mpad, wpad, c->fbase, c->err);
-    }
+    const int N = a.N, p = t * BP, j0 = p + BP, n_t = N - j0;
+    k_qrt_slice_C<<<dim3((n_t + 7) / 8, nf), 256, 0, s>>>(c->Y, c->perm, a.Cs, c->qt_eC, N, p, j0, a.kpad, a.jpad,
+                                                          a.planeC, c->fbase);
+    k_qrt_gemm1<BP><<<dim3((n_t + 127) / 128, nf), kQT, sm1, s>>>(c->qt_mapC, mapV1, c->qt_eC, c->qt_eV1, c->Sws, a.Ws,
+                                                                  c->qt_eW, N, p, n_t, a.kpad, a.jpad, a.wpad, a.planeW,
+                                                                  c->fbase, c->err);
+    k_qrt_gemm2<BP><<<dim3((n_t + 63) / 64, a.mpad / 128 - p / 128, nf), kQT, sm2, s>>>(
+        c->qt_mapV2, c->qt_mapW, c->qt_eV2, c->qt_eW, c->perm, c->Y, N, p, j0, n_t, a.mpad, a.wpad, c->fbase, c->err);
     return cudaGetLastError();
 }
 
@@ -612,14 +637,17 @@ cudaError_t qrt_init(slmc_ctx* c, void* bf16_base, int* int_base) {
 
 bool qrt_active(const slmc_ctx* c) { return c->qt_C && c->qr_path == 0 && qrt_supported(c->N); }
 
-int qr_launches(const slmc_ctx* c) {
-    if (!qrt_active(c)) return 1;
-    const int BP = qr_panel_width(c), np = (c->N + BP - 1) / BP;
-    return np + 3 * (np - 1);
+int qrt_panels(const slmc_ctx* c) {
+    const int BP = qr_panel_width(c);
+    return (c->N + BP - 1) / BP;
 }
 
-cudaError_t qr_tensor(slmc_ctx* c, int nf, cudaStream_t s) {
-    return qr_panel_width(c) == 32 ? launch_qrt<32>(c, nf, s) : launch_qrt<16>(c, nf, s);
+cudaError_t qrt_panel(slmc_ctx* c, int nf, int t, cudaStream_t s) {
+    return qr_panel_width(c) == 32 ? launch_panel<32>(c, nf, t, s) : launch_panel<16>(c, nf, t, s);
+}
+
+cudaError_t qrt_trailing(slmc_ctx* c, int nf, int t, cudaStream_t s) {
+    return qr_panel_width(c) == 32 ? launch_trailing<32>(c, nf, t, s) : launch_trailing<16>(c, nf, t, s);
 }
 
 }  // namespace slmc

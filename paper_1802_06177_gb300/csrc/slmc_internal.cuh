@@ -234,8 +234,9 @@ bool qrt_supported(int N);
 void qrt_sizes(int N, int F, size_t* bf16_elems, size_t* int_elems);
 cudaError_t qrt_init(slmc_ctx* c, void* bf16_base, int* int_base);
 bool qrt_active(const slmc_ctx* c);
-int qr_launches(const slmc_ctx* c);
-cudaError_t qr_tensor(slmc_ctx* c, int nf, cudaStream_t s);
+int qrt_panels(const slmc_ctx* c);
+cudaError_t qrt_panel(slmc_ctx* c, int nf, int t, cudaStream_t s);     // factor panel t (1 launch)
+cudaError_t qrt_trailing(slmc_ctx* c, int nf, int t, cudaStream_t s);  // its trailing update (3 launches)
 cudaError_t tt_init(slmc_ctx* c);
 cudaError_t qr_blocked(slmc_ctx* c, int nf, cudaStream_t s);
 cudaError_t form_q_blocked(slmc_ctx* c, int nf, bool fp32, cudaStream_t s);

@@ -52,7 +52,7 @@ class TuneResult(ctypes.Structure):
                 ("sec_per_eval", ctypes.c_double), ("max_abs_dlndet", ctypes.c_double), ("candidates", ctypes.c_int)]
 
 PROF_CLASSES = ("slice", "qr", "formq", "tupdate", "final", "greens", "sweep", "eff", "bose", "accept", "fit", "cdw",
-                "wolff", "dqmc")
+                "wolff", "dqmc", "qrtc")
 
 _lib = None
 
