@@ -215,8 +215,14 @@ def test_sub_batch_split_is_bit_identical_and_profiled(precision):
         ctx.profile(False)
         out.append((G.cpu().numpy(), ld.cpu().numpy(), sg.cpu().numpy()))
         groups = -(-L // n_s)
+        # the QR runs as one call per panel of 32 columns (factorisation, "qr") and one per panel
+        # but the last (tensor-core trailing update, "qrtc")
+        npan = -(-(Lx * Lx) // 32)
         ms, calls, busy, units = prof["qr"]
-        assert units == nf * groups and calls == groups * nsub
+        assert units == nf * groups * npan and calls == groups * nsub * npan
+        assert 0.0 < busy <= ms * (1 + 1e-6) + 1e-3
+        ms, calls, busy, units = prof["qrtc"]
+        assert units == nf * groups * (npan - 1) and calls == groups * nsub * (npan - 1)
         assert 0.0 < busy <= ms * (1 + 1e-6) + 1e-3
         assert prof["greens"][3] == nf
     ctx.set_sub_batches(3)
