@@ -51,6 +51,10 @@ constexpr uint32_t kTileA = 128 * 128;       // 128 rows x 64 BF16 (one 128-byte
 constexpr int kSegChunks = 7;                // K chunks (64 rows) per accumulator set of W^T = C^T V
 constexpr int kMaxN = 2 * kSegChunks * 64;   // 896: two accumulator sets
 constexpr int kVRows = 32;                   // rows of the V1 slice buffer per field (BP <= 32)
+// W^T = C^T V streams the seven C slices of a K chunk through a ring of three tiles (tile a is
+// released once its products with the seven V slices are issued), so two CTAs fit on an SM: one's
+// FP64 epilogue then overlaps the other's copies and products.
+constexpr int kRing = 3;
 // 2^-54: the digits' units 2^(e - 6) per operand and the level weights 2^(-7 level), 2^-42 at level 6
 constexpr int kUnitShift = 2 * 6 + 7 * (kLv - 1);
 
@@ -65,8 +69,13 @@ __device__ __forceinline__ void levels_to_int(const uint32_t (&v)[kLv], long lon
 }
 
 // ---- panel ----------------------------------------------------------------------------------
+// 16 warps per field: the panel is a chain of latency-bound column steps (dot products, warp
+// reductions, a block barrier each) that leaves the FP64 pipe half idle with 8 warps.
+constexpr int kPT = 512;
+constexpr int kPW = kPT / 32;
+
 template <int BP>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kPT, 2)
     k_qrt_panel(double* __restrict__ Yall, double* __restrict__ lnD_all, double* __restrict__ QRall,
                 double* __restrict__ tau_all, int* __restrict__ perm_all, int* __restrict__ sgnU,
                 double* __restrict__ Sall, unsigned int* __restrict__ err, int N, int t, double* __restrict__ lnDn_ws,
@@ -82,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     double* Vp = reinterpret_cast<double*>(smraw);
     double* Ssm = Vp + (size_t)N * BPS;
     double* Wsm = Ssm + BP * BP;
-    double* s_key = Wsm + kWarps * BP * kCT;
+    double* s_key = Wsm + kWarps * BP * kCT;  // the layout of QrSmem<BP> (Wsm holds the Gram matrix here)
     double* s_lnd = s_key + N;
     double* s_lnDn = s_lnd + N;
     double* s_g = s_lnDn + N;
@@ -94,7 +103,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int p = t * BP, nb = min(BP, N - p), npanels = (N + BP - 1) / BP;
 
-    for (int j = tid; j < N; j += kThreads) s_lnd[j] = lnD_all[(size_t)f * N + j];
+    for (int j = tid; j < N; j += kPT) s_lnd[j] = lnD_all[(size_t)f * N + j];
     if (tid == 0) {
         s_ntriv = 0;
         s_wide = 0;
@@ -109,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (lane == 0) s_mx = mx;
         }
         __syncthreads();
-        for (int j = warp; j < N; j += kWarps) {
+        for (int j = warp; j < N; j += kPW) {
             double a = 0.0;
             for (int i = lane; i < N; i += 32) {
                 const double y = Y[(size_t)j * N + i];
@@ -122,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
         }
         __syncthreads();
-        for (int j = tid; j < N; j += kThreads) {
+        for (int j = tid; j < N; j += kPT) {
             const double kj = s_key[j];
             int r = 0;
             for (int i = 0; i < N; ++i) {
@@ -132,21 +141,21 @@ __global__ void __launch_bounds__(kThreads, 2)
             s_perm[r] = j;
         }
         __syncthreads();
-        for (int j = tid; j < N; j += kThreads) perm_all[(size_t)f * N + j] = s_perm[j];
+        for (int j = tid; j < N; j += kPT) perm_all[(size_t)f * N + j] = s_perm[j];
     } else {
-        for (int j = tid; j < N; j += kThreads) s_perm[j] = perm_all[(size_t)f * N + j];
-        for (int i = tid; i < p; i += kThreads) {
+        for (int j = tid; j < N; j += kPT) s_perm[j] = perm_all[(size_t)f * N + j];
+        for (int i = tid; i < p; i += kPT) {
             const double l = lnDn_ws[(size_t)gf * N + i];
             s_lnDn[i] = l;
             s_g[i] = exp(-l);
             if (fabs(l) > 600.0) s_wide = 1;
         }
     }
-    for (int k = tid; k < N; k += kThreads)
+    for (int k = tid; k < N; k += kPT)
         if (fabs(s_lnd[k]) > 600.0) s_wide = 1;
     __syncthreads();
 
-    panel_step<BP>(Y, QR, tau_all + (size_t)f * N, Sall + (size_t)f * N * BP, Vp, Ssm, Wsm, s_lnd, s_lnDn, s_g, s_tau,
+    panel_step<BP, kPT>(Y, QR, tau_all + (size_t)f * N, Sall + (size_t)f * N * BP, Vp, Ssm, Wsm, s_lnd, s_lnDn, s_g, s_tau,
                    s_beta, s_perm, &s_ntriv, &s_wide, N, p, nb);
     __syncthreads();
     if (tid < nb) lnDn_ws[(size_t)gf * N + p + tid] = s_lnDn[p + tid];
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     if (t == npanels - 1) {  // every scale is known: publish ln D'
         bool bad = false;
-        for (int k = tid; k < N; k += kThreads) {
+        for (int k = tid; k < N; k += kPT) {
             lnD_all[(size_t)f * N + k] = s_lnDn[k];
             bad |= !isfinite(s_lnDn[k]);
         }
@@ -166,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     // V1: reflector m over rows p..N-1 (K-major, K chunks from the one holding row p)
     const int kstart = (p / 64) * 64;
-    for (int m = warp; m < BP; m += kWarps) {
+    for (int m = warp; m < BP; m += kPW) {
         long long mx = 0;
         for (int r = p + lane; r < N; r += 32) mx = max(mx, abs_bits(Vp[r * BPS + m]));
         const int e = exponent_of_bits(warp_max_bits(mx));
@@ -181,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     // V2: row r over the reflectors (K = the BP reflectors, padded to 64 with zeros set at init),
     // rows of the first row tile that holds row p onward
-    for (int r = (p / 128) * 128 + warp; r < mpad; r += kWarps) {
+    for (int r = (p / 128) * 128 + warp; r < mpad; r += kPW) {
         const double v = (r >= p && r < N && lane < BP) ? Vp[r * BPS + lane] : 0.0;
         const int e = exponent_of_bits(warp_max_bits(abs_bits(v)));
         if (lane == 0) eV2[(size_t)gf * mpad + r] = e;
@@ -221,7 +230,7 @@ __global__ void __launch_bounds__(256) k_qrt_slice_C(const double* __restrict__ 
 // through a 7-tile ring and the seven V slices double-buffered; products (a, b), a + b <= 6, go to
 // the accumulator of level a + b of the chunk's segment (seven chunks per segment).
 template <int BP>
-__global__ void __launch_bounds__(kQT, 1)
+__global__ void __launch_bounds__(kQT, 2)
     k_qrt_gemm1(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmV,
                 const int* __restrict__ eC, const int* __restrict__ eV1, const double* __restrict__ Sall,
                 __nv_bfloat16* __restrict__ Ws, int* __restrict__ eW, int N, int p, int n_t, int kpad, int jpad,
@@ -234,19 +243,20 @@ __global__ void __launch_bounds__(kQT, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kc0 = p / 64, nkc = kpad / 64 - kc0;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar_full[kS], bar_empty[kS], bar_bfull[2], bar_bempty[2], bar_acc, bar_done;
+    __shared__ __align__(8) uint64_t bar_full[kRing], bar_empty[kRing], bar_bfull[2], bar_bempty[2], bar_acc, bar_done;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
+    __shared__ int eV_sh[BP];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t bbuf = base, aring = base + 2 * kChunkB;
-    // after the MMAs: stage of W [128][WS], W' [128][WS] and S [BP][BP] in the ring
-    double* stW = reinterpret_cast<double*>(smem_raw + (aring - raw));
+    // after the MMAs: stage of W [128][WS], W' [128][WS] and S [BP][BP] over the B buffers and the ring
+    double* stW = reinterpret_cast<double*>(smem_raw + (bbuf - raw));
     double* stWp = stW + 128 * WS;
     double* Ssh = stWp + 128 * WS;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kS; ++s) {
+        for (int s = 0; s < kRing; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
@@ -259,8 +269,11 @@ __global__ void __launch_bounds__(kQT, 1)
         abort_sh = 0;
         fence_barrier_init();
     }
+    if (threadIdx.x < BP) eV_sh[threadIdx.x] = eV1[(size_t)gf * kVRows + threadIdx.x];
+    const int nseg = (nkc + kSegChunks - 1) / kSegChunks;
+    const uint32_t tcols = nseg == 1 ? 256u : 512u;  // 7 levels x BP columns per accumulator set
     if (warp == 9) {
-        tmem_alloc(smem_u32(&tmem_base_sh), 512);
+        tmem_alloc(smem_u32(&tmem_base_sh), tcols);
         tc_fence_before();
     }
     __syncthreads();
@@ -281,19 +294,20 @@ __global__ void __launch_bounds__(kQT, 1)
                 for (int b = 0; b < kS; ++b) tma_load_3d(bbuf + bs * kChunkB + b * kTileB, &tmV, kc * 64, gf * kVRows, b, bb);
                 issued_b = u + 1;
                 for (int a = 0; a < kS; ++a) {
-                    const int q = u * kS + a;
-                    if (q >= kS && !mbar_wait(smem_u32(&bar_empty[a]), ((q / kS) - 1) & 1, err)) {
+                    const int q = u * kS + a, slot = q % kRing;
+                    if (q >= kRing && !mbar_wait(smem_u32(&bar_empty[slot]), ((q / kRing) - 1) & 1, err)) {
                         abort_sh = 1;
                         break;
                     }
-                    const uint32_t fb = smem_u32(&bar_full[a]);
+                    const uint32_t fb = smem_u32(&bar_full[slot]);
                     mbar_expect_tx(fb, kTileA);
-                    tma_load_3d(aring + a * kTileA, &tmC, kc * 64, gf * jpad + mt * 128, a, fb);
+                    tma_load_3d(aring + slot * kTileA, &tmC, kc * 64, gf * jpad + mt * 128, a, fb);
                     issued_a = q + 1;
                 }
+                if (abort_sh) break;
             }
-            for (int q = issued_a - 1; q >= 0 && q >= issued_a - kS; --q)
-                mbar_wait(smem_u32(&bar_full[q % kS]), (q / kS) & 1, err);
+            for (int q = issued_a - 1; q >= 0 && q >= issued_a - kRing; --q)
+                mbar_wait(smem_u32(&bar_full[q % kRing]), (q / kRing) & 1, err);
             for (int u = issued_b - 1; u >= 0 && u >= issued_b - 2; --u)
                 mbar_wait(smem_u32(&bar_bfull[u & 1]), (u >> 1) & 1, err);
         }
@@ -308,15 +322,15 @@ __global__ void __launch_bounds__(kQT, 1)
                     break;
                 }
                 for (int a = 0; a < kS && ok; ++a) {
-                    const int q = u * kS + a;
-                    if (!mbar_wait(smem_u32(&bar_full[a]), (q / kS) & 1, err) || abort_sh) {
+                    const int q = u * kS + a, slot = q % kRing;
+                    if (!mbar_wait(smem_u32(&bar_full[slot]), (q / kRing) & 1, err) || abort_sh) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t ad = smem_desc_sw128(aring + a * kTileA + ks * 32);
+                        const uint64_t ad = smem_desc_sw128(aring + slot * kTileA + ks * 32);
 #pragma unroll
                         for (int b = 0; b < kS; ++b) {
                             if (a + b >= kLv) continue;
@@ -326,7 +340,7 @@ __global__ void __launch_bounds__(kQT, 1)
                             written |= 1u << acc;
                         }
                     }
-                    mma_commit(smem_u32(&bar_empty[a]));
+                    mma_commit(smem_u32(&bar_empty[slot]));
                 }
                 if (ok) mma_commit(smem_u32(&bar_bempty[bs]));
             }
@@ -339,7 +353,6 @@ __global__ void __launch_bounds__(kQT, 1)
         // ---- epilogue: warp w drains rows 32 (w % 4).. for reflectors (w / 4) BP/2 .. ----
         constexpr int HC = BP / 2;
         const int q4 = warp & 3, h = warp >> 2, r = 32 * q4 + lane, jj = mt * 128 + r;
-        const int nseg = (nkc + kSegChunks - 1) / kSegChunks;
         const bool bad = !mbar_wait(smem_u32(&bar_acc), 0, err) || abort_sh;
         if (!named_sync_or(1, 256, bad)) {
             tc_fence_after();
@@ -370,7 +383,7 @@ __global__ void __launch_bounds__(kQT, 1)
                 for (int c = 0; c < 8; ++c) {
                     const int m = h * HC + c0 + c;
                     stW[r * WS + m] = fma(__ll2double_rn(hi[c]), 268435456.0, __ll2double_rn(lo[c])) *
-                                      pow2d(ec + eV1[(size_t)gf * kVRows + m] - kUnitShift);
+                                      pow2d(ec + eV_sh[m] - kUnitShift);
                 }
             }
             for (int idx = threadIdx.x; idx < BP * BP; idx += 256) Ssh[idx] = Sall[((size_t)f * N + p) * BP + idx];
@@ -406,7 +419,7 @@ __global__ void __launch_bounds__(kQT, 1)
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 9) tmem_dealloc(tmem, 512);
+    if (warp == 9) tmem_dealloc(tmem, tcols);
 }
 
 // ---- C -= V W' -----------------------------------------------------------------------------
@@ -525,7 +538,7 @@ __global__ void __launch_bounds__(kQT, 1)
     if (warp == 9) tmem_dealloc(tmem, 512);
 }
 
-size_t gemm1_smem(int BP) { return 1024 + 2 * (size_t)kS * BP * 128 + (size_t)kS * kTileA; }
+size_t gemm1_smem(int BP) { return 1024 + 2 * (size_t)kS * BP * 128 + (size_t)kRing * kTileA; }
 size_t gemm2_smem() { return 1024 + (size_t)kS * (kTileA + 64 * 128); }
 
 struct QrtArgs {
@@ -559,7 +572,7 @@ cudaError_t launch_panel(slmc_ctx* c, int nf, int t, cudaStream_t s) {
     const size_t smP = QrSmem<BP>::bytes(a.N);
     cudaError_t e = cudaFuncSetAttribute(k_qrt_panel<BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smP);
     if (e != cudaSuccess) return e;
-    k_qrt_panel<BP><<<nf, kThreads, smP, s>>>(c->Y, c->lnD, c->QR, c->tau, c->perm, c->sgnU, c->Sws, c->err, a.N, t,
+    k_qrt_panel<BP><<<nf, kPT, smP, s>>>(c->Y, c->lnD, c->QR, c->tau, c->perm, c->sgnU, c->Sws, c->err, a.N, t,
                                               c->qt_lnDn, c->qt_ntriv, a.V1, c->qt_eV1, a.V2, c->qt_eV2, a.kpad,
                                               a.mpad, a.plane1, a.plane2, c->fbase);
     return cudaGetLastError();

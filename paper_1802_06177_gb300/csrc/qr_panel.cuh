@@ -227,16 +227,17 @@ __device__ __forceinline__ int k_of(int p, int c) { return p + c; }
 // columns p .. p + nb - 1 of the packed output (Rt above the diagonal, v below), then leaves the clean
 // reflectors V (unit diagonal, zeros above) in Vp and the compact-WY triangle S of the panel in Ssm
 // and in Sall_f. G (BP x BP) is scratch. Rows i < p of the output use the scales s_lnDn / s_g of the
-// earlier panels.
-template <int BP>
+// earlier panels. NT threads (8 or more warps; the arithmetic of every column does not depend on NT).
+template <int BP, int NT = kThreads>
 __device__ __forceinline__ void panel_step(const double* __restrict__ Y, double* __restrict__ QR,
                                            double* __restrict__ tau_f, double* __restrict__ Sall_f, double* Vp,
                                            double* Ssm, double* G, const double* s_lnd, double* s_lnDn, double* s_g,
                                            double* s_tau, double* s_beta, const int* s_perm, int* s_ntriv,
                                            int* s_wide, int N, int p, int nb) {
     constexpr int BPS = BP + 1;
+    constexpr int NW = NT / 32;  // warps of the CTA
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int idx = tid; idx < nb * (N - p); idx += kThreads) {
+    for (int idx = tid; idx < nb * (N - p); idx += NT) {
         const int c = idx / (N - p), rr = idx - c * (N - p);
         Vp[(p + rr) * BPS + c] = Y[(size_t)s_perm[p + c] * N + p + rr];
     }
@@ -256,8 +257,8 @@ __device__ __forceinline__ void panel_step(const double* __restrict__ Y, double*
                 panel_reflector<BP>(Vp, k + 1, c + 1, N, lane, s_tau, s_beta, tau_f, s_ntriv);
             }
         } else if (tau != 0.0) {
-            // columns c0, c0 + 7, ... below nb (warp-uniform count nv <= 5)
-            const int c0 = c + 2 + (warp - 1), cs = kWarps - 1;
+            // columns c0, c0 + NW - 1, ... below nb (warp-uniform count nv <= 5 for NW >= 8)
+            const int c0 = c + 2 + (warp - 1), cs = NW - 1;
             const int nv = (c0 < nb) ? (nb - 1 - c0) / cs + 1 : 0;
             switch (nv) {
                 case 0: break;
@@ -281,7 +282,7 @@ __device__ __forceinline__ void panel_step(const double* __restrict__ Y, double*
     __syncthreads();
     // write logical columns p..p+nb-1 of the packed output (Rt above, v below)
     const bool wide = *s_wide != 0;
-    for (int c = warp; c < nb; c += kWarps) {
+    for (int c = warp; c < nb; c += NW) {
         const int k = p + c;
         const int pc = s_perm[k];
         const double lk = s_lnd[pc];
@@ -301,7 +302,7 @@ __device__ __forceinline__ void panel_step(const double* __restrict__ Y, double*
     }
     __syncthreads();
     // clean V (unit diagonal, zeros above) and the Gram matrix G = V^T V
-    for (int idx = tid; idx < nb * nb; idx += kThreads) {
+    for (int idx = tid; idx < nb * nb; idx += NT) {
         const int a = idx / nb, c = idx - a * nb;  // Vp row p+a, column c
         if (a < c) Vp[(p + a) * BPS + c] = 0.0;
         else if (a == c) Vp[(p + a) * BPS + c] = 1.0;
@@ -309,7 +310,7 @@ __device__ __forceinline__ void panel_step(const double* __restrict__ Y, double*
     __syncthreads();
         {   // G[a][c] = v_a . v_c for a < c; each warp interleaves four pairs (independent chains)
         const int npairs = nb * (nb - 1) / 2;
-        for (int q0 = warp * 4; q0 < npairs; q0 += kWarps * 4) {
+        for (int q0 = warp * 4; q0 < npairs; q0 += NW * 4) {
             int pa[4], pc[4];
             double d[4];
 #pragma unroll
@@ -362,7 +363,7 @@ __device__ __forceinline__ void panel_step(const double* __restrict__ Y, double*
         }
     }
     __syncthreads();
-    for (int idx = tid; idx < nb * BP; idx += kThreads) {
+    for (int idx = tid; idx < nb * BP; idx += NT) {
         const int a = idx / BP, b = idx - a * BP;
         Sall_f[(size_t)(p + a) * BP + b] = (b < nb) ? Ssm[a * BP + b] : 0.0;
     }
