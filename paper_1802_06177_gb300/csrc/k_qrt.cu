@@ -24,7 +24,7 @@
 //   k_qrt_slice_C    slice the trailing columns of C (rows p..N-1), one exponent per column;
 //   k_qrt_gemm1<BP>  W^T = C^T V on the tensor cores (M = trailing columns, N = BP, K = rows), then
 //                    W'^T = W^T S and its slices, one exponent per trailing column;
-//   k_qrt_gemm2<BP>  C -= V W' on the tensor cores (M = rows, N = trailing columns, K = BP), the
+//   k_qrt_gemm2<BP>  C -= V W' on the tensor cores (M = rows, N = 32 trailing columns, K = BP), the
 //                    FP64 read-modify-write of C in the epilogue.
 // Outputs are those of k_qrb (packed QR, tau, perm, new ln D, sgnU, the panels' S). All waits are
 // clock-bounded and set SLMC_EBIT_TIMEOUT; a CTA that gives up drains its copies and frees its
@@ -423,42 +423,49 @@ __global__ void __launch_bounds__(kQT, 2)
 }
 
 // ---- C -= V W' -----------------------------------------------------------------------------
-// CTA = 128 rows (row tile p/128 + blockIdx.y) x 64 trailing columns of one field; one K chunk
-// (BP reflectors) of seven V slices and seven W' slices.
+// CTA = 128 rows (row tile p/128 + blockIdx.y) x kNC trailing columns of one field; one K chunk (BP
+// reflectors): the seven W' slices resident, the seven V slices streamed through the 3-tile ring.
+// 32 columns keep the accumulators at 7 x 32 tensor-memory columns, so two CTAs share an SM.
+constexpr int kNC = 32;
+
 template <int BP>
-__global__ void __launch_bounds__(kQT, 1)
+__global__ void __launch_bounds__(kQT, 2)
     k_qrt_gemm2(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmW,
                 const int* __restrict__ eV2, const int* __restrict__ eW, const int* __restrict__ perm_all,
                 double* __restrict__ Yall, int N, int p, int j0, int n_t, int mpad, int wpad, int fbase,
                 unsigned int* __restrict__ err) {
-    constexpr uint32_t kTileW = 64 * 128;
-    constexpr uint32_t kIdesc = idesc_f32acc(1, 128, 64);
+    constexpr uint32_t kTileW = kNC * 128;
+    constexpr uint32_t kIdesc = idesc_f32acc(1, 128, kNC);
     const int nt = blockIdx.x, mt = p / 128 + blockIdx.y, f = blockIdx.z, gf = fbase + f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar_full, bar_acc, bar_done;
+    __shared__ __align__(8) uint64_t bar_full[kRing], bar_empty[kRing], bar_bfull, bar_acc, bar_done;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
-    __shared__ int eW_sh[64];
-    __shared__ int col_sh[64];
+    __shared__ int eW_sh[kNC];
+    __shared__ int col_sh[kNC];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const uint32_t abuf = base, bbuf = base + kS * kTileA;
+    const uint32_t bbuf = base, aring = base + kS * kTileW;
 
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&bar_full), 1);
+        for (int q = 0; q < kRing; ++q) {
+            mbar_init(smem_u32(&bar_full[q]), 1);
+            mbar_init(smem_u32(&bar_empty[q]), 1);
+        }
+        mbar_init(smem_u32(&bar_bfull), 1);
         mbar_init(smem_u32(&bar_acc), 1);
         mbar_init(smem_u32(&bar_done), 1);
         abort_sh = 0;
         fence_barrier_init();
     }
-    if (threadIdx.x < 64) {
-        const int jj = nt * 64 + threadIdx.x;
+    if (threadIdx.x < kNC) {
+        const int jj = nt * kNC + threadIdx.x;
         eW_sh[threadIdx.x] = jj < n_t ? eW[(size_t)gf * wpad + jj] : 0;
         col_sh[threadIdx.x] = jj < n_t ? perm_all[(size_t)f * N + j0 + jj] : 0;
     }
     if (warp == 9) {
-        tmem_alloc(smem_u32(&tmem_base_sh), 512);
+        tmem_alloc(smem_u32(&tmem_base_sh), 256);
         tc_fence_before();
     }
     __syncthreads();
@@ -467,40 +474,56 @@ __global__ void __launch_bounds__(kQT, 1)
 
     if (warp == 8) {
         if (lane == 0) {
-            const uint32_t fb = smem_u32(&bar_full);
-            mbar_expect_tx(fb, kS * (kTileA + kTileW));
-            for (int a = 0; a < kS; ++a) tma_load_3d(abuf + a * kTileA, &tmV, 0, gf * mpad + mt * 128, a, fb);
-            for (int b = 0; b < kS; ++b) tma_load_3d(bbuf + b * kTileW, &tmW, 0, gf * wpad + nt * 64, b, fb);
-            mbar_wait(fb, 0, err);  // (bounded) the copies have landed before the CTA can exit
+            const uint32_t bb = smem_u32(&bar_bfull);
+            mbar_expect_tx(bb, kS * kTileW);
+            for (int b = 0; b < kS; ++b) tma_load_3d(bbuf + b * kTileW, &tmW, 0, gf * wpad + nt * kNC, b, bb);
+            int issued = 0;
+            for (int a = 0; a < kS; ++a) {
+                const int slot = a % kRing;
+                if (a >= kRing && !mbar_wait(smem_u32(&bar_empty[slot]), ((a / kRing) - 1) & 1, err)) break;
+                const uint32_t fb = smem_u32(&bar_full[slot]);
+                mbar_expect_tx(fb, kTileA);
+                tma_load_3d(aring + slot * kTileA, &tmV, 0, gf * mpad + mt * 128, a, fb);
+                issued = a + 1;
+            }
+            // (bounded) the copies have landed before the CTA can exit
+            mbar_wait(bb, 0, err);
+            for (int a = issued - 1; a >= 0 && a >= issued - kRing; --a)
+                mbar_wait(smem_u32(&bar_full[a % kRing]), (a / kRing) & 1, err);
         }
     } else if (warp == 9) {
         if (lane == 0) {
-            if (mbar_wait(smem_u32(&bar_full), 0, err)) {
+            bool ok = mbar_wait(smem_u32(&bar_bfull), 0, err);
+            uint32_t written = 0;
+            for (int a = 0; a < kS && ok; ++a) {
+                const int slot = a % kRing;
+                if (!mbar_wait(smem_u32(&bar_full[slot]), (a / kRing) & 1, err)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
-                uint32_t written = 0;
 #pragma unroll
-                for (int ks = 0; ks < BP / 16; ++ks)
+                for (int ks = 0; ks < BP / 16; ++ks) {
+                    const uint64_t ad = smem_desc_sw128(aring + slot * kTileA + ks * 32);
 #pragma unroll
-                    for (int a = 0; a < kS; ++a) {
-                        const uint64_t ad = smem_desc_sw128(abuf + a * kTileA + ks * 32);
-#pragma unroll
-                        for (int b = 0; b < kS; ++b) {
-                            if (a + b >= kLv) continue;
-                            const int lv = a + b;
-                            const uint64_t bd = smem_desc_sw128(bbuf + b * kTileW + ks * 32);
-                            mma_bf16(tmem + (uint32_t)(lv * 64), ad, bd, kIdesc, (written >> lv) & 1u);
-                            written |= 1u << lv;
-                        }
+                    for (int b = 0; b < kS; ++b) {
+                        if (a + b >= kLv) continue;
+                        const int lv = a + b;
+                        const uint64_t bd = smem_desc_sw128(bbuf + b * kTileW + ks * 32);
+                        mma_bf16(tmem + (uint32_t)(lv * kNC), ad, bd, kIdesc, (written >> lv) & 1u);
+                        written |= 1u << lv;
                     }
-                mma_commit(smem_u32(&bar_acc));
-            } else {
-                abort_sh = 1;
+                }
+                mma_commit(smem_u32(&bar_empty[slot]));
             }
+            if (ok) mma_commit(smem_u32(&bar_acc));
+            else abort_sh = 1;
             mma_commit(smem_u32(&bar_done));
             mbar_wait(smem_u32(&bar_done), 0, err);
         }
     } else {
-        // ---- epilogue: warp w: rows 32 (w % 4).. of the tile, columns 32 (w / 4)..; C -= V W' ----
+        // ---- epilogue: warp w: rows 32 (w % 4).. of the tile, columns 16 (w / 4)..; C -= V W' ----
+        constexpr int HC = kNC / 2;
         const int q4 = warp & 3, h = warp >> 2, r = mt * 128 + 32 * q4 + lane;
         const bool bad = !mbar_wait(smem_u32(&bar_acc), 0, err) || abort_sh;
         if (!named_sync_or(1, 256, bad)) {
@@ -509,15 +532,15 @@ __global__ void __launch_bounds__(kQT, 1)
             const int ev = row_ok ? eV2[(size_t)gf * mpad + r] : 0;
             double* Yf = Yall + (size_t)f * N * N;
 #pragma unroll
-            for (int c0 = 0; c0 < 32; c0 += 8) {
+            for (int c0 = 0; c0 < HC; c0 += 8) {
                 uint32_t v[kLv][8];
-                const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(32 * h + c0);
+                const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(HC * h + c0);
 #pragma unroll
-                for (int lv = 0; lv < kLv; ++lv) tmem_ld8(tl + (uint32_t)(lv * 64), v[lv]);
+                for (int lv = 0; lv < kLv; ++lv) tmem_ld8(tl + (uint32_t)(lv * kNC), v[lv]);
                 tmem_ld_wait();
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const int cc = 32 * h + c0 + c, jj = nt * 64 + cc;
+                    const int cc = HC * h + c0 + c, jj = nt * kNC + cc;
                     if (!row_ok || jj >= n_t) continue;
                     uint32_t w[kLv];
 #pragma unroll
@@ -535,11 +558,11 @@ __global__ void __launch_bounds__(kQT, 1)
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 9) tmem_dealloc(tmem, 512);
+    if (warp == 9) tmem_dealloc(tmem, 256);
 }
 
 size_t gemm1_smem(int BP) { return 1024 + 2 * (size_t)kS * BP * 128 + (size_t)kRing * kTileA; }
-size_t gemm2_smem() { return 1024 + (size_t)kS * (kTileA + 64 * 128); }
+size_t gemm2_smem() { return 1024 + (size_t)kS * kNC * 128 + (size_t)kRing * kTileA; }
 
 struct QrtArgs {
     int N, kpad, mpad, wpad, jpad;
@@ -593,7 +616,7 @@ cudaError_t launch_trailing(slmc_ctx* c, int nf, int t, cudaStream_t s) {
     k_qrt_gemm1<BP><<<dim3((n_t + 127) / 128, nf), kQT, sm1, s>>>(c->qt_mapC, mapV1, c->qt_eC, c->qt_eV1, c->Sws, a.Ws,
                                                                   c->qt_eW, N, p, n_t, a.kpad, a.jpad, a.wpad, a.planeW,
                                                                   c->fbase, c->err);
-    k_qrt_gemm2<BP><<<dim3((n_t + 63) / 64, a.mpad / 128 - p / 128, nf), kQT, sm2, s>>>(
+    k_qrt_gemm2<BP><<<dim3((n_t + kNC - 1) / kNC, a.mpad / 128 - p / 128, nf), kQT, sm2, s>>>(
         c->qt_mapV2, c->qt_mapW, c->qt_eV2, c->qt_eW, c->perm, c->Y, N, p, j0, n_t, a.mpad, a.wpad, c->fbase, c->err);
     return cudaGetLastError();
 }
@@ -643,7 +666,7 @@ cudaError_t qrt_init(slmc_ctx* c, void* bf16_base, int* int_base) {
         !make_map_sw128(&c->qt_mapV1_32, c->qt_V1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, kpad, F * kVRows, kS, 32) ||
         !make_map_sw128(&c->qt_mapV1_16, c->qt_V1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, kpad, F * kVRows, kS, 16) ||
         !make_map_sw128(&c->qt_mapV2, c->qt_V2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 64, F * mpad, kS, 128) ||
-        !make_map_sw128(&c->qt_mapW, c->qt_W, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 64, F * wpad, kS, 64))
+        !make_map_sw128(&c->qt_mapW, c->qt_W, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 64, F * wpad, kS, kNC))
         return cudaErrorInvalidValue;
     return cudaSuccess;
 }
