@@ -218,7 +218,8 @@ slmc_ctx make_view(slmc_ctx* c, int f0) {
     v.qt_mpad = c->qt_mpad;
     v.qt_wpad = c->qt_wpad;
     v.qr_path = c->qr_path;
-    v.qt_mapC = c->qt_mapC;
+    v.qt_mapC96 = c->qt_mapC96;
+    v.qt_mapC112 = c->qt_mapC112;
     v.qt_mapV1_16 = c->qt_mapV1_16;
     v.qt_mapV1_32 = c->qt_mapV1_32;
     v.qt_mapV2 = c->qt_mapV2;

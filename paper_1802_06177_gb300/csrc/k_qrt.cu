@@ -155,8 +155,9 @@ __global__ void __launch_bounds__(kPT, 2)
         if (fabs(s_lnd[k]) > 600.0) s_wide = 1;
     __syncthreads();
 
+    // the Gram matrix and S of every panel but the last are formed on the tensor cores (k_qrt_gemm1)
     panel_step<BP, kPT>(Y, QR, tau_all + (size_t)f * N, Sall + (size_t)f * N * BP, Vp, Ssm, Wsm, s_lnd, s_lnDn, s_g, s_tau,
-                   s_beta, s_perm, &s_ntriv, &s_wide, N, p, nb);
+                        s_beta, s_perm, &s_ntriv, &s_wide, N, p, nb, t == npanels - 1);
     __syncthreads();
     if (tid < nb) lnDn_ws[(size_t)gf * N + p + tid] = s_lnDn[p + tid];
     if (tid == 0) {  // reflectors with tau != 0 so far (their parity is the sign of det U)
@@ -225,20 +226,25 @@ __global__ void __launch_bounds__(256) k_qrt_slice_C(const double* __restrict__ 
     }
 }
 
-// ---- W^T = C^T V, then W'^T = W^T S and its slices ------------------------------------------
-// CTA = 128 trailing columns of one field. TMA streams per 64-row K chunk the seven C slices
-// through a 7-tile ring and the seven V slices double-buffered; products (a, b), a + b <= 6, go to
+// ---- [G; W^T] = [V C]^T V, S from G, then W'^T = W^T S and its slices -----------------------
+// CTA = the BP reflectors plus 128 - BP trailing columns of one field: each 128-row A tile holds the
+// slices of V's columns (rows 0..BP-1, from the reflector slice buffer) above those of the CTA's
+// trailing columns of C, so the product's first BP rows are the panel's Gram matrix G = V^T V. The
+// epilogue forms the compact-WY triangle S from G (the panel kernel no longer does; CTA 0 writes it
+// out for the formation of Q), then W' = S^T W. TMA streams per 64-row K chunk the seven A slices
+// through a 3-tile ring and the seven V slices double-buffered; products (a, b), a + b <= 6, go to
 // the accumulator of level a + b of the chunk's segment (seven chunks per segment).
 template <int BP>
 __global__ void __launch_bounds__(kQT, 2)
     k_qrt_gemm1(const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmV,
-                const int* __restrict__ eC, const int* __restrict__ eV1, const double* __restrict__ Sall,
-                __nv_bfloat16* __restrict__ Ws, int* __restrict__ eW, int N, int p, int n_t, int kpad, int jpad,
-                int wpad, size_t planeW, int fbase, unsigned int* __restrict__ err) {
+                const int* __restrict__ eC, const int* __restrict__ eV1, const double* __restrict__ tau_all,
+                double* __restrict__ Sall, __nv_bfloat16* __restrict__ Ws, int* __restrict__ eW, int N, int p,
+                int n_t, int kpad, int jpad, int wpad, size_t planeW, int fbase, unsigned int* __restrict__ err) {
     constexpr uint32_t kTileB = BP * 128;
     constexpr uint32_t kChunkB = kS * kTileB;
     constexpr uint32_t kIdesc = idesc_f32acc(1, 128, BP);
     constexpr int WS = BP + 1;
+    constexpr int kMC = 128 - BP;  // trailing columns per CTA
     const int mt = blockIdx.x, f = blockIdx.y, gf = fbase + f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kc0 = p / 64, nkc = kpad / 64 - kc0;
@@ -247,10 +253,11 @@ __global__ void __launch_bounds__(kQT, 2)
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
     __shared__ int eV_sh[BP];
+    __shared__ double tau_sh[BP];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t bbuf = base, aring = base + 2 * kChunkB;
-    // after the MMAs: stage of W [128][WS], W' [128][WS] and S [BP][BP] over the B buffers and the ring
+    // after the MMAs: stage of [G; W] [128][WS], W' [128][WS] and S [BP][BP] over the B buffers and the ring
     double* stW = reinterpret_cast<double*>(smem_raw + (bbuf - raw));
     double* stWp = stW + 128 * WS;
     double* Ssh = stWp + 128 * WS;
@@ -269,7 +276,10 @@ __global__ void __launch_bounds__(kQT, 2)
         abort_sh = 0;
         fence_barrier_init();
     }
-    if (threadIdx.x < BP) eV_sh[threadIdx.x] = eV1[(size_t)gf * kVRows + threadIdx.x];
+    if (threadIdx.x < BP) {
+        eV_sh[threadIdx.x] = eV1[(size_t)gf * kVRows + threadIdx.x];
+        tau_sh[threadIdx.x] = tau_all[(size_t)f * N + p + threadIdx.x];
+    }
     const int nseg = (nkc + kSegChunks - 1) / kSegChunks;
     const uint32_t tcols = nseg == 1 ? 256u : 512u;  // 7 levels x BP columns per accumulator set
     if (warp == 9) {
@@ -300,8 +310,9 @@ __global__ void __launch_bounds__(kQT, 2)
                         break;
                     }
                     const uint32_t fb = smem_u32(&bar_full[slot]);
-                    mbar_expect_tx(fb, kTileA);
-                    tma_load_3d(aring + slot * kTileA, &tmC, kc * 64, gf * jpad + mt * 128, a, fb);
+                    mbar_expect_tx(fb, kTileA);  // BP rows of V + kMC rows of C
+                    tma_load_3d(aring + slot * kTileA, &tmV, kc * 64, gf * kVRows, a, fb);
+                    tma_load_3d(aring + slot * kTileA + kTileB, &tmC, kc * 64, gf * jpad + mt * kMC, a, fb);
                     issued_a = q + 1;
                 }
                 if (abort_sh) break;
@@ -351,12 +362,14 @@ __global__ void __launch_bounds__(kQT, 2)
         }
     } else {
         // ---- epilogue: warp w drains rows 32 (w % 4).. for reflectors (w / 4) BP/2 .. ----
+        // row r < BP: G[r][.] (exponents of the reflectors); row r >= BP: W of trailing column
+        // jj = mt kMC + r - BP
         constexpr int HC = BP / 2;
-        const int q4 = warp & 3, h = warp >> 2, r = 32 * q4 + lane, jj = mt * 128 + r;
+        const int q4 = warp & 3, h = warp >> 2, r = 32 * q4 + lane, jj = mt * kMC + r - BP;
         const bool bad = !mbar_wait(smem_u32(&bar_acc), 0, err) || abort_sh;
         if (!named_sync_or(1, 256, bad)) {
             tc_fence_after();
-            const int ec = jj < n_t ? eC[(size_t)gf * jpad + jj] : 0;
+            const int er = r < BP ? eV_sh[r] : (jj < n_t ? eC[(size_t)gf * jpad + jj] : 0);
 #pragma unroll
             for (int c0 = 0; c0 < HC; c0 += 8) {
                 long long hi[8], lo[8];
@@ -383,24 +396,31 @@ __global__ void __launch_bounds__(kQT, 2)
                 for (int c = 0; c < 8; ++c) {
                     const int m = h * HC + c0 + c;
                     stW[r * WS + m] = fma(__ll2double_rn(hi[c]), 268435456.0, __ll2double_rn(lo[c])) *
-                                      pow2d(ec + eV_sh[m] - kUnitShift);
+                                      pow2d(er + eV_sh[m] - kUnitShift);
                 }
             }
-            for (int idx = threadIdx.x; idx < BP * BP; idx += 256) Ssh[idx] = Sall[((size_t)f * N + p) * BP + idx];
         }
         named_sync(1, 256);
         if (!bad) {
-            // W'[m] = sum_{q <= m} S[q][m] W[q]  (S upper triangular); thread (row, half)
-            const int rr = threadIdx.x & 127, hh = threadIdx.x >> 7;
-            for (int m = hh * HC; m < hh * HC + HC; ++m) {
-                double a = 0.0;
-                for (int q = 0; q <= m; ++q) a = fma(Ssh[q * BP + m], stW[rr * WS + q], a);
-                stWp[rr * WS + m] = a;
-            }
+            if (warp == 0) wy_triangle<BP>(stW, WS, tau_sh, Ssh, BP, lane);  // S from G = rows 0..BP-1
         }
         named_sync(1, 256);
-        if (!bad && threadIdx.x < 128) {
-            const int rr = threadIdx.x, j2 = mt * 128 + rr;
+        if (!bad) {
+            if (mt == 0)  // S of the panel for the formation of Q
+                for (int idx = threadIdx.x; idx < BP * BP; idx += 256)
+                    Sall[((size_t)f * N + p) * BP + idx] = Ssh[idx];
+            // W'[m] = sum_{q <= m} S[q][m] W[q]  (S upper triangular); thread (row, half)
+            const int rr = BP + (threadIdx.x & 127) % kMC, hh = threadIdx.x >> 7;
+            if ((threadIdx.x & 127) < kMC)
+                for (int m = hh * HC; m < hh * HC + HC; ++m) {
+                    double a = 0.0;
+                    for (int q = 0; q <= m; ++q) a = fma(Ssh[q * BP + m], stW[rr * WS + q], a);
+                    stWp[rr * WS + m] = a;
+                }
+        }
+        named_sync(1, 256);
+        if (!bad && threadIdx.x < kMC) {
+            const int rr = BP + threadIdx.x, j2 = mt * kMC + threadIdx.x;
             if (j2 < n_t) {
                 long long mx = 0;
                 for (int m = 0; m < BP; ++m) mx = max(mx, abs_bits(stWp[rr * WS + m]));
@@ -613,9 +633,10 @@ cudaError_t launch_trailing(slmc_ctx* c, int nf, int t, cudaStream_t s) {
     const int N = a.N, p = t * BP, j0 = p + BP, n_t = N - j0;
     k_qrt_slice_C<<<dim3((n_t + 7) / 8, nf), 256, 0, s>>>(c->Y, c->perm, a.Cs, c->qt_eC, N, p, j0, a.kpad, a.jpad,
                                                           a.planeC, c->fbase);
-    k_qrt_gemm1<BP><<<dim3((n_t + 127) / 128, nf), kQT, sm1, s>>>(c->qt_mapC, mapV1, c->qt_eC, c->qt_eV1, c->Sws, a.Ws,
-                                                                  c->qt_eW, N, p, n_t, a.kpad, a.jpad, a.wpad, a.planeW,
-                                                                  c->fbase, c->err);
+    const CUtensorMap& mapC = BP == 32 ? c->qt_mapC96 : c->qt_mapC112;
+    k_qrt_gemm1<BP><<<dim3((n_t + 127 - BP) / (128 - BP), nf), kQT, sm1, s>>>(
+        mapC, mapV1, c->qt_eC, c->qt_eV1, c->tau, c->Sws, a.Ws, c->qt_eW, N, p, n_t, a.kpad, a.jpad, a.wpad, a.planeW,
+        c->fbase, c->err);
     k_qrt_gemm2<BP><<<dim3((n_t + kNC - 1) / kNC, a.mpad / 128 - p / 128, nf), kQT, sm2, s>>>(
         c->qt_mapV2, c->qt_mapW, c->qt_eV2, c->qt_eW, c->perm, c->Y, N, p, j0, n_t, a.mpad, a.wpad, c->fbase, c->err);
     return cudaGetLastError();
@@ -662,7 +683,8 @@ cudaError_t qrt_init(slmc_ctx* c, void* bf16_base, int* int_base) {
     cudaError_t e = cudaMemset(bf16_base, 0, nb16 * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMemset(int_base, 0, nint * sizeof(int));
     if (e != cudaSuccess) return e;
-    if (!make_map_sw128(&c->qt_mapC, c->qt_C, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, kpad, F * mpad, kS, 128) ||
+    if (!make_map_sw128(&c->qt_mapC96, c->qt_C, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, kpad, F * mpad, kS, 96) ||
+        !make_map_sw128(&c->qt_mapC112, c->qt_C, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, kpad, F * mpad, kS, 112) ||
         !make_map_sw128(&c->qt_mapV1_32, c->qt_V1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, kpad, F * kVRows, kS, 32) ||
         !make_map_sw128(&c->qt_mapV1_16, c->qt_V1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, kpad, F * kVRows, kS, 16) ||
         !make_map_sw128(&c->qt_mapV2, c->qt_V2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 64, F * mpad, kS, 128) ||

@@ -221,6 +221,38 @@ __device__ __forceinline__ void panel_apply(double* __restrict__ Vp, int k, int 
 
 __device__ __forceinline__ int k_of(int p, int c) { return p + c; }
 
+// Compact-WY triangle of a panel of nb reflectors, by one warp (lane = row): S_cc = tau_c,
+// S[0:c, c] = -tau_c S[0:c, 0:c] G[0:c, c], from the strictly upper part of the Gram matrix
+// G = V^T V (row stride ldg). S (BP x BP, row-major) is zero below the diagonal and beyond nb.
+template <int BP>
+__device__ __forceinline__ void wy_triangle(const double* G, int ldg, const double* tau, double* Ssm, int nb,
+                                            int lane) {
+    for (int c = 0; c < nb; ++c) {
+        const double tc = tau[c];
+        double v = 0.0;
+        if (lane < c) {  // four independent partial sums (short dependency chains)
+            double v4[4] = {0.0, 0.0, 0.0, 0.0};
+            int q = lane;
+            for (; q + 4 <= c; q += 4) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * ldg + c], v4[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (q + j < c) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * ldg + c], v4[j]);
+            v = -tc * ((v4[0] + v4[1]) + (v4[2] + v4[3]));
+        } else if (lane == c) {
+            v = tc;
+        }
+        if (lane < BP) Ssm[lane * BP + c] = (lane <= c) ? v : 0.0;
+        __syncwarp();
+    }
+    for (int c = nb; c < BP; ++c) {
+        if (lane < BP) Ssm[lane * BP + c] = 0.0;
+    }
+    __syncwarp();
+}
+
 // Factors panel t (logical columns p .. p + nb - 1, already updated by the earlier panels) of one
 // field by one CTA: loads it from Y in pre-pivoted order, forms its Householder reflectors in shared
 // memory (tau), the new scales ln D'_k = ln|beta_k| + ln D_{perm(k)} of its rows, writes logical
@@ -228,12 +260,13 @@ __device__ __forceinline__ int k_of(int p, int c) { return p + c; }
 // reflectors V (unit diagonal, zeros above) in Vp and the compact-WY triangle S of the panel in Ssm
 // and in Sall_f. G (BP x BP) is scratch. Rows i < p of the output use the scales s_lnDn / s_g of the
 // earlier panels. NT threads (8 or more warps; the arithmetic of every column does not depend on NT).
+// want_wy = false stops after V is clean: no Gram matrix, no S (the caller forms them).
 template <int BP, int NT = kThreads>
 __device__ __forceinline__ void panel_step(const double* __restrict__ Y, double* __restrict__ QR,
                                            double* __restrict__ tau_f, double* __restrict__ Sall_f, double* Vp,
                                            double* Ssm, double* G, const double* s_lnd, double* s_lnDn, double* s_g,
                                            double* s_tau, double* s_beta, const int* s_perm, int* s_ntriv,
-                                           int* s_wide, int N, int p, int nb) {
+                                           int* s_wide, int N, int p, int nb, bool want_wy = true) {
     constexpr int BPS = BP + 1;
     constexpr int NW = NT / 32;  // warps of the CTA
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -308,7 +341,8 @@ __device__ __forceinline__ void panel_step(const double* __restrict__ Y, double*
         else if (a == c) Vp[(p + a) * BPS + c] = 1.0;
     }
     __syncthreads();
-        {   // G[a][c] = v_a . v_c for a < c; each warp interleaves four pairs (independent chains)
+    if (!want_wy) return;  // the Gram matrix and S are formed elsewhere
+    {   // G[a][c] = v_a . v_c for a < c; each warp interleaves four pairs (independent chains)
         const int npairs = nb * (nb - 1) / 2;
         for (int q0 = warp * 4; q0 < npairs; q0 += NW * 4) {
             int pa[4], pc[4];
@@ -339,29 +373,7 @@ __device__ __forceinline__ void panel_step(const double* __restrict__ Y, double*
         }
     }
     __syncthreads();
-    // S: S_cc = tau_c, S[0:c, c] = -tau_c S[0:c, 0:c] G[0:c, c]  (one warp, lane = row)
-    if (warp == 0) {
-        for (int c = 0; c < nb; ++c) {
-            const double tc = s_tau[c];
-            double v = 0.0;
-            if (lane < c) {  // four independent partial sums (short dependency chains)
-                double v4[4] = {0.0, 0.0, 0.0, 0.0};
-                int q = lane;
-                for (; q + 4 <= c; q += 4) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * BP + c], v4[j]);
-                }
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    if (q + j < c) v4[j] = fma(Ssm[lane * BP + q + j], G[(q + j) * BP + c], v4[j]);
-                v = -tc * ((v4[0] + v4[1]) + (v4[2] + v4[3]));
-            } else if (lane == c) {
-                v = tc;
-            }
-            if (lane < BP) Ssm[lane * BP + c] = (lane <= c) ? v : 0.0;
-            __syncwarp();
-        }
-    }
+    if (warp == 0) wy_triangle<BP>(G, BP, s_tau, Ssm, nb, lane);
     __syncthreads();
     for (int idx = tid; idx < nb * BP; idx += NT) {
         const int a = idx / BP, b = idx - a * BP;

@@ -103,7 +103,7 @@ struct slmc_ctx {
     int* qt_ntriv;
     double* qt_lnDn;
     int qt_kpad, qt_mpad, qt_wpad, qr_path;
-    CUtensorMap qt_mapC, qt_mapV1_16, qt_mapV1_32, qt_mapV2, qt_mapW;
+    CUtensorMap qt_mapC96, qt_mapC112, qt_mapV1_16, qt_mapV1_32, qt_mapV2, qt_mapW;
     int fbase;  // first field of this context's workspace within the owner's (views of sub-batches)
     // Split-TF32 slice path (SLMC_PREC_TF32X3): operand pieces of F and of the running slice
     // product (ping/pong), FP32 copies of it, and their TMA descriptors.
