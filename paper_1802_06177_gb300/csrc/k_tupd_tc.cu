@@ -19,10 +19,11 @@
 //
 // Kernels: k_tt_slice_B (columns of T_old gathered by the pivots, sliced per column, written
 // K-major, and the tiles' flags cleared), k_tt_slice_A (rows of Rt sliced per row, the bound
-// checked per row), k_tt_gemm (one CTA per 128 rows x 64 columns of one field: TMA streams the
-// seven A slices of each 64-wide K chunk through a 7-tile ring and the seven B slices double-buffered,
+// checked per row), k_tt_gemm (one CTA per 128 rows x 32 columns of one field: TMA streams the
+// seven A slices of each 64-wide K chunk through a 3-tile ring and the seven B slices double-buffered,
 // one thread issues the MMAs, eight warps drain the accumulators, stage the tile in shared memory
-// and write T_new row-major with coalesced stores). Row-tile mt starts its K loop at row 128 mt
+// and write T_new row-major with coalesced stores; 32 columns per CTA keep the accumulators at
+// 7 x 32 tensor-memory columns and the shared memory near 105 KB, so two CTAs share an SM). Row-tile mt starts its K loop at row 128 mt
 // (Rt is zero to the left of its diagonal). All waits are clock-bounded as in the other
 // tensor-core kernels.
 #include <cuda_bf16.h>
@@ -42,12 +43,13 @@ using slmc::s7::warp_max_bits;
 
 constexpr int kW = 7;
 constexpr int kLevels = 7;   // a + b = 0..6
-constexpr int kNT = 64;      // columns per CTA
+constexpr int kNT = 32;      // columns per CTA (7 x 32 accumulator columns: two CTAs per SM)
 constexpr int kThreads = 320;
 constexpr uint32_t kATile = 128 * 128;  // 128 rows x 64 BF16
-constexpr uint32_t kBTile = kNT * 128;  // 64 rows (columns of T) x 64 BF16
+constexpr uint32_t kBTile = kNT * 128;  // 32 rows (columns of T) x 64 BF16
 constexpr uint32_t kBChunk = kS * kBTile;
-constexpr uint32_t kTmemCols = 512;     // 7 x 64 = 448 used
+constexpr uint32_t kTmemCols = 256;     // 7 x 32 = 224 used
+constexpr int kRingA = 3;               // A slices in flight (tile a is released after its products)
 constexpr uint32_t kIdesc = idesc_f32acc(1, 128, kNT);
 
 __device__ __forceinline__ int warp_sum_int(int v) {
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256) k_tt_slice_A(const double* __restrict__ Q
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_tt_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const int* __restrict__ eA, const int* __restrict__ eB, const int* __restrict__ flag,
               const double* __restrict__ QRall, const double* __restrict__ Told, const int* __restrict__ perm_all,
@@ -147,18 +149,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = npad / 64, kc0 = (mt * 128) / 64, nkc = nk - kc0;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar_full[kS], bar_empty[kS], bar_bfull[2], bar_bempty[2], bar_acc, bar_done;
+    __shared__ __align__(8) uint64_t bar_full[kRingA], bar_empty[kRingA], bar_bfull[2], bar_bempty[2], bar_acc, bar_done;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
     __shared__ int eB_sh[kNT];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t bbuf = base, aring = base + 2 * kBChunk;
-    double* stage_out = reinterpret_cast<double*>(smem_raw + (aring - raw));  // [128][kNT + 1] after the MMAs
+    double* stage_out = reinterpret_cast<double*>(smem_raw + (bbuf - raw));  // [128][kNT + 1] after the MMAs
     const bool fallback = force_fallback || flag[(size_t)(fbase + f) * MT + mt] != 0;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kS; ++s) {
+        for (int s = 0; s < kRingA; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
@@ -181,26 +183,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = tmem_base_sh;
 
     if (fallback) {
-        // Plain FP64 loop for this tile: thread (row r, column half h) accumulates 32 columns.
+        // Plain FP64 loop for this tile: thread (row r, column half h) accumulates kNT / 2 columns.
+        constexpr int HC = kNT / 2;
         if (warp < 8) {
             const int r = threadIdx.x & 127, h = threadIdx.x >> 7, i = mt * 128 + r;
             const double* QR = QRall + (size_t)f * N * N;
             const double* T = Told + (size_t)f * N * N;
             const int* perm = perm_all + (size_t)f * N;
-            double acc[32];
+            double acc[HC];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+            for (int c = 0; c < HC; ++c) acc[c] = 0.0;
             for (int k = mt * 128; k < N; ++k) {
                 const double a = (i < N && k >= i) ? QR[(size_t)k * N + i] : 0.0;
-                const double* trow = T + (size_t)perm[k] * N + j0 + 32 * h;
+                const double* trow = T + (size_t)perm[k] * N + j0 + HC * h;
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    if (j0 + 32 * h + c < N) acc[c] = fma(a, trow[c], acc[c]);
+                for (int c = 0; c < HC; ++c)
+                    if (j0 + HC * h + c < N) acc[c] = fma(a, trow[c], acc[c]);
             }
             if (i < N)
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    if (j0 + 32 * h + c < N) Tnew[((size_t)f * N + i) * N + j0 + 32 * h + c] = acc[c];
+                for (int c = 0; c < HC; ++c)
+                    if (j0 + HC * h + c < N) Tnew[((size_t)f * N + i) * N + j0 + HC * h + c] = acc[c];
         }
     } else if (warp == 8) {
         // ---- TMA producer: per K chunk the six B slices, then the six A slices ----
@@ -218,20 +221,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tma_load_3d(bbuf + bs * kBChunk + b * kBTile, &tmB, kc * 64, (fbase + f) * npad + j0, b, bb);
                 issued_b = u + 1;
                 for (int a = 0; a < kS; ++a) {
-                    const int t = u * kS + a;
-                    if (t >= kS && !mbar_wait(smem_u32(&bar_empty[a]), ((t / kS) - 1) & 1, err)) {
+                    const int t = u * kS + a, slot = t % kRingA;
+                    if (t >= kRingA && !mbar_wait(smem_u32(&bar_empty[slot]), ((t / kRingA) - 1) & 1, err)) {
                         abort_sh = 1;
                         break;
                     }
-                    const uint32_t fb = smem_u32(&bar_full[a]);
+                    const uint32_t fb = smem_u32(&bar_full[slot]);
                     mbar_expect_tx(fb, kATile);
-                    tma_load_3d(aring + a * kATile, &tmA, kc * 64, (fbase + f) * mpad + mt * 128, a, fb);
+                    tma_load_3d(aring + slot * kATile, &tmA, kc * 64, (fbase + f) * mpad + mt * 128, a, fb);
                     issued_a = t + 1;
                 }
+                if (abort_sh) break;
             }
             // teardown: copies in flight (bounded)
-            for (int t = issued_a - 1; t >= 0 && t >= issued_a - kS; --t)
-                mbar_wait(smem_u32(&bar_full[t % kS]), (t / kS) & 1, err);
+            for (int t = issued_a - 1; t >= 0 && t >= issued_a - kRingA; --t)
+                mbar_wait(smem_u32(&bar_full[t % kRingA]), (t / kRingA) & 1, err);
             for (int u = issued_b - 1; u >= 0 && u >= issued_b - 2; --u)
                 mbar_wait(smem_u32(&bar_bfull[u & 1]), (u >> 1) & 1, err);
         }
@@ -247,15 +251,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 for (int a = 0; a < kS && ok; ++a) {
-                    const int t = u * kS + a;
-                    if (!mbar_wait(smem_u32(&bar_full[a]), (t / kS) & 1, err) || abort_sh) {
+                    const int t = u * kS + a, slot = t % kRingA;
+                    if (!mbar_wait(smem_u32(&bar_full[slot]), (t / kRingA) & 1, err) || abort_sh) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t ad = smem_desc_sw128(aring + a * kATile + ks * 32);
+                        const uint64_t ad = smem_desc_sw128(aring + slot * kATile + ks * 32);
 #pragma unroll
                         for (int b = 0; b < kS; ++b) {
                             if (a + b >= kLevels) continue;
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             written |= 1u << lv;
                         }
                     }
-                    mma_commit(smem_u32(&bar_empty[a]));
+                    mma_commit(smem_u32(&bar_empty[slot]));
                 }
                 if (ok) mma_commit(smem_u32(&bar_bempty[bs]));
             }
@@ -275,16 +279,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_wait(smem_u32(&bar_done), 0, err);
         }
     } else {
-        // ---- epilogue: warp w drains lanes 32 (w % 4).. (rows) for columns 32 (w / 4).. ----
+        // ---- epilogue: warp w drains lanes 32 (w % 4).. (rows) for columns (kNT / 2) (w / 4).. ----
         const int q = warp & 3, h = warp >> 2, r = 32 * q + lane, i = mt * 128 + r;
         const bool bad = !mbar_wait(smem_u32(&bar_acc), 0, err) || abort_sh;
         if (!named_sync_or(1, 256, bad)) {
             tc_fence_after();
             const int ea = i < N ? eA[(size_t)(fbase + f) * mpad + i] : 0;
 #pragma unroll
-            for (int c0 = 0; c0 < 32; c0 += 8) {
+            for (int c0 = 0; c0 < kNT / 2; c0 += 8) {
                 uint32_t v[kLevels][8];
-                const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h + c0);
+                const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((kNT / 2) * h + c0);
 #pragma unroll
                 for (int lv = 0; lv < kLevels; ++lv) tmem_ld8(tl + (uint32_t)(lv * kNT), v[lv]);
                 tmem_ld_wait();
@@ -298,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     long long lo = (long long)__float2int_rn(__uint_as_float(v[3][c]));
 #pragma unroll
                     for (int lv = 4; lv < kLevels; ++lv) lo = lo * 128 + (long long)__float2int_rn(__uint_as_float(v[lv][c]));
-                    const int col = 32 * h + c0 + c;
+                    const int col = (kNT / 2) * h + c0 + c;
                     stage_out[r * (kNT + 1) + col] = fma(__ll2double_rn(hi), 268435456.0, __ll2double_rn(lo)) *
                                                      pow2d(ea + eB_sh[col] - 2 * (kW - 1) - kW * (kLevels - 1));
                 }
@@ -306,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         named_sync(1, 256);
         if (!bad && !abort_sh) {
-            // coalesced row-major stores: warp w writes rows w, w + 8, ..., two columns per lane
+            // coalesced row-major stores: warp w writes rows w, w + 8, ..., one column per lane
             for (int rr = warp; rr < 128; rr += 8) {
                 const int ii = mt * 128 + rr;
                 if (ii >= N) break;
@@ -368,7 +372,7 @@ cudaError_t t_update(slmc_ctx* c, int nf, cudaStream_t s) {
                                                                c->fbase, pb, CB);
     k_tt_slice_A<<<dim3((N + RB - 1) / RB, nf), 256, smA, s>>>(c->QR, A, c->tt_eA, c->tt_flag, N, npad, mpad, MT,
                                                                c->fbase, pa, RB);
-    const size_t smem = 1024 + 2 * (size_t)kBChunk + (size_t)kS * kATile;
+    const size_t smem = 1024 + 2 * (size_t)kBChunk + (size_t)kRingA * kATile;
     e = cudaFuncSetAttribute(k_tt_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_tt_gemm<<<dim3(npad / kNT, MT, nf), kThreads, smem, s>>>(c->tt_mapA, c->tt_mapB, c->tt_eA, c->tt_eB, c->tt_flag,
