@@ -207,10 +207,14 @@ def qrt_panel_sizes(N):
 
 
 def qr_panel_flops(N):
-    """FP64 flops of the panels of one QR: Householder QR of each m x BP panel (2 m BP^2 - 2/3 BP^3),
-    its Gram matrix V^T V (m BP^2) and compact-WY triangle S (BP^3 / 3)."""
+    """FP64 flops of the panel kernels of one QR: Householder QR of each m x BP panel (2 m BP^2 - 2/3 BP^3);
+    the last panel also forms its Gram matrix V^T V (m BP^2) and compact-WY triangle S (BP^3 / 3), which
+    the tensor-core products form for the other panels."""
     bp = qr_panel_width(N)
-    return sum(2.0 * m * bp * bp - 2.0 / 3.0 * bp ** 3 + m * bp * bp + bp ** 3 / 3.0 for _, m, _ in qrt_panel_sizes(N))
+    sizes = qrt_panel_sizes(N)
+    w = sum(2.0 * m * bp * bp - 2.0 / 3.0 * bp ** 3 for _, m, _ in sizes)
+    m_last = sizes[-1][1]
+    return w + m_last * bp * bp + bp ** 3 / 3.0
 
 
 def qr_trailing_flops(N):
@@ -621,7 +625,8 @@ def run_gpu(args):
             t = tensor_use(wl, nf, ngroups, args.precision, prof, peaks).get("qrtc:" + args.precision)
             if t:
                 roof = dict(common, bound="tensor", achieved=t["issued_tflops"], peak=t["peak_tflops"],
-                            unit="TFLOP/s", frac=t["frac_of_peak"], traffic=None, peak_source=t["peak_source"])
+                            unit="TFLOP/s", frac=t["frac_of_peak"], traffic=traffic, peak_source=t["peak_source"],
+                            fp64_equivalent_tflops=t["fp64_equivalent_tflops"])
         elif kind == "flop":  # tensor-core classes: issued BF16 flops against the measured BF16 rate
             t = tensor_use(wl, nf, ngroups, args.precision, prof, peaks).get(dom + ":" + args.precision)
             if t:
