@@ -17,7 +17,12 @@
 //    along y commute); the mu factors of B_l and B_l^-1 cancel, and the wrap becomes four
 //    in-place circulant transforms along the lines of G: 2 N^2 (Lx + Ly) FMAs instead of
 //    the 2 N^3 of two dense products;
-//  * G stays in shared memory when it fits (N <= 160), else in global memory (L2-resident);
+//  * G stays in shared memory when it fits (N <= 160), else in global memory (L2-resident). There the
+//    accepted moves of a slice are delayed in batches of up to 32 (Ad, Bd in shared memory, with the
+//    running diagonal of G for the decisions): each new move needs only the current column and row
+//    of G, and the batch is added to G in one pass. Every entry is formed by the same FMA chain in
+//    the same order as immediate rank-1 updates, so the results are bit-identical, for one read and
+//    write of G per batch instead of per move;
 //  * the proposal, Delta_ii, exp(d ln w_bose) and both uniforms of every site of a slice are
 //    computed in parallel before the slice's sites are visited; each thread then takes the
 //    site's decision itself (u < R^2 exp(d ln w_bose), the same test as
@@ -38,13 +43,44 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// G0 += sum_{q < cnt} A_q B_q^T in place (rows by warps, 4 columns per lane per pass), each entry by the
+// FMA chain of cnt immediate rank-1 updates in their order: the result equals theirs bit for bit, for
+// one read and one write of G per batch instead of per accepted move.
+__device__ __forceinline__ void dqmc_flush(double* G, const double* Ad, const double* Bd, int cnt, int N, int lane,
+                                           int warp) {
+    for (int j = warp; j < N; j += kThreads / 32) {
+        double* Gj = G + (size_t)j * N;
+        for (int m0 = 0; m0 < N; m0 += 128) {
+            double acc[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int m = m0 + lane + 32 * t;
+                acc[t] = m < N ? Gj[m] : 0.0;
+            }
+            for (int q = 0; q < cnt; ++q) {
+                const double aj = Ad[q * N + j];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int m = m0 + lane + 32 * t;
+                    if (m < N) acc[t] = fma(aj, Bd[q * N + m], acc[t]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int m = m0 + lane + 32 * t;
+                if (m < N) Gj[m] = acc[t];
+            }
+        }
+    }
+}
+
 template <int LMAX>
 __global__ void __launch_bounds__(kThreads) k_dqmc_slices(double* __restrict__ x, double* __restrict__ Gall, int Lx,
                                                           int Ly, int L, int l0, int nsl, double dtau,
                                                           const double* __restrict__ kron,
                                                           double lam, double w02, double delta, uint32_t key0,
                                                           uint32_t key1, uint32_t sweep, int chain0, int g_in_smem,
-                                                          unsigned long long* __restrict__ n_acc) {
+                                                          int kd, unsigned long long* __restrict__ n_acc) {
     extern __shared__ double dsm[];
     constexpr int QMAX = (LMAX * LMAX + 31) / 32;  // columns per lane in the rank-1 update
     const int N = Lx * Ly;
@@ -64,6 +100,12 @@ __global__ void __launch_bounds__(kThreads) k_dqmc_slices(double* __restrict__ x
     double* exi = ex + slmc::kKronTab;   // [2 Lx] E_x^-1
     double* ey = exi + slmc::kKronTab;   // [2 Ly] E_y
     double* eyi = ey + slmc::kKronTab;   // [2 Ly] E_y^-1
+    // delayed updates (kd > 0, G in global memory): accepted moves q < cnt of the current batch as
+    // G = G0 + sum_q A_q B_q^T, A_q = -(Delta/R) G[:, i_q], B_q = e_i - G[i_q, :] ([kd][N] each), and the
+    // running diagonal of G
+    double* Ad = eyi + slmc::kKronTab;
+    double* Bd = Ad + (size_t)kd * N;
+    double* dg = Bd + (size_t)kd * N;
     double* xf = x + (size_t)f * N * L;
     const uint32_t chain = (uint32_t)(chain0 + f);
 
@@ -110,11 +152,44 @@ __global__ void __launch_bounds__(kThreads) k_dqmc_slices(double* __restrict__ x
             slmc::circ_line<LMAX, true>(G, ix * N + j, Lx * N, Ly, ey, nullptr, 0, s + ix, Lx, sinv[j]);  // row ix + Lx d
         }
         __syncthreads();
+        if (kd > 0) {
+            for (int j = tid; j < N; j += kThreads) dg[j] = G[(size_t)j * N + j];
+            __syncthreads();
+        }
+        int cnt = 0;  // delayed moves of the current batch (block-uniform)
         for (int i = 0; i < N; ++i) {
             // every thread takes the same decision from the same G_ii
-            const double R = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -G[(size_t)i * N + i]), dl[i]));
+            const double gii = kd > 0 ? dg[i] : G[(size_t)i * N + i];
+            const double R = __dadd_rn(1.0, __dmul_rn(__dadd_rn(1.0, -gii), dl[i]));
             if (!(ua[i] < R * R * eb[i])) continue;
             const double a = dl[i] * __drcp_rn(R);
+            if (kd > 0) {
+                // the current column G[:, i] and row G[i, :] from G0 and the batch, each entry by the
+                // same FMA chain the immediate update would have applied to it
+                for (int j = tid; j < N; j += kThreads) {
+                    double cj = G[(size_t)j * N + i], rj = G[(size_t)i * N + j];
+                    for (int q = 0; q < cnt; ++q) {
+                        cj = fma(Ad[q * N + j], Bd[q * N + i], cj);
+                        rj = fma(Ad[q * N + i], Bd[q * N + j], rj);
+                    }
+                    const double aj = -a * cj;
+                    const double bj = (j == i ? 1.0 : 0.0) - rj;
+                    Ad[cnt * N + j] = aj;
+                    Bd[cnt * N + j] = bj;
+                    dg[j] = fma(aj, bj, dg[j]);
+                }
+                if (tid == 0) {
+                    xf[(size_t)i * L + c] = xn[i];
+                    ++accepted;
+                }
+                __syncthreads();
+                if (++cnt == kd) {
+                    dqmc_flush(G, Ad, Bd, cnt, N, lane, warp);
+                    cnt = 0;
+                    __syncthreads();
+                }
+                continue;
+            }
             for (int j = tid; j < N; j += kThreads) {
                 ac[j] = -a * G[(size_t)j * N + i];
                 rw[j] = (j == i ? 1.0 : 0.0) - G[(size_t)i * N + j];
@@ -138,6 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_dqmc_slices(double* __restrict__ x
             }
             __syncthreads();
         }
+        if (cnt > 0) dqmc_flush(G, Ad, Bd, cnt, N, lane, warp);  // the slice's last batch
         __syncthreads();  // rejected sites take no barrier: the next slice's tables wait for all threads here
     }
     if (tid == 0 && n_acc) n_acc[f] += (unsigned long long)accepted;
@@ -280,9 +356,12 @@ cudaError_t gemm64(const GemmArgs& g, double* C, int N, int nf, int sstride, cud
     return launch_gemm<32, kAik, kBjk, kCrow>(g, C, N, nf, sstride, s);
 }
 
-size_t dqmc_smem_bytes(int N, bool g_in_smem) {
-    return ((g_in_smem ? (size_t)N * N : 0) + 8 * (size_t)N + 4 * slmc::kKronTab) * sizeof(double);
+size_t dqmc_smem_bytes(int N, bool g_in_smem, int kd = 0) {
+    return ((g_in_smem ? (size_t)N * N : 0) + 8 * (size_t)N + 4 * slmc::kKronTab + (kd > 0 ? (2 * (size_t)kd + 1) * N : 0)) *
+           sizeof(double);
 }
+
+constexpr int kDelayMax = 32;  // accepted moves per delayed batch (G in global memory)
 
 bool dqmc_supported(const slmc_ctx* c) { return c->L >= 2 && c->kron != nullptr; }
 
@@ -294,13 +373,20 @@ cudaError_t launch_slices(slmc_ctx* c, double* x, double* G, int nf, int chain0,
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     const bool in_smem = dqmc_smem_bytes(c->N, true) <= (size_t)optin;
-    const size_t bytes = dqmc_smem_bytes(c->N, in_smem);
+    // G in global memory: batch up to kd accepted moves in shared memory (delayed updates)
+    int kd = 0;
+    if (!in_smem) {
+        kd = kDelayMax;
+        while (kd > 1 && dqmc_smem_bytes(c->N, false, kd) > (size_t)optin) kd /= 2;
+        if (dqmc_smem_bytes(c->N, false, kd) > (size_t)optin) kd = 0;
+    }
+    const size_t bytes = dqmc_smem_bytes(c->N, in_smem, kd);
     e = cudaFuncSetAttribute(k_dqmc_slices<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     k_dqmc_slices<LMAX><<<nf, kThreads, bytes, s>>>(
         x, G, c->p.Lx, c->p.Ly, c->L, l0, nsl, c->p.dtau, c->kron, c->p.lambda, c->p.omega0 * c->p.omega0,
         c->p.sweep_delta, (uint32_t)(c->p.seed & 0xffffffffu), (uint32_t)(c->p.seed >> 32), (uint32_t)sweep, chain0,
-        in_smem ? 1 : 0, reinterpret_cast<unsigned long long*>(n_acc));
+        in_smem ? 1 : 0, kd, reinterpret_cast<unsigned long long*>(n_acc));
     return cudaGetLastError();
 }
 
