@@ -19,10 +19,11 @@
 //    the 2 N^3 of two dense products;
 //  * G stays in shared memory when it fits (N <= 160), else in global memory (L2-resident). There the
 //    accepted moves of a slice are delayed in batches of up to 32 (Ad, Bd in shared memory, with the
-//    running diagonal of G for the decisions): each new move needs only the current column and row
-//    of G, and the batch is added to G in one pass. Every entry is formed by the same FMA chain in
-//    the same order as immediate rank-1 updates, so the results are bit-identical, for one read and
-//    write of G per batch instead of per move;
+//    running diagonal of G for the decisions; the batch size is what the shared memory left holds):
+//    each new move needs only the current column and row of G, and the batch is added to G in one
+//    register-tiled pass. Every entry is formed by the same FMA chain in the same order as immediate
+//    rank-1 updates, so the results are bit-identical, for one read and write of G per batch
+//    instead of per move;
 //  * the proposal, Delta_ii, exp(d ln w_bose) and both uniforms of every site of a slice are
 //    computed in parallel before the slice's sites are visited; each thread then takes the
 //    site's decision itself (u < R^2 exp(d ln w_bose), the same test as
@@ -373,7 +374,9 @@ cudaError_t launch_slices(slmc_ctx* c, double* x, double* G, int nf, int chain0,
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     const bool in_smem = dqmc_smem_bytes(c->N, true) <= (size_t)optin;
-    // G in global memory: batch up to kd accepted moves in shared memory (delayed updates)
+    // G in global memory: batch up to kd accepted moves in shared memory (delayed updates). With G in
+    // shared memory the immediate rank-1 updates were faster (12x12: 463 against 418 chain-sweeps/s
+    // with batches of 16), since there a pass over G costs no L2 traffic.
     int kd = 0;
     if (!in_smem) {
         kd = kDelayMax;
