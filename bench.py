@@ -706,7 +706,7 @@ def run_gpu(args):
 
 def run_uneven_batch(args, dev, seed):
     """Uneven batch: 64 chains each of 8x8/L=80, 10x10/L=100, 12x12/L=120, 16x16/L=160 (beta = L dtau),
-    FP32 slices, n_s and tiles autotuned per class, advanced round by round (one cumulative update of
+    slices in the --batch-precision mode, n_s and tiles autotuned per class, advanced round by round (one cumulative update of
     every chain per round, 20 E_eff sweeps each) by replaying one captured CUDA graph. Per update the
     E_eff sweeps of all 256 chains run in one persistent queue launch; the same batch with each
     class's kernel-per-half-sweep sequence instead is timed beside it."""
@@ -714,14 +714,16 @@ def run_uneven_batch(args, dev, seed):
     from paper_1802_06177_gb300.workloads import UNEVEN_BATCH
     tuned, classes = {}, []
     for Lx, L, n in UNEVEN_BATCH:
-        r = autotune(Lx, Lx, L, precision="fp32", ntune=16, tol=5e-5, seed=seed)
+        r = autotune(Lx, Lx, L, precision=args.batch_precision, ntune=16, tol=5e-5, seed=seed)
         tuned["%dx%d_L%d" % (Lx, Lx, L)] = {"n_s": r["n_s"], "qr_panel": r["qr_panel"],
                                             "slice_cols": r["slice_cols"], "max_abs_dlndet": r["max_abs_dlndet"]}
-        classes.append(dict(Lx=Lx, L=L, nchains=n, n_s=r["n_s"], precision="fp32", seed=seed, sweep_delta=0.3,
+        classes.append(dict(Lx=Lx, L=L, nchains=n, n_s=r["n_s"], precision=args.batch_precision, seed=seed,
+                            sweep_delta=0.3,
                             tuning=(r["qr_panel"], r["slice_cols"])))
     out = _time_uneven(args, dev, seed, classes, queue=True)
     out["per_class_kernels"] = _time_uneven(args, dev, seed, classes, queue=False)
     out["tuned"] = tuned
+    out["precision"] = args.batch_precision
     return out
 
 
@@ -938,6 +940,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-rounds", type=int, default=100)
+    ap.add_argument("--batch-precision", default="fp32", choices=["fp64", "fp32", "tf32x3", "bf16x9"],
+                    help="slice precision of the uneven batch")
     ap.add_argument("--sub-batches", type=int, default=0, help="forked streams per batch (0 = library default)")
     ap.add_argument("--slice-groups", type=int, default=0, help="FP32 slice kernel column groups (0 = default)")
     ap.add_argument("--sub-priorities", type=int, default=-1, help="descending sub-batch stream priorities (1/0)")
