@@ -940,7 +940,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-rounds", type=int, default=100)
-    ap.add_argument("--batch-precision", default="fp32", choices=["fp64", "fp32", "tf32x3", "bf16x9"],
+    ap.add_argument("--batch-precision", default="bf16x9", choices=["fp64", "fp32", "tf32x3", "bf16x9"],
                     help="slice precision of the uneven batch")
     ap.add_argument("--sub-batches", type=int, default=0, help="forked streams per batch (0 = library default)")
     ap.add_argument("--slice-groups", type=int, default=0, help="FP32 slice kernel column groups (0 = default)")

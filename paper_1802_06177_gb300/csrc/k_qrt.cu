@@ -68,6 +68,67 @@ __device__ __forceinline__ void levels_to_int(const uint32_t (&v)[kLv], long lon
     for (int lv = 4; lv < kLv; ++lv) lo = lo * 128 + (long long)__float2int_rn(__uint_as_float(v[lv]));
 }
 
+// Compact-WY triangle S of BP reflectors from their Gram matrix G (row stride ldg) and tau, by the 256
+// threads of the 8 epilogue warps (named barrier 1), in blocks: S is the inverse of the upper
+// triangular T with T_cc = 1 / tau_c and T_qc = G_qc (q < c), so the four diagonal blocks of BP/4
+// columns follow the column recurrence S_cc = tau_c, S[., c] = -tau_c S[., <c] G[<c, c] (one warp
+// each), and blocks merge as S12 = -S11 T12 S22 (T12 = G of the two blocks; no division by tau, so a
+// trivial reflector, tau = 0, gives its zero column as the recurrence does). The recurrence of one
+// warp over all BP columns was a chain of BP dependent steps. tmp holds BP x BP doubles.
+template <int BP>
+__device__ __forceinline__ void wy_triangle_blocked(const double* G, int ldg, const double* tau, double* S, double* tmp,
+                                                    int tid) {
+    constexpr int B4 = BP / 4, B2 = BP / 2;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int idx = tid; idx < BP * BP; idx += 256) S[idx] = 0.0;
+    slmc::tc::named_sync(1, 256);
+    if (warp < 4) {  // diagonal block b = warp: rows and columns o .. o + B4 - 1
+        const int o = warp * B4;
+        for (int c = 0; c < B4; ++c) {
+            double v = 0.0;
+            if (lane < c) {
+                for (int q = lane; q < c; ++q) v = fma(S[(o + lane) * BP + o + q], G[(o + q) * ldg + o + c], v);
+                v = -tau[o + c] * v;
+            } else if (lane == c) {
+                v = tau[o + c];
+            }
+            if (lane <= c) S[(o + lane) * BP + o + c] = v;
+            __syncwarp();
+        }
+    }
+    slmc::tc::named_sync(1, 256);
+    {  // two merges of block pairs (2m, 2m + 1) into B2 x B2 triangles: U = T12 S22, then S12 = -S11 U
+        const int m = tid / (B4 * B4), e = tid % (B4 * B4), r = e / B4, c = e % B4;
+        const int o1 = m * B2, o2 = o1 + B4;
+        if (m < 2) {
+            double u = 0.0;
+            for (int k = 0; k <= c; ++k) u = fma(G[(o1 + r) * ldg + o2 + k], S[(o2 + k) * BP + o2 + c], u);
+            tmp[m * B4 * B4 + e] = u;
+        }
+        slmc::tc::named_sync(1, 256);
+        if (m < 2) {
+            double v = 0.0;
+            for (int k = r; k < B4; ++k) v = fma(S[(o1 + r) * BP + o1 + k], tmp[m * B4 * B4 + k * B4 + c], v);
+            S[(o1 + r) * BP + o2 + c] = -v;
+        }
+        slmc::tc::named_sync(1, 256);
+    }
+    for (int e = tid; e < B2 * B2; e += 256) {  // the last merge: U = T12 S22 over the two halves
+        const int r = e / B2, c = e % B2;
+        double u = 0.0;
+        for (int k = 0; k <= c; ++k) u = fma(G[r * ldg + B2 + k], S[(B2 + k) * BP + B2 + c], u);
+        tmp[e] = u;
+    }
+    slmc::tc::named_sync(1, 256);
+    for (int e = tid; e < B2 * B2; e += 256) {  // S12 = -S11 U
+        const int r = e / B2, c = e % B2;
+        double v = 0.0;
+        for (int k = r; k < B2; ++k) v = fma(S[r * BP + k], tmp[k * B2 + c], v);
+        S[r * BP + B2 + c] = -v;
+    }
+    slmc::tc::named_sync(1, 256);
+}
+
 // ---- panel ----------------------------------------------------------------------------------
 // 16 warps per field: the panel is a chain of latency-bound column steps (dot products, warp
 // reductions, a block barrier each) that leaves the FP64 pipe half idle with 8 warps.
@@ -401,10 +462,7 @@ __global__ void __launch_bounds__(kQT, 2)
             }
         }
         named_sync(1, 256);
-        if (!bad) {
-            if (warp == 0) wy_triangle<BP>(stW, WS, tau_sh, Ssh, BP, lane);  // S from G = rows 0..BP-1
-        }
-        named_sync(1, 256);
+        if (!bad) wy_triangle_blocked<BP>(stW, WS, tau_sh, Ssh, stWp, threadIdx.x);  // S from G = rows 0..BP-1
         if (!bad) {
             if (mt == 0)  // S of the panel for the formation of Q
                 for (int idx = threadIdx.x; idx < BP * BP; idx += 256)
@@ -419,19 +477,21 @@ __global__ void __launch_bounds__(kQT, 2)
                 }
         }
         named_sync(1, 256);
-        if (!bad && threadIdx.x < kMC) {
-            const int rr = BP + threadIdx.x, j2 = mt * kMC + threadIdx.x;
-            if (j2 < n_t) {
-                long long mx = 0;
-                for (int m = 0; m < BP; ++m) mx = max(mx, abs_bits(stWp[rr * WS + m]));
-                const int e = exponent_of_bits(mx);
-                eW[(size_t)gf * wpad + j2] = e;
-                __nv_bfloat16* dst = Ws + ((size_t)gf * wpad + j2) * 64;
-                for (int m = 0; m < BP; ++m) {
+        if (!bad) {
+            // slices of W', one row (trailing column) per warp at a time, lane = reflector: the row's
+            // exponent by a warp reduction, each plane's row one coalesced store
+            for (int t = warp; t < kMC; t += 8) {
+                const int rr = BP + t, j2 = mt * kMC + t;
+                if (j2 >= n_t) break;
+                const double v = lane < BP ? stWp[rr * WS + lane] : 0.0;
+                const int e = exponent_of_bits(warp_max_bits(abs_bits(v)));
+                if (lane == 0) eW[(size_t)gf * wpad + j2] = e;
+                if (lane < BP) {
                     __nv_bfloat16 q[kS];
-                    slice7(stWp[rr * WS + m], e, q);
+                    slice7(v, e, q);
+                    __nv_bfloat16* dst = Ws + ((size_t)gf * wpad + j2) * 64 + lane;
 #pragma unroll
-                    for (int s = 0; s < kS; ++s) dst[(size_t)s * planeW + m] = q[s];
+                    for (int s = 0; s < kS; ++s) dst[(size_t)s * planeW] = q[s];
                 }
             }
         }
