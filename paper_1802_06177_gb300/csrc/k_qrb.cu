@@ -91,10 +91,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_qrb(double* __restrict__ Yall, 
     }
     __syncthreads();
     for (int j = tid; j < N; j += kThreads) {
-        const double kj = s_key[j];
+        // keys are >= +0 or -1: their bit patterns as 64-bit integers order as the values do, and
+        // the integer compares leave the FP64 pipe to the factorisation
+        const long long kj = __double_as_longlong(s_key[j]);
         int r = 0;
         for (int i = 0; i < N; ++i) {
-            const double ki = s_key[i];
+            const long long ki = __double_as_longlong(s_key[i]);
             r += (ki > kj) || (ki == kj && i < j);
         }
         s_perm[r] = j;
