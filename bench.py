@@ -706,8 +706,8 @@ def run_gpu(args):
 
 def run_uneven_batch(args, dev, seed):
     """Uneven batch: 64 chains each of 8x8/L=80, 10x10/L=100, 12x12/L=120, 16x16/L=160 (beta = L dtau),
-    slices in the --batch-precision mode, n_s and tiles autotuned per class, advanced round by round (one cumulative update of
-    every chain per round, 20 E_eff sweeps each) by replaying one captured CUDA graph. Per update the
+    slices in the --batch-precision mode, n_s and tiles autotuned per class, advanced round by round (one
+    cumulative update of every chain per round, 20 E_eff sweeps each) by replaying one captured CUDA graph. Per update the
     E_eff sweeps of all 256 chains run in one persistent queue launch; the same batch with each
     class's kernel-per-half-sweep sequence instead is timed beside it."""
     from paper_1802_06177_gb300.slmc import autotune
